@@ -1,0 +1,234 @@
+/*
+ * fvv.h -- C ABI of the GB300 (sm_103a) coarse-to-fine visual-hull library.
+ *
+ * The library implements steps (B)-(D) of "A Fast Free-viewpoint Video
+ * Synthesis Algorithm for Sports Scenes" (arXiv 1903.11785) for calibrated,
+ * static cameras (Sec. II-A) and per-frame binary silhouettes:
+ *
+ *   B-1 coarse ("sparse") volumetric visual hull            Sec. II-B-1
+ *   B-2 26-connected CCL, minimum 3D box, noise filter       Sec. II-B-2, Eq. (1)
+ *   B-3 fine ("dense") hull inside each 3D ROI               Sec. II-B-3
+ *   C   exact edge/hull intersection + marching cubes        Sec. II-C, Eqs. (2)-(3)
+ *   D-1 per-camera depth image                               Sec. II-D-1, Eq. (4)
+ *   D-2 visibility by T_v and colour from the nearest
+ *       unoccluded camera (per vertex)                       Sec. II-D-2, II-E
+ *
+ * Conventions.  World coordinates in metres.  Camera n projects a world point
+ * X through its row-major 3x4 matrix P_n: (x', y', w') = P_n (X, 1); the pixel
+ * is (floor(x'/w'), floor(y'/w')), pixel (px, py) covering [px, px+1) x
+ * [py, py+1); images are row-major, W pixels per row.  Voxel i of a grid with
+ * origin o and step s is tested at its centre o + (i + 1/2) s.  Linear voxel
+ * index L = (z*ny + y)*nx + x (x fastest).  All floating point on the device
+ * is IEEE binary32, round to nearest, in a fixed order with no fused
+ * multiply-add, so results are reproducible bit for bit.
+ *
+ * Memory.  As the paper does (Sec. III-B), all device memory a rig needs is
+ * taken once, at fvv_create_rig, as one arena: either a buffer the caller
+ * passes (for example a torch tensor) or one the library allocates.  It never
+ * grows.  A rig has max_slots frame slots; a slot holds one frame's packed
+ * silhouettes, grids, mesh, depth images and colours.  Results of a slot stay
+ * valid until that slot is uploaded to or reconstructed again.
+ *
+ * Streams.  Every call that takes `void* stream` (a cudaStream_t; NULL is the
+ * legacy default stream) only enqueues work on it and returns; calls on one
+ * rig must be ordered on one stream (or by the caller's events), because they
+ * share the rig's slots.  fvv_get_counts synchronises the stream it is given.
+ *
+ * Errors.  Every call returns an fvv_status and never throws.  A NULL or
+ * inconsistent argument gives FVV_ERR_INVALID_ARG; a failed CUDA call gives
+ * FVV_ERR_CUDA; work that exceeds a capacity chosen at creation is detected
+ * on the device, skipped without writing out of bounds, and reported by
+ * fvv_get_counts as FVV_ERR_CAPACITY with the overflowing capacity in
+ * fvv_counts.flags.  fvv_last_error gives a message for the last failure.
+ *
+ * Thread safety.  A rig may be used by one host thread at a time.
+ */
+#ifndef FVV_H
+#define FVV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FVV_VERSION 1
+#define FVV_MAX_CAMS 64      /* cameras per rig                              */
+#define FVV_MAX_BATCH 256    /* slots per fvv_reconstruct / fvv_colour call   */
+
+typedef struct fvv_rig fvv_rig;
+
+typedef enum {
+    FVV_OK = 0,
+    FVV_ERR_INVALID_ARG = 1,
+    FVV_ERR_OUT_OF_MEMORY = 2,
+    FVV_ERR_CAPACITY = 3,
+    FVV_ERR_NOT_READY = 4,
+    FVV_ERR_TIMEOUT = 5,
+    FVV_ERR_CUDA = 6
+} fvv_status;
+
+/* What a camera whose image does not contain a point's projection (or that
+ * has the point behind it) does.  STRICT: it votes background, the literal
+ * reading of Sec. II-B, where a voxel projecting outside a silhouette is
+ * empty.
+ * ABSTAIN: it does not vote; a point no camera votes for is unoccupied. */
+enum { FVV_OOB_STRICT = 0, FVV_OOB_ABSTAIN = 1 };
+
+/* Bits of fvv_counts.flags: which capacity a reconstruction exceeded. */
+enum {
+    FVV_FLAG_ROOTS = 1u << 0,      /* raw 26-connected components > max_components */
+    FVV_FLAG_ROIS = 1u << 1,       /* kept components > max_rois                   */
+    FVV_FLAG_FINE = 1u << 2,       /* fine grid words > max_fine_words, or a ROI
+                                      side longer than 32765 fine voxels          */
+    FVV_FLAG_VERTS = 1u << 3,      /* vertices > max_verts                         */
+    FVV_FLAG_TRIS = 1u << 4,       /* triangles > max_tris                         */
+    FVV_FLAG_LOOP = 1u << 5        /* an iteration bound of union-find was hit    */
+};
+
+/* The cameras (Sec. II-A: calibrated in advance, static).  All arrays are
+ * host memory, read during fvv_create_rig only. */
+typedef struct {
+    int n_cams;            /* 1..FVV_MAX_CAMS                                 */
+    const float *P;        /* n_cams x 12: row-major 3x4 world -> pixel       */
+    const float *centre;   /* n_cams x 3: camera centres (depth, colour rank) */
+    const int *width;      /* n_cams: image width in pixels, 1..65535         */
+    const int *height;     /* n_cams: image height in pixels, 1..65535        */
+    int max_slots;         /* frames that can be held at once, >= 1           */
+    int host_staging;      /* 1: reserve per-slot buffers so masks and RGB can
+                              be passed in host memory; 0: device pointers only */
+} fvv_rig_desc;
+
+/* Reconstruction parameters.  The capacities are per slot; 0 picks a default
+ * derived from the grid (see fvv_query_arena). */
+typedef struct {
+    float vol_min[3], vol_max[3]; /* the pre-defined 3D volume, metres        */
+    float coarse_m;        /* coarse voxel step (Sec. II-B-1), metres          */
+    float fine_m;          /* fine voxel step (Sec. II-B-3), metres            */
+    int bisect_steps;      /* bisections per bipolar edge, 0..30 (0 = midpoint) */
+    int t_np, t_nb;        /* Eq. (1): keep a component iff t_np <= voxels <= t_nb */
+    float t_v;             /* Sec. II-D-2 occlusion threshold, metres          */
+    int oob_policy;        /* FVV_OOB_STRICT or FVV_OOB_ABSTAIN                */
+    int max_components;    /* raw components per frame (<= 8192)              */
+    int max_rois;          /* kept components per frame (<= 4096)             */
+    long long max_fine_words;  /* 32-sample words of all padded fine grids    */
+    long long max_verts;   /* mesh vertices per frame                          */
+    long long max_tris;    /* mesh triangles per frame                         */
+} fvv_recon_params;
+
+/* One kept object and its 3D ROI (Sec. II-B-2, II-B-3). */
+typedef struct {
+    int cmin[3], cmax[3];  /* inclusive coarse index box of the component     */
+    int gmin[3], gmax[3];  /* the box grown by one coarse voxel, clamped      */
+    int fdim[3];           /* fine voxels per axis covering the grown box     */
+    float forigin[3];      /* world position of the grown box's lower corner  */
+    int count;             /* coarse voxels in the component                  */
+    int label;             /* canonical label, 1..n_rois                      */
+    long long vert_offset, n_verts;  /* this object's vertices in the slot's mesh  */
+    long long tri_offset, n_tris;    /* this object's triangles in the slot's mesh */
+} fvv_roi;
+
+typedef struct {
+    unsigned int flags;    /* FVV_FLAG_* capacities exceeded (0 = none)        */
+    int n_components;      /* 26-connected components before the filter       */
+    int n_rois;            /* components kept                                 */
+    int pad_;
+    long long n_coarse_on; /* occupied coarse voxels                          */
+    long long n_fine_words;
+    long long n_verts, n_tris;
+    long long tests_coarse, tests_fine, tests_bisect; /* camera tests, with the
+                              per-point early exit at the first background vote */
+} fvv_counts;
+
+/* Per-slot debug views for tests (fvv_get_debug). */
+enum {
+    FVV_DEBUG_SIL_BITS = 0,   /* uint32: per camera H rows of ceil(W/32) words  */
+    FVV_DEBUG_COARSE_BITS = 1,/* uint32: nz*ny rows of ceil(nx/32) words        */
+    FVV_DEBUG_LABELS = 2,     /* int32 nz*ny*nx canonical labels (0 = none)     */
+    FVV_DEBUG_FINE_BITS = 3,  /* uint32: per ROI, (fz+2)*(fy+2) rows of
+                                 ceil((fx+2)/32) words of the padded fine grid  */
+    FVV_DEBUG_DEPTH = 4       /* float32: per camera H*W depth, +inf = empty     */
+};
+
+/* Bytes of device memory fvv_create_rig needs for these arguments (after the
+ * defaults for zero capacities are applied). */
+fvv_status fvv_query_arena(const fvv_rig_desc *desc, const fvv_recon_params *params,
+                           size_t *bytes);
+
+/* Create a rig: validate the cameras and parameters, lay out the arena and
+ * build the marching-cubes table.  `arena` is a device buffer of at least
+ * fvv_query_arena bytes, aligned to 256 bytes, owned by the caller and kept
+ * alive until fvv_destroy_rig; or NULL, in which case the library allocates
+ * (and later frees) it.  On success *out is the new rig. */
+fvv_status fvv_create_rig(const fvv_rig_desc *desc, const fvv_recon_params *params,
+                          void *arena, size_t arena_bytes, fvv_rig **out);
+
+/* Free the rig (and the arena if the library allocated it). Synchronises the
+ * device first.  NULL is accepted. */
+fvv_status fvv_destroy_rig(fvv_rig *rig);
+
+/* Pack one frame's silhouettes into slot `slot` (step a0): masks[n] points
+ * to camera n's H x W uint8 image, nonzero = foreground (Sec. II-A).  With
+ * masks_on_device = 1 the pointers are device memory that must stay valid
+ * until the work on `stream` has run; with 0 they are host memory (pinned
+ * memory makes the copy asynchronous; pageable memory is copied before this
+ * call returns) and the rig needs host_staging. */
+fvv_status fvv_upload_silhouettes(fvv_rig *rig, int slot, const uint8_t *const *masks,
+                                  int masks_on_device, void *stream);
+
+/* Reconstruct the frames in `slots` (n_slots distinct slots, each uploaded):
+ * coarse hull, CCL, filter and ROIs, fine hull, bisected marching-cubes mesh
+ * and per-camera depth images (steps a1..a9).  All slots are processed by the
+ * same launches.  No host synchronisation happens inside. */
+fvv_status fvv_reconstruct(fvv_rig *rig, const int *slots, int n_slots, void *stream);
+
+/* Colour the meshes of `slots` for a virtual viewpoint (step a10, Sec. II-D-2
+ * and II-E): cameras are ranked by distance to viewpoints[3*i..3*i+2]; each
+ * vertex takes the colour of the first camera in that order that has it in
+ * front, inside its image and not occluded (|v - C| - depth <= t_v), else
+ * (0,0,0) and camera -1.  rgb[i*n_cams + n] is camera n's H x W x 3 uint8
+ * image for slots[i]; device or host memory as for fvv_upload_silhouettes. */
+fvv_status fvv_colour(fvv_rig *rig, const int *slots, int n_slots, const uint8_t *const *rgb,
+                      int rgb_on_device, const float *viewpoints, void *stream);
+
+/* Synchronise `stream` and read slot's counts; returns FVV_ERR_CAPACITY if a
+ * capacity was exceeded (counts->flags says which), else FVV_OK. */
+fvv_status fvv_get_counts(fvv_rig *rig, int slot, fvv_counts *counts, void *stream);
+
+/* Copy slot's results into caller-owned buffers (any may be NULL):
+ * rois[n_rois], verts[n_verts*3] float, tris[n_tris*3] uint32 (indices into
+ * the slot's vertices), rgb[n_verts*3] uint8, cam[n_verts] int32.  Sizes come
+ * from fvv_get_counts.  dst_on_device says whether the buffers are device
+ * memory.  The copies are enqueued on `stream` (ROIs are read synchronously). */
+fvv_status fvv_get_results(fvv_rig *rig, int slot, fvv_roi *rois, float *verts, uint32_t *tris,
+                           uint8_t *rgb, int32_t *cam, int dst_on_device, void *stream);
+
+/* Size in bytes of a debug view of slot (fvv_get_counts must have been
+ * called after the reconstruction for FINE_BITS). */
+fvv_status fvv_debug_bytes(fvv_rig *rig, int slot, int what, size_t *bytes);
+
+/* Write a debug view of slot into device buffer dst (bytes from
+ * fvv_debug_bytes), enqueued on `stream`. */
+fvv_status fvv_get_debug(fvv_rig *rig, int slot, int what, void *dst, size_t bytes, void *stream);
+
+/* The marching-cubes table the library built from its face rule: ntri[256]
+ * triangle counts and edges[256*12*3] cube-edge numbers (corner c = dx + 2dy
+ * + 4dz; cube edge e has axis e/4 and lower corner with the other two
+ * coordinates (e%4 & 1, e%4 >> 1) in axis order).  Host memory; no GPU needed. */
+fvv_status fvv_mc_table(uint8_t *ntri, uint8_t *edges);
+
+/* Message of the last failure on rig (or of the last failed create if rig is
+ * NULL).  The string stays valid until the next call on the rig. */
+const char *fvv_last_error(const fvv_rig *rig);
+
+/* Static name of a status code. */
+const char *fvv_status_string(fvv_status status);
+
+int fvv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FVV_H */

@@ -1,0 +1,510 @@
+// fvv_api.cu -- the C ABI of libfvv (include/fvv.h): rig creation and arena
+// layout, argument checking, and the launch sequences of each call.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fvv_internal.h"
+
+using namespace fvv;
+
+struct fvv_rig {
+    CamSet cams;
+    Grid grid;
+    Layout L;
+    int max_slots = 0;
+    int host_staging = 0;
+    int device = 0;
+    int sms = 1;
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    bool own_arena = false;
+    uint8_t* mc_ntri = nullptr;    // device
+    uint8_t* mc_edges = nullptr;   // device
+    float* viewpoints = nullptr;   // device, FVV_MAX_BATCH x 3
+    size_t sil_words = 0, npix = 0;
+    std::vector<int> state;        // per slot: 0 empty, 1 uploaded, 2 reconstructed
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+fvv_status fail(fvv_rig* rig, fvv_status st, const std::string& msg) {
+    if (rig) rig->err = msg;
+    else g_create_err = msg;
+    return st;
+}
+
+fvv_status cuda_fail(fvv_rig* rig, cudaError_t e, const char* what) {
+    return fail(rig, FVV_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+long long um_of(float m) { return llround((double)m * 1e6); }
+
+struct Plan {
+    CamSet cams;
+    Grid grid;
+    Layout L;        // offsets only (base unset)
+    size_t common = 0;   // bytes before the slots region
+    size_t total = 0;
+    size_t sil_words = 0, npix = 0;
+};
+
+// Validate the arguments and lay out the arena.
+fvv_status make_plan(const fvv_rig_desc* d, const fvv_recon_params* p, Plan& pl, std::string& err) {
+    if (!d || !p) { err = "desc and params must not be NULL"; return FVV_ERR_INVALID_ARG; }
+    if (d->n_cams < 1 || d->n_cams > FVV_MAX_CAMS) { err = "n_cams must be 1..64"; return FVV_ERR_INVALID_ARG; }
+    if (!d->P || !d->centre || !d->width || !d->height) { err = "camera arrays must not be NULL"; return FVV_ERR_INVALID_ARG; }
+    if (d->max_slots < 1 || d->max_slots > 65536) { err = "max_slots must be 1..65536"; return FVV_ERR_INVALID_ARG; }
+    CamSet& cs = pl.cams;
+    std::memset(&cs, 0, sizeof(cs));
+    cs.n = d->n_cams;
+    if (p->oob_policy != FVV_OOB_STRICT && p->oob_policy != FVV_OOB_ABSTAIN) { err = "bad oob_policy"; return FVV_ERR_INVALID_ARG; }
+    cs.oob = p->oob_policy;
+    size_t words = 0, pix = 0;
+    for (int n = 0; n < cs.n; ++n) {
+        Cam& c = cs.c[n];
+        for (int k = 0; k < 12; ++k) {
+            c.P[k] = d->P[12 * n + k];
+            if (!std::isfinite(c.P[k])) { err = "P must be finite"; return FVV_ERR_INVALID_ARG; }
+        }
+        for (int k = 0; k < 3; ++k) {
+            c.C[k] = d->centre[3 * n + k];
+            if (!std::isfinite(c.C[k])) { err = "centre must be finite"; return FVV_ERR_INVALID_ARG; }
+        }
+        c.W = d->width[n];
+        c.H = d->height[n];
+        if (c.W < 1 || c.W > 65535 || c.H < 1 || c.H > 65535) { err = "image sizes must be 1..65535"; return FVV_ERR_INVALID_ARG; }
+        c.Wq = (c.W + 31) / 32;
+        c.bit_off = (uint32_t)words;
+        c.pix_off = pix;
+        words += (size_t)c.H * c.Wq;
+        pix += (size_t)c.H * c.W;
+        if (words >= (1ull << 32)) { err = "silhouettes too large"; return FVV_ERR_INVALID_ARG; }
+    }
+    pl.sil_words = words;
+    pl.npix = pix;
+    Grid& g = pl.grid;
+    std::memset(&g, 0, sizeof(g));
+    if (!(p->coarse_m > 0) || !(p->fine_m > 0) || !std::isfinite(p->coarse_m) || !std::isfinite(p->fine_m)) {
+        err = "voxel sizes must be positive"; return FVV_ERR_INVALID_ARG;
+    }
+    g.coarse_um = um_of(p->coarse_m);
+    g.fine_um = um_of(p->fine_m);
+    if (g.coarse_um < 1 || g.fine_um < 1) { err = "voxel sizes must be >= 1 micrometre"; return FVV_ERR_INVALID_ARG; }
+    int dims[3];
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(p->vol_min[a]) || !std::isfinite(p->vol_max[a])) { err = "volume must be finite"; return FVV_ERR_INVALID_ARG; }
+        const long long span = um_of(p->vol_max[a]) - um_of(p->vol_min[a]);
+        if (span <= 0) { err = "vol_max must exceed vol_min"; return FVV_ERR_INVALID_ARG; }
+        const long long n = (span + g.coarse_um - 1) / g.coarse_um;
+        if (n > 32767) { err = "coarse grid too large"; return FVV_ERR_INVALID_ARG; }
+        dims[a] = (int)n;
+        g.o[a] = p->vol_min[a];
+    }
+    g.nx = dims[0]; g.ny = dims[1]; g.nz = dims[2];
+    if ((long long)g.nx * g.ny * g.nz >= (1ll << 31)) { err = "coarse grid too large"; return FVV_ERR_INVALID_ARG; }
+    g.nxw = (g.nx + 31) / 32;
+    g.sc = p->coarse_m;
+    g.sf = p->fine_m;
+    if (p->bisect_steps < 0 || p->bisect_steps > 30) { err = "bisect_steps must be 0..30"; return FVV_ERR_INVALID_ARG; }
+    g.steps = p->bisect_steps;
+    g.t_np = p->t_np;
+    g.t_nb = p->t_nb;
+    g.t_v = p->t_v;
+    if (std::isnan(p->t_v)) { err = "t_v must not be NaN"; return FVV_ERR_INVALID_ARG; }
+    g.max_comp = p->max_components > 0 ? p->max_components : kMaxComponents;
+    g.max_rois = p->max_rois > 0 ? p->max_rois : 256;
+    if (g.max_comp > kMaxComponents || g.max_rois > kMaxRois) { err = "max_components <= 8192, max_rois <= 4096"; return FVV_ERR_INVALID_ARG; }
+    long long fw = p->max_fine_words;
+    if (fw <= 0) {
+        // the whole volume at the fine step, in words, over 16; clamped
+        double vol = 1.0;
+        for (int a = 0; a < 3; ++a) vol *= (double)(um_of(p->vol_max[a]) - um_of(p->vol_min[a])) / (double)g.fine_um;
+        fw = (long long)std::min(std::max(vol / 32.0 / 16.0, (double)(1 << 18)), (double)(1 << 23));
+    }
+    long long mv = p->max_verts > 0 ? p->max_verts : 2 * fw;
+    long long mt = p->max_tris > 0 ? p->max_tris : 2 * mv;
+    if (fw > (1ll << 30) || mv > (1ll << 30) || mt > (1ll << 30)) { err = "capacities must be <= 2^30"; return FVV_ERR_INVALID_ARG; }
+    g.max_fine_words = (uint32_t)fw;
+    g.max_chunks = (uint32_t)((fw + kChunk - 1) / kChunk);
+    g.max_verts = (uint32_t)mv;
+    g.max_tris = (uint32_t)mt;
+
+    Layout& L = pl.L;
+    std::memset(&L, 0, sizeof(L));
+    size_t o = 0;
+    auto take = [&](size_t& off, size_t bytes) { off = o; o = align_up(o + std::max<size_t>(bytes, 1)); };
+    const size_t nvox = (size_t)g.nx * g.ny * g.nz;
+    take(L.info, sizeof(SlotInfo));
+    take(L.sil, words * 4);
+    take(L.coarse, (size_t)g.nz * g.ny * g.nxw * 4);
+    take(L.parent, nvox * 4);
+    take(L.roots, (size_t)g.max_comp * 4);
+    take(L.cstat, (size_t)g.max_comp * 7 * 4);
+    take(L.rois, (size_t)g.max_rois * sizeof(DRoi));
+    take(L.roi_label, (size_t)g.max_comp * 4);
+    take(L.fine, (size_t)fw * 4);
+    take(L.emask, (size_t)fw * 12);
+    take(L.vcnt, (size_t)fw * 4);
+    take(L.tcnt, (size_t)fw * 4);
+    take(L.vpre, (size_t)fw * 4);
+    take(L.tpre, (size_t)fw * 4);
+    take(L.cpart, (size_t)g.max_chunks * 8);
+    take(L.vrec, (size_t)mv * 8);
+    take(L.verts, (size_t)mv * 12);
+    take(L.tris, (size_t)mt * 12);
+    take(L.vrgb, (size_t)mv * 3);
+    take(L.vcam, (size_t)mv * 4);
+    take(L.depth, align_up(pix * 4));
+    if (d->host_staging) {
+        take(L.mask_stage, pix);
+        take(L.rgb_stage, pix * 3);
+    }
+    take(L.rgb_ptrs, (size_t)FVV_MAX_CAMS * sizeof(void*));
+    L.stride = o;
+    pl.common = align_up(256) + align_up(256 * kMaxTriPerCell * 3) + align_up(FVV_MAX_BATCH * 3 * sizeof(float));
+    pl.total = pl.common + (size_t)d->max_slots * L.stride;
+    return FVV_OK;
+}
+
+bool check_slot(fvv_rig* rig, int slot) { return rig && slot >= 0 && slot < rig->max_slots; }
+
+__global__ void k_zero_info(const __grid_constant__ Layout L, const __grid_constant__ SlotList sl) {
+    uint32_t* p = reinterpret_cast<uint32_t*>(slot_ptr<SlotInfo>(L, sl.s[blockIdx.x], L.info));
+    for (unsigned i = threadIdx.x; i < sizeof(SlotInfo) / 4; i += blockDim.x) p[i] = 0u;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fvv_version(void) { return FVV_VERSION; }
+
+const char* fvv_status_string(fvv_status s) {
+    switch (s) {
+        case FVV_OK: return "FVV_OK";
+        case FVV_ERR_INVALID_ARG: return "FVV_ERR_INVALID_ARG";
+        case FVV_ERR_OUT_OF_MEMORY: return "FVV_ERR_OUT_OF_MEMORY";
+        case FVV_ERR_CAPACITY: return "FVV_ERR_CAPACITY";
+        case FVV_ERR_NOT_READY: return "FVV_ERR_NOT_READY";
+        case FVV_ERR_TIMEOUT: return "FVV_ERR_TIMEOUT";
+        case FVV_ERR_CUDA: return "FVV_ERR_CUDA";
+    }
+    return "unknown fvv_status";
+}
+
+const char* fvv_last_error(const fvv_rig* rig) { return rig ? rig->err.c_str() : g_create_err.c_str(); }
+
+fvv_status fvv_mc_table(uint8_t* ntri, uint8_t* edges) {
+    if (!ntri || !edges) return fail(nullptr, FVV_ERR_INVALID_ARG, "NULL table buffer");
+    std::memset(edges, 0, 256 * kMaxTriPerCell * 3);
+    build_mc_table(ntri, edges);
+    return FVV_OK;
+}
+
+fvv_status fvv_query_arena(const fvv_rig_desc* desc, const fvv_recon_params* params, size_t* bytes) {
+    Plan pl;
+    std::string err;
+    const fvv_status st = make_plan(desc, params, pl, err);
+    if (st != FVV_OK) return fail(nullptr, st, err);
+    if (!bytes) return fail(nullptr, FVV_ERR_INVALID_ARG, "bytes must not be NULL");
+    *bytes = pl.total;
+    return FVV_OK;
+}
+
+fvv_status fvv_create_rig(const fvv_rig_desc* desc, const fvv_recon_params* params, void* arena, size_t arena_bytes,
+                          fvv_rig** out) {
+    if (!out) return fail(nullptr, FVV_ERR_INVALID_ARG, "out must not be NULL");
+    *out = nullptr;
+    Plan pl;
+    std::string err;
+    fvv_status st = make_plan(desc, params, pl, err);
+    if (st != FVV_OK) return fail(nullptr, st, err);
+    if (arena && (arena_bytes < pl.total || (reinterpret_cast<uintptr_t>(arena) % kAlign) != 0))
+        return fail(nullptr, FVV_ERR_INVALID_ARG, "arena too small or not 256-byte aligned (need " +
+                                                      std::to_string(pl.total) + " bytes)");
+    fvv_rig* rig = new (std::nothrow) fvv_rig();
+    if (!rig) return fail(nullptr, FVV_ERR_OUT_OF_MEMORY, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&rig->device);
+    if (e != cudaSuccess) { delete rig; return cuda_fail(nullptr, e, "cudaGetDevice"); }
+    e = cudaDeviceGetAttribute(&rig->sms, cudaDevAttrMultiProcessorCount, rig->device);
+    if (e != cudaSuccess) { delete rig; return cuda_fail(nullptr, e, "cudaDeviceGetAttribute"); }
+    if (!arena) {
+        e = cudaMalloc(&arena, pl.total);
+        if (e != cudaSuccess) {
+            delete rig;
+            cudaGetLastError();
+            return fail(nullptr, FVV_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(pl.total) + " bytes failed");
+        }
+        rig->own_arena = true;
+    }
+    rig->arena = static_cast<char*>(arena);
+    rig->arena_bytes = pl.total;
+    rig->cams = pl.cams;
+    rig->grid = pl.grid;
+    rig->L = pl.L;
+    rig->L.base = rig->arena + pl.common;
+    rig->max_slots = desc->max_slots;
+    rig->host_staging = desc->host_staging;
+    rig->sil_words = pl.sil_words;
+    rig->npix = pl.npix;
+    rig->state.assign(desc->max_slots, 0);
+    rig->mc_ntri = reinterpret_cast<uint8_t*>(rig->arena);
+    rig->mc_edges = reinterpret_cast<uint8_t*>(rig->arena + align_up(256));
+    rig->viewpoints = reinterpret_cast<float*>(rig->arena + align_up(256) + align_up(256 * kMaxTriPerCell * 3));
+    std::vector<uint8_t> ntri(256), edges(256 * kMaxTriPerCell * 3, 0);
+    build_mc_table(ntri.data(), edges.data());
+    e = cudaMemcpy(rig->mc_ntri, ntri.data(), ntri.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(rig->mc_edges, edges.data(), edges.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (rig->own_arena) cudaFree(rig->arena);
+        delete rig;
+        return cuda_fail(nullptr, e, "uploading the MC table");
+    }
+    *out = rig;
+    return FVV_OK;
+}
+
+fvv_status fvv_destroy_rig(fvv_rig* rig) {
+    if (!rig) return FVV_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (rig->own_arena) {
+        cudaError_t f = cudaFree(rig->arena);
+        if (e == cudaSuccess) e = f;
+    }
+    delete rig;
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "fvv_destroy_rig");
+    return FVV_OK;
+}
+
+fvv_status fvv_upload_silhouettes(fvv_rig* rig, int slot, const uint8_t* const* masks, int masks_on_device,
+                                  void* stream) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    if (!check_slot(rig, slot)) return fail(rig, FVV_ERR_INVALID_ARG, "slot out of range");
+    if (!masks) return fail(rig, FVV_ERR_INVALID_ARG, "masks is NULL");
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint8_t* src[FVV_MAX_CAMS];
+    for (int n = 0; n < rig->cams.n; ++n) {
+        if (!masks[n]) return fail(rig, FVV_ERR_INVALID_ARG, "a mask pointer is NULL");
+        src[n] = masks[n];
+    }
+    if (!masks_on_device) {
+        if (!rig->host_staging) return fail(rig, FVV_ERR_INVALID_ARG, "host masks need a rig with host_staging");
+        uint8_t* stage = slot_ptr<uint8_t>(rig->L, slot, rig->L.mask_stage);
+        for (int n = 0; n < rig->cams.n; ++n) {
+            const Cam& c = rig->cams.c[n];
+            const cudaError_t e = cudaMemcpyAsync(stage + c.pix_off, masks[n], (size_t)c.W * c.H,
+                                                  cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(rig, e, "copying masks");
+            src[n] = stage + c.pix_off;
+        }
+    }
+    const cudaError_t e = launch_pack(rig->cams, rig->L, slot, src, st);
+    if (e != cudaSuccess) return cuda_fail(rig, e, "pack kernel");
+    rig->state[slot] = 1;
+    return FVV_OK;
+}
+
+static fvv_status make_slot_list(fvv_rig* rig, const int* slots, int n_slots, int need_state, SlotList& sl) {
+    if (!slots || n_slots < 1 || n_slots > FVV_MAX_BATCH || n_slots > rig->max_slots)
+        return fail(rig, FVV_ERR_INVALID_ARG, "slots must list 1..min(256, max_slots) slots");
+    std::vector<char> seen(rig->max_slots, 0);
+    sl.n = n_slots;
+    for (int i = 0; i < n_slots; ++i) {
+        if (!check_slot(rig, slots[i])) return fail(rig, FVV_ERR_INVALID_ARG, "slot out of range");
+        if (seen[slots[i]]) return fail(rig, FVV_ERR_INVALID_ARG, "slots must be distinct");
+        seen[slots[i]] = 1;
+        if (rig->state[slots[i]] < need_state) return fail(rig, FVV_ERR_NOT_READY, "slot not ready for this call");
+        sl.s[i] = slots[i];
+    }
+    return FVV_OK;
+}
+
+fvv_status fvv_reconstruct(fvv_rig* rig, const int* slots, int n_slots, void* stream) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    SlotList sl;
+    fvv_status s = make_slot_list(rig, slots, n_slots, 1, sl);
+    if (s != FVV_OK) return s;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    k_zero_info<<<sl.n, 32, 0, st>>>(rig->L, sl);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_coarse_carve(rig->cams, rig->grid, rig->L, sl, rig->sms, st);
+    if (e == cudaSuccess) e = launch_ccl(rig->grid, rig->L, sl, rig->sms, st);
+    if (e == cudaSuccess) e = launch_fine_carve(rig->cams, rig->grid, rig->L, sl, rig->sms, st);
+    if (e == cudaSuccess) e = launch_mesh(rig->cams, rig->grid, rig->L, sl, McTable{rig->mc_ntri, rig->mc_edges},
+                                          rig->sms, st);
+    if (e == cudaSuccess) e = launch_depth(rig->cams, rig->grid, rig->L, sl, rig->sms, align_up(rig->npix * 4), st);
+    if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_reconstruct launch");
+    for (int i = 0; i < sl.n; ++i) rig->state[sl.s[i]] = 2;
+    return FVV_OK;
+}
+
+fvv_status fvv_colour(fvv_rig* rig, const int* slots, int n_slots, const uint8_t* const* rgb, int rgb_on_device,
+                      const float* viewpoints, void* stream) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    SlotList sl;
+    fvv_status s = make_slot_list(rig, slots, n_slots, 2, sl);
+    if (s != FVV_OK) return s;
+    if (!rgb || !viewpoints) return fail(rig, FVV_ERR_INVALID_ARG, "rgb and viewpoints must not be NULL");
+    if (!rgb_on_device && !rig->host_staging) return fail(rig, FVV_ERR_INVALID_ARG, "host RGB needs host_staging");
+    for (int i = 0; i < 3 * n_slots; ++i)
+        if (!std::isfinite(viewpoints[i])) return fail(rig, FVV_ERR_INVALID_ARG, "viewpoints must be finite");
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(rig->viewpoints, viewpoints, sizeof(float) * 3 * n_slots, cudaMemcpyHostToDevice, st);
+    const int N = rig->cams.n;
+    for (int i = 0; i < n_slots && e == cudaSuccess; ++i) {
+        const uint8_t* ptrs[FVV_MAX_CAMS];
+        for (int n = 0; n < N; ++n) {
+            const uint8_t* src = rgb[(size_t)i * N + n];
+            if (!src) return fail(rig, FVV_ERR_INVALID_ARG, "an rgb pointer is NULL");
+            if (rgb_on_device) {
+                ptrs[n] = src;
+            } else {
+                const Cam& c = rig->cams.c[n];
+                uint8_t* dst = slot_ptr<uint8_t>(rig->L, sl.s[i], rig->L.rgb_stage) + 3 * c.pix_off;
+                e = cudaMemcpyAsync(dst, src, (size_t)3 * c.W * c.H, cudaMemcpyHostToDevice, st);
+                if (e != cudaSuccess) break;
+                ptrs[n] = dst;
+            }
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(slot_ptr<void>(rig->L, sl.s[i], rig->L.rgb_ptrs), ptrs, sizeof(void*) * N,
+                                cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = launch_colour(rig->cams, rig->grid, rig->L, sl, rig->viewpoints, rig->sms, st);
+    if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_colour");
+    return FVV_OK;
+}
+
+fvv_status fvv_get_counts(fvv_rig* rig, int slot, fvv_counts* out, void* stream) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    if (!check_slot(rig, slot) || !out) return fail(rig, FVV_ERR_INVALID_ARG, "bad slot or NULL counts");
+    if (rig->state[slot] < 2) return fail(rig, FVV_ERR_NOT_READY, "slot was not reconstructed");
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SlotInfo info;
+    cudaError_t e = cudaMemcpyAsync(&info, slot_ptr<SlotInfo>(rig->L, slot, rig->L.info), sizeof(info),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_get_counts");
+    std::memset(out, 0, sizeof(*out));
+    out->flags = info.flags;
+    out->n_components = info.n_roots;
+    out->n_rois = info.n_rois;
+    out->n_coarse_on = info.n_on;
+    out->n_fine_words = info.n_words;
+    out->n_verts = info.n_words ? info.n_verts : 0;
+    out->n_tris = info.n_words ? info.n_tris : 0;
+    out->tests_coarse = (long long)info.tests_coarse;
+    out->tests_fine = (long long)info.tests_fine;
+    out->tests_bisect = (long long)info.tests_bisect;
+    const unsigned cap = FVV_FLAG_ROOTS | FVV_FLAG_ROIS | FVV_FLAG_FINE | FVV_FLAG_VERTS | FVV_FLAG_TRIS | FVV_FLAG_LOOP;
+    if (info.flags & cap) return fail(rig, FVV_ERR_CAPACITY, "a capacity was exceeded (see flags)");
+    return FVV_OK;
+}
+
+fvv_status fvv_get_results(fvv_rig* rig, int slot, fvv_roi* rois, float* verts, uint32_t* tris, uint8_t* rgb,
+                           int32_t* cam, int dst_on_device, void* stream) {
+    fvv_counts c;
+    fvv_status s = fvv_get_counts(rig, slot, &c, stream);
+    if (s != FVV_OK) return s;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaSuccess;
+    if (rois && c.n_rois > 0) {
+        std::vector<DRoi> d(c.n_rois);
+        e = cudaMemcpyAsync(d.data(), slot_ptr<DRoi>(rig->L, slot, rig->L.rois), sizeof(DRoi) * c.n_rois,
+                            cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(rig, e, "reading ROIs");
+        std::vector<fvv_roi> h(c.n_rois);
+        for (int k = 0; k < c.n_rois; ++k) {
+            fvv_roi& r = h[k];
+            for (int a = 0; a < 3; ++a) {
+                r.cmin[a] = d[k].cmin[a]; r.cmax[a] = d[k].cmax[a];
+                r.gmin[a] = d[k].gmin[a]; r.gmax[a] = d[k].gmax[a];
+                r.fdim[a] = d[k].fdim[a]; r.forigin[a] = d[k].fo[a];
+            }
+            r.count = d[k].count;
+            r.label = k + 1;
+            r.vert_offset = d[k].vert_off;
+            r.tri_offset = d[k].tri_off;
+            r.n_verts = (k + 1 < c.n_rois ? (long long)d[k + 1].vert_off : c.n_verts) - r.vert_offset;
+            r.n_tris = (k + 1 < c.n_rois ? (long long)d[k + 1].tri_off : c.n_tris) - r.tri_offset;
+        }
+        if (dst_on_device) e = cudaMemcpyAsync(rois, h.data(), sizeof(fvv_roi) * c.n_rois, cudaMemcpyHostToDevice, st);
+        else std::memcpy(rois, h.data(), sizeof(fvv_roi) * c.n_rois);
+    }
+    const Layout& L = rig->L;
+    if (e == cudaSuccess && verts && c.n_verts)
+        e = cudaMemcpyAsync(verts, slot_ptr<float>(L, slot, L.verts), 12 * (size_t)c.n_verts, kind, st);
+    if (e == cudaSuccess && tris && c.n_tris)
+        e = cudaMemcpyAsync(tris, slot_ptr<uint32_t>(L, slot, L.tris), 12 * (size_t)c.n_tris, kind, st);
+    if (e == cudaSuccess && rgb && c.n_verts)
+        e = cudaMemcpyAsync(rgb, slot_ptr<uint8_t>(L, slot, L.vrgb), 3 * (size_t)c.n_verts, kind, st);
+    if (e == cudaSuccess && cam && c.n_verts)
+        e = cudaMemcpyAsync(cam, slot_ptr<int32_t>(L, slot, L.vcam), 4 * (size_t)c.n_verts, kind, st);
+    if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_get_results");
+    return FVV_OK;
+}
+
+fvv_status fvv_debug_bytes(fvv_rig* rig, int slot, int what, size_t* bytes) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    if (!check_slot(rig, slot) || !bytes) return fail(rig, FVV_ERR_INVALID_ARG, "bad slot or NULL bytes");
+    const Grid& g = rig->grid;
+    switch (what) {
+        case FVV_DEBUG_SIL_BITS: *bytes = rig->sil_words * 4; return FVV_OK;
+        case FVV_DEBUG_COARSE_BITS: *bytes = (size_t)g.nz * g.ny * g.nxw * 4; return FVV_OK;
+        case FVV_DEBUG_LABELS: *bytes = (size_t)g.nz * g.ny * g.nx * 4; return FVV_OK;
+        case FVV_DEBUG_DEPTH: *bytes = rig->npix * 4; return FVV_OK;
+        case FVV_DEBUG_FINE_BITS: {
+            SlotInfo info;
+            const cudaError_t e = cudaMemcpy(&info, slot_ptr<SlotInfo>(rig->L, slot, rig->L.info), sizeof(info),
+                                             cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_debug_bytes");
+            *bytes = (size_t)info.n_words * 4;
+            return FVV_OK;
+        }
+    }
+    return fail(rig, FVV_ERR_INVALID_ARG, "unknown debug view");
+}
+
+fvv_status fvv_get_debug(fvv_rig* rig, int slot, int what, void* dst, size_t bytes, void* stream) {
+    size_t need = 0;
+    fvv_status s = fvv_debug_bytes(rig, slot, what, &need);
+    if (s != FVV_OK) return s;
+    if (!dst || bytes < need) return fail(rig, FVV_ERR_INVALID_ARG, "debug buffer too small");
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Layout& L = rig->L;
+    cudaError_t e = cudaSuccess;
+    switch (what) {
+        case FVV_DEBUG_SIL_BITS:
+            e = cudaMemcpyAsync(dst, slot_ptr<void>(L, slot, L.sil), need, cudaMemcpyDeviceToDevice, st);
+            break;
+        case FVV_DEBUG_COARSE_BITS:
+            e = cudaMemcpyAsync(dst, slot_ptr<void>(L, slot, L.coarse), need, cudaMemcpyDeviceToDevice, st);
+            break;
+        case FVV_DEBUG_FINE_BITS:
+            if (need) e = cudaMemcpyAsync(dst, slot_ptr<void>(L, slot, L.fine), need, cudaMemcpyDeviceToDevice, st);
+            break;
+        case FVV_DEBUG_LABELS:
+            e = cudaMemsetAsync(dst, 0, need, st);
+            if (e == cudaSuccess) e = launch_debug_labels(rig->grid, L, slot, static_cast<int32_t*>(dst), st);
+            break;
+        case FVV_DEBUG_DEPTH:
+            e = launch_debug_depth(rig->cams, L, slot, static_cast<float*>(dst), rig->npix, st);
+            break;
+    }
+    if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_get_debug");
+    return FVV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,148 @@
+// fvv_internal.h -- device-side data layout and kernel launchers of libfvv.
+//
+// Everything a kernel needs about the rig travels by value in kernel
+// parameters (cameras, grid, per-slot arena layout); everything per frame
+// lives in the slot's part of the arena.  Launchers enqueue on a stream and
+// never synchronise.
+#pragma once
+
+#include <algorithm>
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fvv.h"
+
+namespace fvv {
+
+constexpr int kMaxComponents = 8192;  // raw components sortable by one block
+constexpr int kMaxRois = 4096;
+constexpr int kChunk = 256;           // fine words per scan chunk (= block size)
+constexpr uint32_t kEmptyDepth = 0xFFFFFFFFu;  // depth-buffer bits meaning +inf
+constexpr int kMaxTriPerCell = 12;
+
+struct Cam {
+    float P[12];
+    float C[3];
+    int W, H, Wq;        // Wq = 32-bit words per silhouette row
+    uint32_t bit_off;    // first silhouette word of this camera in a slot
+    uint64_t pix_off;    // first pixel of this camera in per-slot pixel arrays
+};
+
+struct CamSet {
+    int n;
+    int oob;             // FVV_OOB_*
+    Cam c[FVV_MAX_CAMS];
+};
+
+struct Grid {
+    float o[3];          // volume origin (vol_min)
+    float sc, sf;        // coarse and fine steps
+    int nx, ny, nz, nxw; // coarse dims, words per coarse row
+    long long coarse_um, fine_um;
+    int steps;           // bisection steps
+    int t_np, t_nb;
+    float t_v;
+    int max_comp, max_rois;
+    uint32_t max_fine_words, max_chunks;
+    uint32_t max_verts, max_tris;
+};
+
+// Per-slot device bookkeeping (zeroed at the start of each reconstruction).
+struct SlotInfo {
+    unsigned int flags;
+    int n_roots;
+    int n_rois;
+    uint32_t n_words;           // fine words in use
+    uint32_t n_chunks;
+    uint32_t n_verts, n_tris;
+    uint32_t n_on;
+    unsigned long long tests_coarse, tests_fine, tests_bisect;
+};
+
+// Device ROI record (one per kept component).
+struct DRoi {
+    int cmin[3], cmax[3], gmin[3], gmax[3], fdim[3];
+    float fo[3];
+    int count;
+    int nxw;                    // words per padded fine row
+    uint32_t word_off;          // first fine word of this ROI in the slot
+    uint32_t n_words;
+    uint32_t vert_off, tri_off; // filled after the scans (for fvv_roi)
+};
+
+// Offsets (bytes) of each per-slot array from the slot base.  All 256-aligned.
+struct Layout {
+    char* base;                 // arena + slots region
+    size_t stride;              // bytes per slot
+    size_t info;                // SlotInfo
+    size_t sil;                 // uint32 silhouette bits
+    size_t coarse;              // uint32 coarse bits (nz*ny*nxw)
+    size_t parent;              // int32 union-find parents, nx*ny*nz
+    size_t roots;               // int32 root linear indices, max_comp
+    size_t cstat;               // int32 per component: count, min xyz, max xyz (7 each)
+    size_t rois;                // DRoi, max_rois
+    size_t roi_label;           // int32 label per sorted component (0 = removed)
+    size_t fine;                // uint32 fine bits, max_fine_words
+    size_t emask;               // uint32 x3 bipolar-edge masks per fine word
+    size_t vcnt, tcnt;          // uint32 per fine word
+    size_t vpre, tpre;          // uint32 exclusive prefixes per fine word
+    size_t cpart;               // uint32 x2 per chunk: vertex and triangle sums
+    size_t vrec;                // uint64 vertex records, max_verts
+    size_t verts;               // float x3, max_verts
+    size_t tris;                // uint32 x3, max_tris
+    size_t vrgb;                // uint8 x3, max_verts
+    size_t vcam;                // int32, max_verts
+    size_t depth;               // uint32 per pixel of all cameras
+    size_t mask_stage;          // uint8 per pixel (host uploads), or 0
+    size_t rgb_stage;           // uint8 x3 per pixel (host uploads), or 0
+    size_t rgb_ptrs;            // const uint8_t* per camera: colour sources
+};
+
+template <typename T>
+__host__ __device__ inline T* slot_ptr(const Layout& L, int slot, size_t off) {
+    return reinterpret_cast<T*>(L.base + (size_t)slot * L.stride + off);
+}
+
+struct SlotList {
+    int n;
+    int s[FVV_MAX_BATCH];
+};
+
+// Marching-cubes table in device memory.
+struct McTable {
+    const uint8_t* ntri;        // [256]
+    const uint8_t* edges;       // [256][12][3]
+};
+
+// Blocks per slot for a grid-stride kernel: enough for the work, at most
+// about 8 blocks per SM over the whole batch.
+inline int grid_x(int sms, int n_slots, long long work_items, int per_block) {
+    const long long want = (work_items + per_block - 1) / per_block;
+    const long long cap = std::max(1LL, (long long)sms * 8 / std::max(1, n_slots));
+    return (int)std::max(1LL, std::min(want, cap));
+}
+
+// Builds the 256-case table from the face rule (host).
+void build_mc_table(uint8_t ntri[256], uint8_t edges[256 * kMaxTriPerCell * 3]);
+
+// ---- launchers (all enqueue on `st`)
+cudaError_t launch_pack(const CamSet& cams, const Layout& L, int slot, const uint8_t* const* src,
+                        cudaStream_t st);
+cudaError_t launch_coarse_carve(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
+                                int sms, cudaStream_t st);
+cudaError_t launch_ccl(const Grid& g, const Layout& L, const SlotList& sl, int sms, cudaStream_t st);
+cudaError_t launch_fine_carve(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
+                              int sms, cudaStream_t st);
+cudaError_t launch_mesh(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
+                        const McTable& mc, int sms, cudaStream_t st);
+cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
+                         int sms, size_t depth_bytes, cudaStream_t st);
+cudaError_t launch_colour(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
+                          const float* viewpoints, int sms, cudaStream_t st);
+cudaError_t launch_debug_labels(const Grid& g, const Layout& L, int slot, int32_t* dst, cudaStream_t st);
+cudaError_t launch_debug_depth(const CamSet& cams, const Layout& L, int slot, float* dst, size_t npix,
+                               cudaStream_t st);
+
+}  // namespace fvv

@@ -1,0 +1,356 @@
+// kernels_ccl.cu -- Sec. II-B-2: 26-connected component labelling of the
+// coarse hull, the minimum 3D box of each component, the noise filter of
+// Eq. (1) and the 3D ROI table.
+//
+// Union-find over the occupied voxels with atomics (Playne & Hawick style):
+// parents live in a dense int32 array indexed by the linear voxel index and
+// are only ever touched at occupied voxels (the coarse carve initialised
+// them), so nothing is cleared per frame.  A union links the larger root
+// below the smaller with atomicMin, so every root is the smallest linear
+// index of its component; sorting the roots therefore numbers components in
+// order of their smallest index, the canonical order of the oracle.  The
+// paper's block-local-then-global scheme is replaced by this lock-free
+// union, which needs no second pass over block borders.
+#include "fvv_device.cuh"
+
+namespace fvv {
+namespace {
+
+// Every thread gets a budget of find/union steps for the whole launch; valid
+// input never comes near it, and a thread that exhausts it stops, sets
+// FVV_FLAG_LOOP and returns, so no launch can run unbounded.
+constexpr int kStepBudget = 1 << 22;
+
+__device__ __forceinline__ int find_root(const int* parent, int x, int& budget) {
+    while (budget > 0) {
+        --budget;
+        const int p = __ldcg(parent + x);
+        if (p == x || p < 0) return x;
+        x = p;
+    }
+    return x;
+}
+
+__device__ __forceinline__ void unite(int* parent, int a, int b, int& budget) {
+    while (budget > 0) {
+        a = find_root(parent, a, budget);
+        b = find_root(parent, b, budget);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicMin(parent + a, b);
+        if (old == a) return;
+        a = old;
+    }
+}
+
+__device__ __forceinline__ bool coarse_on(const uint32_t* bits, const Grid& g, int x, int y, int z) {
+    if (x < 0 || y < 0 || z < 0 || x >= g.nx || y >= g.ny || z >= g.nz) return false;
+    return (__ldg(bits + ((size_t)z * g.ny + y) * g.nxw + (x >> 5)) >> (x & 31)) & 1u;
+}
+
+// Union of every occupied voxel with its 13 occupied neighbours that come
+// before it in linear order (the other 13 see it in turn).
+__global__ void __launch_bounds__(256) k_union(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
+                                               const __grid_constant__ SlotList sl) {
+    const int slot = sl.s[blockIdx.y];
+    const uint32_t* bits = slot_ptr<uint32_t>(L, slot, L.coarse);
+    int* parent = slot_ptr<int>(L, slot, L.parent);
+    const uint32_t nwords = (uint32_t)g.nz * g.ny * g.nxw;
+    int budget = kStepBudget;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords && budget > 0; w += gridDim.x * blockDim.x) {
+        uint32_t word = __ldg(bits + w);
+        if (!word) continue;
+        const uint32_t row = w / (uint32_t)g.nxw;
+        const int wx = (int)(w - row * g.nxw);
+        const int y = (int)(row % (uint32_t)g.ny), z = (int)(row / (uint32_t)g.ny);
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            const int x = wx * 32 + b;
+            const int Lin = (int)row * g.nx + x;
+            for (int dz = -1; dz <= 0; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (dz == 0 && (dy > 0 || (dy == 0 && dx >= 0))) continue;
+                        if (!coarse_on(bits, g, x + dx, y + dy, z + dz)) continue;
+                        unite(parent, Lin, ((z + dz) * g.ny + (y + dy)) * g.nx + (x + dx), budget);
+                    }
+        }
+    }
+    if (budget <= 0) atomicOr(&slot_ptr<SlotInfo>(L, slot, L.info)->flags, (unsigned)FVV_FLAG_LOOP);
+}
+
+// Point every voxel at its root and list the roots (unordered).
+__global__ void __launch_bounds__(256) k_compress(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
+                                                  const __grid_constant__ SlotList sl) {
+    const int slot = sl.s[blockIdx.y];
+    const uint32_t* bits = slot_ptr<uint32_t>(L, slot, L.coarse);
+    int* parent = slot_ptr<int>(L, slot, L.parent);
+    int* roots = slot_ptr<int>(L, slot, L.roots);
+    SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const uint32_t nwords = (uint32_t)g.nz * g.ny * g.nxw;
+    int budget = kStepBudget;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords && budget > 0; w += gridDim.x * blockDim.x) {
+        uint32_t word = __ldg(bits + w);
+        if (!word) continue;
+        const uint32_t row = w / (uint32_t)g.nxw;
+        const int wx = (int)(w - row * g.nxw);
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            const int Lin = (int)row * g.nx + wx * 32 + b;
+            const int r = find_root(parent, Lin, budget);
+            if (r == Lin) {
+                const int k = atomicAdd(&info->n_roots, 1);
+                if (k < g.max_comp) roots[k] = Lin;
+            } else {
+                parent[Lin] = r;
+            }
+        }
+    }
+    if (budget <= 0) atomicOr(&info->flags, (unsigned)FVV_FLAG_LOOP);
+}
+
+// One block per slot: sort the roots (bitonic, in shared memory) so that
+// component i is the one with the i-th smallest least index; tag each root's
+// parent entry with -(i+1); reset the per-component statistics.
+__global__ void __launch_bounds__(1024) k_sort_roots(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
+                                                     const __grid_constant__ SlotList sl) {
+    __shared__ int key[kMaxComponents];
+    const int slot = sl.s[blockIdx.x];
+    SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    int* roots = slot_ptr<int>(L, slot, L.roots);
+    int* parent = slot_ptr<int>(L, slot, L.parent);
+    int* cstat = slot_ptr<int>(L, slot, L.cstat);
+    int n = info->n_roots;
+    if (n > g.max_comp) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            info->flags |= FVV_FLAG_ROOTS;
+            info->n_roots = 0;
+        }
+        return;
+    }
+    int m = 1;
+    while (m < n) m <<= 1;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) key[i] = i < n ? roots[i] : 0x7FFFFFFF;
+    __syncthreads();
+    for (int k = 2; k <= m; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                const int p = i ^ j;
+                if (p > i) {
+                    const bool up = (i & k) == 0;
+                    const int a = key[i], b = key[p];
+                    if ((a > b) == up) {
+                        key[i] = b;
+                        key[p] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        roots[i] = key[i];
+        parent[key[i]] = -(i + 1);
+        int* s = cstat + 7 * i;
+        s[0] = 0;
+        s[1] = s[2] = s[3] = 0x7FFFFFFF;
+        s[4] = s[5] = s[6] = -1;
+    }
+}
+
+__device__ __forceinline__ void flush_stats(int* s, int cnt, const int* lo, const int* hi) {
+    atomicAdd(s, cnt);
+    for (int a = 0; a < 3; ++a) {
+        atomicMin(s + 1 + a, lo[a]);
+        atomicMax(s + 4 + a, hi[a]);
+    }
+}
+
+// Voxel count and inclusive box of every component (Sec. II-B-2 takes the
+// smallest box holding each labelled set after labelling).  Runs of
+// voxels of one component in a word are merged before the atomics.
+__global__ void __launch_bounds__(256) k_stats(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
+                                               const __grid_constant__ SlotList sl) {
+    const int slot = sl.s[blockIdx.y];
+    const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    if (info->n_roots <= 0) return;
+    const uint32_t* bits = slot_ptr<uint32_t>(L, slot, L.coarse);
+    const int* parent = slot_ptr<int>(L, slot, L.parent);
+    int* cstat = slot_ptr<int>(L, slot, L.cstat);
+    const uint32_t nwords = (uint32_t)g.nz * g.ny * g.nxw;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) {
+        uint32_t word = __ldg(bits + w);
+        if (!word) continue;
+        const uint32_t row = w / (uint32_t)g.nxw;
+        const int wx = (int)(w - row * g.nxw);
+        const int y = (int)(row % (uint32_t)g.ny), z = (int)(row / (uint32_t)g.ny);
+        int cur = -1, cnt = 0, lo[3], hi[3];
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            const int x = wx * 32 + b;
+            const int Lin = (int)row * g.nx + x;
+            const int r = parent[Lin];
+            const int t = r < 0 ? r : parent[r];
+            if (t >= 0) continue;  // roots were not tagged (capacity overflow)
+            const int idx = -t - 1;
+            if (idx != cur) {
+                if (cur >= 0) flush_stats(cstat + 7 * cur, cnt, lo, hi);
+                cur = idx;
+                cnt = 0;
+                lo[0] = lo[1] = lo[2] = 0x7FFFFFFF;
+                hi[0] = hi[1] = hi[2] = -1;
+            }
+            ++cnt;
+            lo[0] = min(lo[0], x); hi[0] = max(hi[0], x);
+            lo[1] = min(lo[1], y); hi[1] = max(hi[1], y);
+            lo[2] = min(lo[2], z); hi[2] = max(hi[2], z);
+        }
+        if (cur >= 0) flush_stats(cstat + 7 * cur, cnt, lo, hi);
+    }
+}
+
+// One block per slot: Eq. (1) as its prose states it (keep iff
+// t_np <= count <= t_nb), canonical labels 1..K in component order, and the
+// ROI of each kept component: its box grown by one coarse voxel per side and
+// clamped (Sec. II-B-3 treats it as a volume of its own), covered by whole
+// fine voxels counted in integer micrometres, with the fine grid's origin and
+// word layout.  Capacity overflows set a flag and leave the slot with no ROIs.
+__global__ void __launch_bounds__(1024) k_filter(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
+                                                 const __grid_constant__ SlotList sl) {
+    __shared__ uint32_t sh[33];
+    __shared__ int s_fail;
+    const int slot = sl.s[blockIdx.x];
+    SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const int n = info->n_roots;
+    const int* cstat = slot_ptr<int>(L, slot, L.cstat);
+    int* label = slot_ptr<int>(L, slot, L.roi_label);
+    DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
+    if (threadIdx.x == 0) s_fail = 0;
+    // pass 1: labels; components are processed in tiles of blockDim
+    uint32_t base = 0;
+    for (int t0 = 0; t0 < n; t0 += blockDim.x) {
+        const int i = t0 + threadIdx.x;
+        uint32_t keep = 0;
+        if (i < n) {
+            const int c = cstat[7 * i];
+            keep = (c >= g.t_np && c <= g.t_nb) ? 1u : 0u;
+        }
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(keep, sh, tot);
+        if (i < n) label[i] = keep ? (int)(base + ex + 1) : 0;
+        if (keep && base + ex < (uint32_t)g.max_rois) {
+            DRoi r;
+            const int* s = cstat + 7 * i;
+            const int dims[3] = {g.nx, g.ny, g.nz};
+            bool ok = true;
+            for (int a = 0; a < 3; ++a) {
+                r.cmin[a] = s[1 + a];
+                r.cmax[a] = s[4 + a];
+                r.gmin[a] = max(r.cmin[a] - 1, 0);
+                r.gmax[a] = min(r.cmax[a] + 1, dims[a] - 1);
+                const long long span = (long long)(r.gmax[a] - r.gmin[a] + 1) * g.coarse_um;
+                const long long fd = (span + g.fine_um - 1) / g.fine_um;
+                ok &= fd + 2 <= 32767;
+                r.fdim[a] = (int)min(fd, 32765LL);
+                r.fo[a] = fadd(g.o[a], fmul((float)r.gmin[a], g.sc));
+            }
+            r.count = s[0];
+            r.nxw = (r.fdim[0] + 2 + 31) / 32;
+            const unsigned long long nw = (unsigned long long)r.nxw * (r.fdim[1] + 2) * (r.fdim[2] + 2);
+            ok &= nw <= g.max_fine_words;
+            r.n_words = ok ? (uint32_t)nw : 0u;
+            r.word_off = 0;
+            r.vert_off = r.tri_off = 0;
+            rois[base + ex] = r;
+            if (!ok) s_fail = 1;
+        }
+        base += tot;
+    }
+    __syncthreads();
+    const int K = (int)base;
+    if (K > g.max_rois || s_fail) {
+        if (threadIdx.x == 0) {
+            info->flags |= (K > g.max_rois ? FVV_FLAG_ROIS : 0u) | (s_fail ? FVV_FLAG_FINE : 0u);
+            info->n_rois = 0;
+            info->n_words = 0;
+        }
+        return;
+    }
+    // pass 2: first fine word of each ROI (exclusive prefix of n_words)
+    unsigned long long wbase = 0;
+    for (int t0 = 0; t0 < K; t0 += blockDim.x) {
+        const int i = t0 + threadIdx.x;
+        const uint32_t nw = i < K ? rois[i].n_words : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(nw, sh, tot);
+        if (i < K && wbase + ex <= 0xFFFFFFFFull) rois[i].word_off = (uint32_t)(wbase + ex);
+        wbase += tot;
+    }
+    if (threadIdx.x == 0) {
+        if (wbase > g.max_fine_words) {
+            info->flags |= FVV_FLAG_FINE;
+            info->n_rois = 0;
+            info->n_words = 0;
+        } else {
+            info->n_rois = K;
+            info->n_words = (uint32_t)wbase;
+            info->n_chunks = (uint32_t)((wbase + kChunk - 1) / kChunk);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_ccl(const Grid& g, const Layout& L, const SlotList& sl, int sms, cudaStream_t st) {
+    const long long words = (long long)g.nz * g.ny * g.nxw;
+    const int gx = grid_x(sms, sl.n, words, 256);
+    k_union<<<dim3(gx, sl.n), 256, 0, st>>>(g, L, sl);
+    k_compress<<<dim3(gx, sl.n), 256, 0, st>>>(g, L, sl);
+    k_sort_roots<<<sl.n, 1024, 0, st>>>(g, L, sl);
+    k_stats<<<dim3(gx, sl.n), 256, 0, st>>>(g, L, sl);
+    k_filter<<<sl.n, 1024, 0, st>>>(g, L, sl);
+    return cudaGetLastError();
+}
+
+// Canonical labels of every coarse voxel, for the parity tests; dst must be
+// zeroed (nz*ny*nx int32).
+namespace {
+__global__ void k_debug_labels(const __grid_constant__ Grid g, const __grid_constant__ Layout L, int slot,
+                               int32_t* dst) {
+    const uint32_t* bits = slot_ptr<uint32_t>(L, slot, L.coarse);
+    const int* parent = slot_ptr<int>(L, slot, L.parent);
+    const int* label = slot_ptr<int>(L, slot, L.roi_label);
+    const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    if (info->n_roots <= 0) return;
+    const uint32_t nwords = (uint32_t)g.nz * g.ny * g.nxw;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) {
+        uint32_t word = bits[w];
+        const uint32_t row = w / (uint32_t)g.nxw;
+        const int wx = (int)(w - row * g.nxw);
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            const int Lin = (int)row * g.nx + wx * 32 + b;
+            const int r = parent[Lin];
+            const int t = r < 0 ? r : parent[r];
+            if (t < 0) dst[Lin] = label[-t - 1];
+        }
+    }
+}
+}  // namespace
+
+cudaError_t launch_debug_labels(const Grid& g, const Layout& L, int slot, int32_t* dst, cudaStream_t st) {
+    const long long words = (long long)g.nz * g.ny * g.nxw;
+    k_debug_labels<<<(unsigned)std::min<long long>((words + 255) / 256, 4096), 256, 0, st>>>(g, L, slot, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace fvv

@@ -1,0 +1,457 @@
+// kernels_mc.cu -- Sec. II-C: surface polygonisation of every fine grid.
+//
+// Each fine grid is padded by one unoccupied sample per side and stored as
+// rows of 32-bit words, so one thread owns 32 cells (or 32 samples) and works
+// with word-wide bit operations:
+//   count     bipolar-edge masks (x: w ^ w>>1, y: w ^ w(y+1), z: w ^ w(z+1)),
+//             vertices = popcounts, triangles = table counts of mixed cells;
+//             per-256-word chunk sums.
+//   scan      one block per frame: exclusive prefix of the chunk sums.
+//   vertices  exclusive prefix per word (block scan + chunk base) and one
+//             record per bipolar edge, in edge-key order (3*Lpad + axis).
+//   bisect    one thread per vertex: fixed-count bisection of its edge
+//             against the silhouettes (the exact intersection of Eqs. (2)-(3)
+//             read as the hull crossing on the edge).
+//   triangles table triangles of each mixed cell, vertex ids = word prefix +
+//             rank of the edge inside its word.
+// Vertex and triangle order is therefore (ROI, key) and (ROI, cell, table
+// order): independent of scheduling, identical to a serial scan.
+#include "fvv_device.cuh"
+
+namespace fvv {
+
+// ------------------------------------------------------------ MC table (host)
+//
+// Corners are numbered x + 2y + 4z.  Cube edge e runs along axis e/4 from its
+// lower corner, whose other two coordinates, in increasing axis order, are
+// (e & 1, e >> 1 & 1).  On every face the bipolar edges are joined by
+// segments (two bipolar edges: one segment; four, i.e. two diagonal ON
+// corners: one segment around each ON corner, keeping ON corners apart), each
+// directed so that the ON side is on its right seen from outside the cube;
+// chaining them gives loops whose normals point from ON to OFF.  Loops are
+// taken in order of their smallest edge, walked from it, and fanned from the
+// first vertex that shares no face with a vertex it is not adjacent to.
+namespace {
+
+void edge_ends(int e, int& lo, int& hi) {
+    const int axis = e >> 2;
+    int other[2], k = 0;
+    for (int b = 0; b < 3; ++b)
+        if (b != axis) other[k++] = b;
+    lo = ((e & 1) << other[0]) | (((e >> 1) & 1) << other[1]);
+    hi = lo | (1 << axis);
+}
+
+int edge_of(int c0, int c1) {
+    for (int e = 0; e < 12; ++e) {
+        int lo, hi;
+        edge_ends(e, lo, hi);
+        if ((lo == c0 && hi == c1) || (lo == c1 && hi == c0)) return e;
+    }
+    return -1;
+}
+
+}  // namespace
+
+void build_mc_table(uint8_t ntri[256], uint8_t edges[256 * kMaxTriPerCell * 3]) {
+    // face membership of every edge, and each face's corner cycle
+    int face_mask[12] = {0};
+    int cyc[6][4];
+    for (int f = 0; f < 6; ++f) {
+        const int b = f >> 1, t = f & 1;
+        const int p = b == 0 ? 1 : 0, q = b == 2 ? 1 : 2;
+        const int uv[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+        for (int i = 0; i < 4; ++i) cyc[f][i] = (t << b) | (uv[i][0] << p) | (uv[i][1] << q);
+        for (int i = 0; i < 4; ++i) face_mask[edge_of(cyc[f][i], cyc[f][(i + 1) & 3])] |= 1 << f;
+    }
+    for (int cs = 0; cs < 256; ++cs) {
+        int nxt[12];
+        for (int e = 0; e < 12; ++e) nxt[e] = -1;
+        for (int f = 0; f < 6; ++f) {
+            const int b = f >> 1, t = f & 1;
+            const int hand = b == 1 ? -1 : 1;       // (p, q, b) right-handed?
+            const int side = t ? 1 : -1;            // outward normal along b
+            const int uv[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+            int s[4], fe[4], nb = 0;
+            for (int i = 0; i < 4; ++i) s[i] = (cs >> cyc[f][i]) & 1;
+            for (int i = 0; i < 4; ++i)
+                if (s[i] != s[(i + 1) & 3]) fe[nb++] = i;  // face edge i joins corners i, i+1
+            int seg[2][3], ns = 0;                          // (face edge, face edge, ON corner)
+            if (nb == 2) {
+                int on = 0;
+                while (!s[on]) ++on;
+                seg[0][0] = fe[0]; seg[0][1] = fe[1]; seg[0][2] = on;
+                ns = 1;
+            } else if (nb == 4) {
+                for (int i = 0; i < 4; ++i)
+                    if (s[i]) {
+                        seg[ns][0] = (i + 3) & 3; seg[ns][1] = i; seg[ns][2] = i;
+                        ++ns;
+                    }
+            }
+            for (int k = 0; k < ns; ++k) {
+                const int i0 = seg[k][0], i1 = seg[k][1], a = seg[k][2];
+                // doubled face-plane coordinates of the two midpoints and the ON corner
+                const int P[2] = {uv[i0][0] + uv[(i0 + 1) & 3][0], uv[i0][1] + uv[(i0 + 1) & 3][1]};
+                const int Q[2] = {uv[i1][0] + uv[(i1 + 1) & 3][0], uv[i1][1] + uv[(i1 + 1) & 3][1]};
+                const int A[2] = {2 * uv[a][0], 2 * uv[a][1]};
+                const int cr = (Q[0] - P[0]) * (A[1] - P[1]) - (Q[1] - P[1]) * (A[0] - P[0]);
+                const int ep = edge_of(cyc[f][i0], cyc[f][(i0 + 1) & 3]);
+                const int eq = edge_of(cyc[f][i1], cyc[f][(i1 + 1) & 3]);
+                if (cr * hand * side < 0) nxt[ep] = eq;
+                else nxt[eq] = ep;
+            }
+        }
+        int done = 0, nt = 0;
+        for (int e0 = 0; e0 < 12; ++e0) {
+            if (nxt[e0] < 0 || (done >> e0 & 1)) continue;
+            int loop[12], n = 0;
+            for (int e = e0; !(done >> e & 1); e = nxt[e]) {
+                done |= 1 << e;
+                loop[n++] = e;
+            }
+            int apex = 0;
+            for (int i = 0; i < n; ++i) {
+                bool ok = true;
+                for (int d = 2; d + 1 < n && ok; ++d)
+                    if (face_mask[loop[i]] & face_mask[loop[(i + d) % n]]) ok = false;
+                if (ok) {
+                    apex = i;
+                    break;
+                }
+            }
+            for (int d = 1; d + 1 < n; ++d) {
+                uint8_t* o = edges + ((size_t)cs * kMaxTriPerCell + nt) * 3;
+                o[0] = (uint8_t)loop[apex];
+                o[1] = (uint8_t)loop[(apex + d) % n];
+                o[2] = (uint8_t)loop[(apex + d + 1) % n];
+                ++nt;
+            }
+        }
+        ntri[cs] = (uint8_t)nt;
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+namespace {
+
+// The 8 words around fine word w (rows y, y+1 and planes z, z+1; this word
+// and the next in x) as "samples at xp" (c*) and "samples at xp+1" (s*),
+// indexed by corner bits (dy + 2dz).
+struct Nbhd {
+    uint32_t w[4];   // sample xp, corner dy + 2 dz
+    uint32_t s[4];   // sample xp + 1
+};
+
+__device__ __forceinline__ void load_nbhd(const uint32_t* fine, const DRoi& r, uint32_t w, int wx, int yp, int zp,
+                                          Nbhd& n) {
+    const uint32_t rs = (uint32_t)r.nxw, ps = (uint32_t)r.nxw * (uint32_t)(r.fdim[1] + 2);
+    const bool hx = wx + 1 < r.nxw, hy = yp + 1 < r.fdim[1] + 2, hz = zp + 1 < r.fdim[2] + 2;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool dy = k & 1, dz = k >> 1;
+        const bool ok = (!dy || hy) && (!dz || hz);
+        const uint32_t base = w + (dy ? rs : 0u) + (dz ? ps : 0u);
+        const uint32_t a = ok ? __ldg(fine + base) : 0u;
+        const uint32_t b = (ok && hx) ? __ldg(fine + base + 1) : 0u;
+        n.w[k] = a;
+        n.s[k] = (a >> 1) | (b << 31);
+    }
+}
+
+__device__ __forceinline__ uint32_t mixed_cells(const Nbhd& n) {
+    const uint32_t a = n.w[0];
+    return (a ^ n.s[0]) | (a ^ n.w[1]) | (a ^ n.s[1]) | (a ^ n.w[2]) | (a ^ n.s[2]) | (a ^ n.w[3]) | (a ^ n.s[3]);
+}
+
+__device__ __forceinline__ int cell_case(const Nbhd& n, int b) {
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        c |= (int)((n.w[k] >> b) & 1u) << (2 * k);
+        c |= (int)((n.s[k] >> b) & 1u) << (2 * k + 1);
+    }
+    return c;
+}
+
+__device__ __forceinline__ int roi_of_word(const DRoi* rois, int n, uint32_t w) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (rois[mid].word_off <= w) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct WordPos {
+    int k, wx, yp, zp;
+};
+
+__device__ __forceinline__ WordPos word_pos(const DRoi* rois, int nrois, uint32_t w) {
+    WordPos p;
+    p.k = roi_of_word(rois, nrois, w);
+    const DRoi& r = rois[p.k];
+    const uint32_t lw = w - r.word_off;
+    const uint32_t row = lw / (uint32_t)r.nxw;
+    p.wx = (int)(lw - row * (uint32_t)r.nxw);
+    p.yp = (int)(row % (uint32_t)(r.fdim[1] + 2));
+    p.zp = (int)(row / (uint32_t)(r.fdim[1] + 2));
+    return p;
+}
+
+__global__ void __launch_bounds__(kChunk) k_mc_count(const __grid_constant__ Layout L, const __grid_constant__ SlotList sl,
+                                                     const __grid_constant__ McTable mc) {
+    __shared__ uint8_t s_ntri[256];
+    __shared__ uint32_t sh[32];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_ntri[i] = mc.ntri[i];
+    __syncthreads();
+    const int slot = sl.s[blockIdx.y];
+    const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const uint32_t nwords = info->n_words, nchunks = info->n_chunks;
+    const int nrois = info->n_rois;
+    const DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
+    const uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
+    uint32_t* vcnt = slot_ptr<uint32_t>(L, slot, L.vcnt);
+    uint32_t* tcnt = slot_ptr<uint32_t>(L, slot, L.tcnt);
+    uint32_t* emask = slot_ptr<uint32_t>(L, slot, L.emask);
+    uint32_t* cpart = slot_ptr<uint32_t>(L, slot, L.cpart);
+    for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const uint32_t w = c * kChunk + threadIdx.x;
+        uint32_t vc = 0, tc = 0;
+        if (w < nwords) {
+            const WordPos p = word_pos(rois, nrois, w);
+            Nbhd n;
+            load_nbhd(fine, rois[p.k], w, p.wx, p.yp, p.zp, n);
+            const uint32_t xm = n.w[0] ^ n.s[0], ym = n.w[0] ^ n.w[1], zm = n.w[0] ^ n.w[2];
+            vc = __popc(xm) + __popc(ym) + __popc(zm);
+            uint32_t mx = mixed_cells(n);
+            while (mx) {
+                const int b = __ffs(mx) - 1;
+                mx &= mx - 1;
+                tc += s_ntri[cell_case(n, b)];
+            }
+            vcnt[w] = vc;
+            tcnt[w] = tc;
+            emask[3 * (size_t)w + 0] = xm;
+            emask[3 * (size_t)w + 1] = ym;
+            emask[3 * (size_t)w + 2] = zm;
+        }
+        const uint32_t sv = block_sum<uint32_t>(vc, sh);
+        const uint32_t st = block_sum<uint32_t>(tc, sh);
+        if (threadIdx.x == 0) {
+            cpart[2 * (size_t)c] = sv;
+            cpart[2 * (size_t)c + 1] = st;
+        }
+    }
+}
+
+// One block per slot: chunk sums -> exclusive chunk bases, totals, capacity.
+__global__ void __launch_bounds__(1024) k_mc_scan(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
+                                                  const __grid_constant__ SlotList sl) {
+    __shared__ uint32_t sh[33];
+    const int slot = sl.s[blockIdx.x];
+    SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const uint32_t nchunks = info->n_chunks;
+    uint32_t* cpart = slot_ptr<uint32_t>(L, slot, L.cpart);
+    unsigned long long bv = 0, bt = 0;
+    for (uint32_t t0 = 0; t0 < nchunks; t0 += blockDim.x) {
+        const uint32_t i = t0 + threadIdx.x;
+        const uint32_t v = i < nchunks ? cpart[2 * (size_t)i] : 0u;
+        const uint32_t t = i < nchunks ? cpart[2 * (size_t)i + 1] : 0u;
+        uint32_t tv, tt;
+        const uint32_t ev = block_exclusive_scan(v, sh, tv);
+        const uint32_t et = block_exclusive_scan(t, sh, tt);
+        if (i < nchunks) {
+            cpart[2 * (size_t)i] = (uint32_t)(bv + ev);
+            cpart[2 * (size_t)i + 1] = (uint32_t)(bt + et);
+        }
+        bv += tv;
+        bt += tt;
+    }
+    if (threadIdx.x == 0) {
+        unsigned fl = 0;
+        if (bv > g.max_verts) fl |= FVV_FLAG_VERTS;
+        if (bt > g.max_tris) fl |= FVV_FLAG_TRIS;
+        info->flags |= fl;
+        info->n_verts = fl ? 0u : (uint32_t)bv;
+        info->n_tris = fl ? 0u : (uint32_t)bt;
+        if (fl) info->n_words = 0;   // nothing downstream runs on this frame
+    }
+}
+
+// Vertex record: ROI (14 bits) | axis (2) | ON at lower sample (1) | xp, yp, zp (15 bits each).
+__device__ __forceinline__ uint64_t pack_vrec(int k, int axis, int s0on, int xp, int yp, int zp) {
+    return (uint64_t)k | (uint64_t)axis << 14 | (uint64_t)s0on << 16 | (uint64_t)xp << 17 | (uint64_t)yp << 32 |
+           (uint64_t)zp << 47;
+}
+
+__global__ void __launch_bounds__(kChunk) k_mc_vertices(const __grid_constant__ Layout L,
+                                                        const __grid_constant__ SlotList sl) {
+    __shared__ uint32_t sh[33];
+    const int slot = sl.s[blockIdx.y];
+    const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const uint32_t nwords = info->n_words, nchunks = (nwords + kChunk - 1) / kChunk;
+    const int nrois = info->n_rois;
+    DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
+    const uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
+    const uint32_t* vcnt = slot_ptr<uint32_t>(L, slot, L.vcnt);
+    const uint32_t* tcnt = slot_ptr<uint32_t>(L, slot, L.tcnt);
+    const uint32_t* emask = slot_ptr<uint32_t>(L, slot, L.emask);
+    const uint32_t* cpart = slot_ptr<uint32_t>(L, slot, L.cpart);
+    uint32_t* vpre = slot_ptr<uint32_t>(L, slot, L.vpre);
+    uint32_t* tpre = slot_ptr<uint32_t>(L, slot, L.tpre);
+    uint64_t* vrec = slot_ptr<uint64_t>(L, slot, L.vrec);
+    for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const uint32_t w = c * kChunk + threadIdx.x;
+        const bool in = w < nwords;
+        uint32_t tv, tt;
+        const uint32_t ev = block_exclusive_scan(in ? vcnt[w] : 0u, sh, tv) + cpart[2 * (size_t)c];
+        const uint32_t et = block_exclusive_scan(in ? tcnt[w] : 0u, sh, tt) + cpart[2 * (size_t)c + 1];
+        if (!in) continue;
+        vpre[w] = ev;
+        tpre[w] = et;
+        const WordPos p = word_pos(rois, nrois, w);
+        DRoi& r = rois[p.k];
+        if (w == r.word_off) {
+            r.vert_off = ev;
+            r.tri_off = et;
+        }
+        const uint32_t xm = emask[3 * (size_t)w], ym = emask[3 * (size_t)w + 1], zm = emask[3 * (size_t)w + 2];
+        const uint32_t own = __ldg(fine + w);
+        uint32_t any = xm | ym | zm, id = ev;
+        while (any) {
+            const int b = __ffs(any) - 1;
+            any &= any - 1;
+            const int s0 = (own >> b) & 1u, xp = p.wx * 32 + b;
+            if ((xm >> b) & 1u) vrec[id++] = pack_vrec(p.k, 0, s0, xp, p.yp, p.zp);
+            if ((ym >> b) & 1u) vrec[id++] = pack_vrec(p.k, 1, s0, xp, p.yp, p.zp);
+            if ((zm >> b) & 1u) vrec[id++] = pack_vrec(p.k, 2, s0, xp, p.yp, p.zp);
+        }
+    }
+}
+
+// Sec. II-C, exact intersection: between the ON end a and the OFF end b of a
+// bipolar edge, `steps` times m = (a+b)/2, a = m if m is occupied else b = m;
+// the vertex is the final midpoint.
+__global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
+                                                const __grid_constant__ Layout L, const __grid_constant__ SlotList sl) {
+    __shared__ unsigned long long sh_t[32];
+    const int slot = sl.s[blockIdx.y];
+    const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const uint32_t nv = info->n_words ? info->n_verts : 0u;
+    const DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
+    const uint32_t* __restrict__ sil = slot_ptr<uint32_t>(L, slot, L.sil);
+    const uint64_t* vrec = slot_ptr<uint64_t>(L, slot, L.vrec);
+    float* verts = slot_ptr<float>(L, slot, L.verts);
+    uint32_t tests = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
+        const uint64_t rec = vrec[i];
+        const int k = (int)(rec & 0x3FFFu), axis = (int)(rec >> 14 & 3u), s0 = (int)(rec >> 16 & 1u);
+        const int q[3] = {(int)(rec >> 17 & 0x7FFFu), (int)(rec >> 32 & 0x7FFFu), (int)(rec >> 47 & 0x7FFFu)};
+        const DRoi& r = rois[k];
+        float a[3], b[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float c0 = fadd(r.fo[d], fmul(fadd((float)(q[d] - 1), 0.5f), g.sf));
+            const float c1 = fadd(r.fo[d], fmul(fadd((float)(q[d] - 1 + (d == axis)), 0.5f), g.sf));
+            a[d] = s0 ? c0 : c1;
+            b[d] = s0 ? c1 : c0;
+        }
+        for (int it = 0; it < g.steps; ++it) {
+            float m[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) m[d] = fmul(fadd(a[d], b[d]), 0.5f);
+            if (point_on(cams, sil, m[0], m[1], m[2], tests)) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) a[d] = m[d];
+            } else {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) b[d] = m[d];
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) verts[3 * (size_t)i + d] = fmul(fadd(a[d], b[d]), 0.5f);
+    }
+    const unsigned long long t = block_sum<unsigned long long>(tests, sh_t);
+    if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_bisect, t);
+}
+
+__global__ void __launch_bounds__(256) k_mc_triangles(const __grid_constant__ Layout L,
+                                                      const __grid_constant__ SlotList sl,
+                                                      const __grid_constant__ McTable mc) {
+    __shared__ uint8_t s_ntri[256];
+    __shared__ uint8_t s_edges[256 * kMaxTriPerCell * 3];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_ntri[i] = mc.ntri[i];
+    for (int i = threadIdx.x; i < 256 * kMaxTriPerCell * 3; i += blockDim.x) s_edges[i] = mc.edges[i];
+    __syncthreads();
+    const int slot = sl.s[blockIdx.y];
+    const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const uint32_t nwords = info->n_words;
+    const int nrois = info->n_rois;
+    const DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
+    const uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
+    const uint32_t* emask = slot_ptr<uint32_t>(L, slot, L.emask);
+    const uint32_t* vpre = slot_ptr<uint32_t>(L, slot, L.vpre);
+    const uint32_t* tpre = slot_ptr<uint32_t>(L, slot, L.tpre);
+    uint32_t* tris = slot_ptr<uint32_t>(L, slot, L.tris);
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) {
+        const WordPos p = word_pos(rois, nrois, w);
+        const DRoi& r = rois[p.k];
+        Nbhd n;
+        load_nbhd(fine, r, w, p.wx, p.yp, p.zp, n);
+        uint32_t mx = mixed_cells(n);
+        uint32_t t = tpre[w];
+        const uint32_t rs = (uint32_t)r.nxw, ps = rs * (uint32_t)(r.fdim[1] + 2);
+        while (mx) {
+            const int b = __ffs(mx) - 1;
+            mx &= mx - 1;
+            const int cs = cell_case(n, b);
+            const int nt = s_ntri[cs];
+            for (int j = 0; j < nt; ++j) {
+                uint32_t id[3];
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    const int e = s_edges[(cs * kMaxTriPerCell + j) * 3 + v];
+                    const int axis = e >> 2;
+                    // offsets of the edge's lower corner (same convention as the table)
+                    const int o0 = e & 1, o1 = (e >> 1) & 1;
+                    const int dx = axis == 0 ? 0 : o0;
+                    const int dy = axis == 1 ? 0 : (axis == 0 ? o0 : o1);
+                    const int dz = axis == 2 ? 0 : o1;
+                    const int X = p.wx * 32 + b + dx;
+                    const uint32_t wi = w + (uint32_t)(X >> 5) - (uint32_t)p.wx + (dy ? rs : 0u) + (dz ? ps : 0u);
+                    const int bb = X & 31;
+                    const uint32_t lm = (1u << bb) - 1u;
+                    const uint32_t xm = emask[3 * (size_t)wi], ym = emask[3 * (size_t)wi + 1],
+                                   zm = emask[3 * (size_t)wi + 2];
+                    uint32_t rank = __popc(xm & lm) + __popc(ym & lm) + __popc(zm & lm);
+                    if (axis >= 1) rank += (xm >> bb) & 1u;
+                    if (axis >= 2) rank += (ym >> bb) & 1u;
+                    id[v] = vpre[wi] + rank;
+                }
+                tris[3 * (size_t)t + 0] = id[0];
+                tris[3 * (size_t)t + 1] = id[1];
+                tris[3 * (size_t)t + 2] = id[2];
+                ++t;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_mesh(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc,
+                        int sms, cudaStream_t st) {
+    const int gc = grid_x(sms, sl.n, g.max_chunks, 1);
+    k_mc_count<<<dim3(gc, sl.n), kChunk, 0, st>>>(L, sl, mc);
+    k_mc_scan<<<sl.n, 1024, 0, st>>>(g, L, sl);
+    k_mc_vertices<<<dim3(gc, sl.n), kChunk, 0, st>>>(L, sl);
+    const int gv = grid_x(sms, sl.n, g.max_verts, 256);
+    k_bisect<<<dim3(gv, sl.n), 256, 0, st>>>(cams, g, L, sl);
+    const int gw = grid_x(sms, sl.n, g.max_fine_words, 256);
+    k_mc_triangles<<<dim3(gw, sl.n), 256, 0, st>>>(L, sl, mc);
+    return cudaGetLastError();
+}
+
+}  // namespace fvv

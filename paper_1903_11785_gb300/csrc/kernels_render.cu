@@ -1,0 +1,185 @@
+// kernels_render.cu -- Sec. II-D: per-camera depth images (Eq. (4)) and the
+// per-vertex visibility test and colour choice of Sec. II-D-2 and II-E.
+//
+// Depth images hold the binary32 bits of the distance (non-negative, so the
+// unsigned order of the bits is the order of the values) and are merged with
+// atomicMin; 0xFFFFFFFF means no triangle covered the pixel (+infinity).
+#include "fvv_device.cuh"
+
+namespace fvv {
+namespace {
+
+__global__ void __launch_bounds__(256) k_clear_depth(const __grid_constant__ Layout L,
+                                                     const __grid_constant__ SlotList sl, size_t n16) {
+    const int slot = sl.s[blockIdx.y];
+    uint4* d = slot_ptr<uint4>(L, slot, L.depth);
+    const uint4 v = make_uint4(kEmptyDepth, kEmptyDepth, kEmptyDepth, kEmptyDepth);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
+        __stcs(d + i, v);
+}
+
+// One thread per (camera, triangle), camera-major so a warp shares one camera.
+// The triangle is skipped if a vertex is not in front of the camera (w' <= 0)
+// or its projected area is zero.  Its depth is |centroid - C| with the
+// centroid ((v0 + v1) + v2) / 3; it is written into each pixel whose centre
+// lies in the closed box of the projection and on the inner side of (or on)
+// all three edges, for either winding.
+__global__ void __launch_bounds__(256) k_zbuffer(const __grid_constant__ CamSet cams, const __grid_constant__ Layout L,
+                                                 const __grid_constant__ SlotList sl) {
+    const int slot = sl.s[blockIdx.y];
+    const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const uint32_t nt = info->n_words ? info->n_tris : 0u;
+    const float* verts = slot_ptr<float>(L, slot, L.verts);
+    const uint32_t* tris = slot_ptr<uint32_t>(L, slot, L.tris);
+    uint32_t* depth = slot_ptr<uint32_t>(L, slot, L.depth);
+    const uint64_t total = (uint64_t)nt * (uint32_t)cams.n;
+    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (uint64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(idx / nt);
+        const uint32_t t = (uint32_t)(idx - (uint64_t)n * nt);
+        const Cam& c = cams.c[n];
+        float X[3], Y[3], Z[3], U[3], V[3];
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const uint32_t vi = __ldg(tris + 3 * (size_t)t + j);
+            X[j] = __ldg(verts + 3 * (size_t)vi);
+            Y[j] = __ldg(verts + 3 * (size_t)vi + 1);
+            Z[j] = __ldg(verts + 3 * (size_t)vi + 2);
+            float xp, yp, wp;
+            project(c.P, X[j], Y[j], Z[j], xp, yp, wp);
+            ok &= wp > 0.0f;
+            U[j] = __fdiv_rn(xp, wp);
+            V[j] = __fdiv_rn(yp, wp);
+        }
+        if (!ok) continue;
+        const float area = fsub(fmul(fsub(U[1], U[0]), fsub(V[2], V[0])), fmul(fsub(V[1], V[0]), fsub(U[2], U[0])));
+        if (!(area > 0.0f || area < 0.0f)) continue;
+        const float umin = fminf(fminf(U[0], U[1]), U[2]), umax = fmaxf(fmaxf(U[0], U[1]), U[2]);
+        const float vmin = fminf(fminf(V[0], V[1]), V[2]), vmax = fmaxf(fmaxf(V[0], V[1]), V[2]);
+        if (!(umax >= 0.5f) || !(vmax >= 0.5f)) continue;
+        if (!(umin <= fsub((float)c.W, 0.5f)) || !(vmin <= fsub((float)c.H, 0.5f))) continue;
+        const int x0 = umin < 0.0f ? 0 : (int)floorf(umin);
+        const int y0 = vmin < 0.0f ? 0 : (int)floorf(vmin);
+        const int x1 = umax > (float)c.W ? c.W - 1 : min((int)floorf(umax), c.W - 1);
+        const int y1 = vmax > (float)c.H ? c.H - 1 : min((int)floorf(vmax), c.H - 1);
+        const float gx = __fdiv_rn(fadd(fadd(X[0], X[1]), X[2]), 3.0f);
+        const float gy = __fdiv_rn(fadd(fadd(Y[0], Y[1]), Y[2]), 3.0f);
+        const float gz = __fdiv_rn(fadd(fadd(Z[0], Z[1]), Z[2]), 3.0f);
+        const float dx = fsub(gx, c.C[0]), dy = fsub(gy, c.C[1]), dz = fsub(gz, c.C[2]);
+        const float d = __fsqrt_rn(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
+        const uint32_t dbits = __float_as_uint(d);
+        uint32_t* D = depth + c.pix_off;
+        for (int yy = y0; yy <= y1; ++yy) {
+            const float pcy = fadd((float)yy, 0.5f);
+            if (pcy < vmin || pcy > vmax) continue;
+            for (int xx = x0; xx <= x1; ++xx) {
+                const float pcx = fadd((float)xx, 0.5f);
+                if (pcx < umin || pcx > umax) continue;
+                const float e0 = fsub(fmul(fsub(U[1], U[0]), fsub(pcy, V[0])), fmul(fsub(V[1], V[0]), fsub(pcx, U[0])));
+                const float e1 = fsub(fmul(fsub(U[2], U[1]), fsub(pcy, V[1])), fmul(fsub(V[2], V[1]), fsub(pcx, U[1])));
+                const float e2 = fsub(fmul(fsub(U[0], U[2]), fsub(pcy, V[2])), fmul(fsub(V[0], V[2]), fsub(pcx, U[2])));
+                const bool in = (e0 >= 0.0f && e1 >= 0.0f && e2 >= 0.0f) || (e0 <= 0.0f && e1 <= 0.0f && e2 <= 0.0f);
+                if (in) atomicMin(D + (size_t)yy * (unsigned)c.W + xx, dbits);
+            }
+        }
+    }
+}
+
+// Sec. II-D-2 and II-E: cameras ranked by squared distance of their centre to
+// the viewpoint (ties to the lower index); a vertex takes the first camera in
+// rank order that has it in front, inside the image and with
+// |v - C| - depth <= t_v, and that camera's RGB at the vertex's pixel.
+__global__ void __launch_bounds__(256) k_colour(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
+                                                const __grid_constant__ Layout L, const __grid_constant__ SlotList sl,
+                                                const float* __restrict__ viewpoints) {
+    __shared__ int rank_cam[FVV_MAX_CAMS];
+    const int slot = sl.s[blockIdx.y];
+    if (threadIdx.x < (unsigned)cams.n) {
+        const float* vp = viewpoints + 3 * blockIdx.y;
+        float d2[FVV_MAX_CAMS];
+        const int me = threadIdx.x;
+        int r = 0;
+        for (int m = 0; m < cams.n; ++m) {
+            const float ax = fsub(cams.c[m].C[0], vp[0]), ay = fsub(cams.c[m].C[1], vp[1]),
+                        az = fsub(cams.c[m].C[2], vp[2]);
+            d2[m] = fadd(fadd(fmul(ax, ax), fmul(ay, ay)), fmul(az, az));
+        }
+        for (int m = 0; m < cams.n; ++m) r += (d2[m] < d2[me]) || (d2[m] == d2[me] && m < me);
+        rank_cam[r] = me;
+    }
+    __syncthreads();
+    const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const uint32_t nv = info->n_words ? info->n_verts : 0u;
+    const float* verts = slot_ptr<float>(L, slot, L.verts);
+    const uint32_t* depth = slot_ptr<uint32_t>(L, slot, L.depth);
+    const uint8_t* const* rgb = slot_ptr<const uint8_t* const>(L, slot, L.rgb_ptrs);
+    uint8_t* out = slot_ptr<uint8_t>(L, slot, L.vrgb);
+    int* ocam = slot_ptr<int>(L, slot, L.vcam);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
+        const float X = verts[3 * (size_t)i], Y = verts[3 * (size_t)i + 1], Z = verts[3 * (size_t)i + 2];
+        int chosen = -1;
+        uint8_t col[3] = {0, 0, 0};
+        for (int k = 0; k < cams.n; ++k) {
+            const int n = rank_cam[k];
+            const Cam& c = cams.c[n];
+            float xp, yp, wp;
+            project(c.P, X, Y, Z, xp, yp, wp);
+            if (!(wp > 0.0f)) continue;
+            const float fu = floorf(__fdiv_rn(xp, wp)), fv = floorf(__fdiv_rn(yp, wp));
+            if (!(fu >= 0.0f && fu < (float)c.W && fv >= 0.0f && fv < (float)c.H)) continue;
+            const size_t pix = (size_t)(int)fv * (unsigned)c.W + (size_t)(int)fu;
+            const float dx = fsub(X, c.C[0]), dy = fsub(Y, c.C[1]), dz = fsub(Z, c.C[2]);
+            const float dist = __fsqrt_rn(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
+            const uint32_t db = __ldg(depth + c.pix_off + pix);
+            const float dep = db == kEmptyDepth ? __int_as_float(0x7f800000) : __uint_as_float(db);
+            if (!(fsub(dist, dep) <= g.t_v)) continue;
+            const uint8_t* src = rgb[n] + 3 * pix;
+            col[0] = __ldg(src);
+            col[1] = __ldg(src + 1);
+            col[2] = __ldg(src + 2);
+            chosen = n;
+            break;
+        }
+        out[3 * (size_t)i] = col[0];
+        out[3 * (size_t)i + 1] = col[1];
+        out[3 * (size_t)i + 2] = col[2];
+        ocam[i] = chosen;
+    }
+}
+
+__global__ void k_debug_depth(const __grid_constant__ Layout L, int slot, float* dst, size_t npix) {
+    const uint32_t* d = slot_ptr<uint32_t>(L, slot, L.depth);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t b = d[i];
+        dst[i] = b == kEmptyDepth ? __int_as_float(0x7f800000) : __uint_as_float(b);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,
+                         size_t depth_bytes, cudaStream_t st) {
+    const size_t n16 = depth_bytes / 16;
+    const int gc = grid_x(sms, sl.n, (long long)n16, 256);
+    k_clear_depth<<<dim3(gc, sl.n), 256, 0, st>>>(L, sl, n16);
+    const int gz = grid_x(sms, sl.n, (long long)g.max_tris * cams.n, 256);
+    k_zbuffer<<<dim3(gz, sl.n), 256, 0, st>>>(cams, L, sl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colour(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
+                          const float* viewpoints, int sms, cudaStream_t st) {
+    const int gv = grid_x(sms, sl.n, g.max_verts, 256);
+    k_colour<<<dim3(gv, sl.n), 256, 0, st>>>(cams, g, L, sl, viewpoints);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_depth(const CamSet& cams, const Layout& L, int slot, float* dst, size_t npix,
+                               cudaStream_t st) {
+    (void)cams;
+    k_debug_depth<<<(unsigned)std::min<size_t>((npix + 255) / 256, 8192), 256, 0, st>>>(L, slot, dst, npix);
+    return cudaGetLastError();
+}
+
+}  // namespace fvv

@@ -250,11 +250,13 @@ def scene_objects(config: str, index: int = 0):
         objs += ball((min(max(bx + vx * t, -9.0), 9.0), min(max(by + vy * t, -4.5), 4.5), bz), 0.105, g, obj=12)
         return objs
     if config == "judo":
+        # two players 0.45 m apart whose arms (along each player's local x)
+        # overlap between them, so that they form one connected component
         cx, cy = _u(g, -1.0, 1.0), _u(g, -1.0, 1.0)
         yaw = _u(g, 0, 2 * math.pi)
         d = np.array([math.cos(yaw), math.sin(yaw)]) * 0.225
-        objs = player((cx - d[0], cy - d[1]), yaw - math.pi / 2, _u(g, 1.7, 1.9), g, obj=0)
-        objs += player((cx + d[0], cy + d[1]), yaw + math.pi / 2, _u(g, 1.7, 1.9), g, obj=1)
+        objs = player((cx - d[0], cy - d[1]), yaw, _u(g, 1.7, 1.9), g, obj=0)
+        objs += player((cx + d[0], cy + d[1]), yaw + math.pi, _u(g, 1.7, 1.9), g, obj=1)
         ra = _u(g, 0, 2 * math.pi)
         objs += player((cx + 2.6 * math.cos(ra), cy + 2.6 * math.sin(ra)), _u(g, 0, 2 * math.pi), 1.75, g, obj=2)
         return objs

@@ -1,0 +1,183 @@
+"""Parity of the sm_103a path (through the C ABI) with the CPU oracle.
+
+Every output of every step is compared element by element on the same
+seeded inputs: packed silhouettes, coarse occupancy and its test count,
+canonical labels, ROIs, padded fine grids and their test count, vertices,
+triangles, bisection test count, depth images, colours and chosen cameras.
+All of them are bit-exact (the vertex tolerance of 1e-5 m is checked too)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from synth import ABSTAIN, make_frame, make_rig, render, scene_objects
+from synth.scenes import _gen, _make_rig
+from tests.gpu_harness import compare, run_gpu, run_oracle, unpack_rows
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    assert torch.cuda.is_available(), "the -m gpu tests need a CUDA GPU"
+    from paper_1903_11785_gb300.build import build
+    build()
+
+
+def test_tiny_frame_bit_exact():
+    rig, fr = make_frame("tiny", 0)
+    g = run_gpu(rig, [fr])[0]
+    ref = compare(rig, fr, g)
+    assert len(ref.rois) == 1 and len(ref.tris) > 10000
+
+
+def test_tiny_host_buffers_match():
+    rig, fr = make_frame("tiny", 1)
+    g = run_gpu(rig, [fr], host=True)[0]
+    compare(rig, fr, g)
+
+
+def test_batched_slots_each_bit_exact():
+    """Three frames in one reconstruct/colour call, slots listed out of order."""
+    rig = make_rig("tiny")
+    frames = [make_frame("tiny", i, rig=rig)[1] for i in range(3)]
+    outs = run_gpu(rig, frames, slots=[2, 0, 1])
+    for fr, g in zip(frames, outs):
+        compare(rig, fr, g)
+
+
+def test_batched_equals_one_by_one():
+    rig = make_rig("tiny")
+    frames = [make_frame("tiny", i, rig=rig)[1] for i in range(2)]
+    a = run_gpu(rig, frames, batch=True)
+    b = run_gpu(rig, frames, batch=False)
+    for x, y in zip(a, b):
+        for k in ("verts", "tris", "rgb", "cam", "depth", "labels", "fine"):
+            np.testing.assert_array_equal(x[k], y[k])
+
+
+def test_volleyball_frame_bit_exact():
+    rig, fr = make_frame("volleyball", 0)
+    g = run_gpu(rig, [fr])[0]
+    ref = compare(rig, fr, g)
+    assert len(ref.rois) == 13
+
+
+def test_judo_frame_bit_exact():
+    rig, fr = make_frame("judo", 0)
+    g = run_gpu(rig, [fr])[0]
+    compare(rig, fr, g)
+
+
+def test_hd720_frame_bit_exact():
+    rig, fr = make_frame("hd720", 0)
+    g = run_gpu(rig, [fr])[0]
+    compare(rig, fr, g)
+
+
+def test_abstain_policy_and_zero_steps():
+    rig, fr = make_frame("tiny", 2)
+    rig.oob_policy = ABSTAIN
+    rig.bisect_steps = 0
+    g = run_gpu(rig, [fr])[0]
+    ref = compare(rig, fr, g)
+    assert ref.tests_bisect == 0
+
+
+def test_ragged_image_width():
+    """Images whose width is not a multiple of 32 (scalar packing path, partial
+    last word of every silhouette row)."""
+    n, r, h = 6, 6.0, 3.0
+    cs = [(r * math.cos(2 * math.pi * k / n), r * math.sin(2 * math.pi * k / n), h) for k in range(n)]
+    rig = _make_rig("ragged", cs, [(0, 0, 0.9)] * n, 480.0, 630, 349, _gen("ragged/rig"),
+                    (-2.0, -2.0, 0.0), (2.0, 2.0, 2.5), 0.05, 0.01, 6)
+    fr = render(rig, scene_objects("tiny", 3), index=3, config_tag="ragged")
+    g = run_gpu(rig, [fr])[0]
+    compare(rig, fr, g)
+
+
+def test_empty_scene():
+    rig, fr = make_frame("tiny", 0)
+    fr.masks.zero_()
+    g = run_gpu(rig, [fr])[0]
+    c = g["counts"]
+    assert c["n_components"] == 0 and c["n_rois"] == 0 and c["n_verts"] == 0 and c["n_tris"] == 0
+    ref = compare(rig, fr, g)
+    assert ref.coarse.sum() == 0
+    assert np.isinf(g["depth"]).all()
+
+
+def test_noise_only_components_filtered():
+    """Isolated foreground specks in every camera: their hull pieces are tiny
+    components that Eq. (1) removes, and the GPU agrees on all of them."""
+    rig = make_rig("tiny")
+    rig.t_np = 3
+    fr = render(rig, scene_objects("tiny", 0), flip_prob=0.02, config_tag="tiny-noisy")
+    g = run_gpu(rig, [fr])[0]
+    ref = compare(rig, fr, g)
+    assert ref.n_components > len(ref.rois)
+
+
+def test_capacity_overflow_is_reported_and_recovers():
+    """Everything foreground: the one component fills the volume and its fine
+    grid exceeds max_fine_words; the call reports FVV_ERR_CAPACITY (flag FINE)
+    without touching memory beyond the arena, and the coarse stage still
+    matches the oracle.  A following normal frame on the same rig is exact."""
+    from oracle import Oracle
+    from paper_1903_11785_gb300 import fvv
+    rig, fr = make_frame("tiny", 0)
+    full = torch.ones_like(fr.masks)
+    r = fvv.Rig(rig, max_slots=1, host_staging=0, max_fine_words=1 << 16)
+    try:
+        r.upload_silhouettes(0, full.cuda())
+        r.reconstruct([0])
+        with pytest.raises(fvv.FvvError) as e:
+            r.counts(0)
+        assert e.value.status == fvv.FVV_ERR_CAPACITY
+        c = r.counts(0, allow_capacity=True)
+        assert c["flags"] & 4 and c["n_rois"] == 0 and c["n_components"] == 1
+        occ, tests = Oracle(rig).coarse(full.numpy())
+        nx, ny, nz = rig.grid_dims()
+        bits = unpack_rows(r.debug(0, fvv.FVV_DEBUG_COARSE_BITS).cpu().numpy().view(np.uint32), (nz, ny), nx)
+        np.testing.assert_array_equal(bits, occ)
+        assert c["tests_coarse"] == tests
+        # the same rig recovers on a normal frame
+        r.upload_silhouettes(0, fr.masks.cuda())
+        r.reconstruct([0])
+        c2 = r.counts(0)
+        assert c2["flags"] == 0 and c2["n_rois"] == 1
+    finally:
+        r.close()
+
+
+def test_vertex_capacity_overflow():
+    from paper_1903_11785_gb300 import fvv
+    rig, fr = make_frame("tiny", 0)
+    r = fvv.Rig(rig, max_slots=1, host_staging=0, max_verts=1000)
+    try:
+        r.upload_silhouettes(0, fr.masks.cuda())
+        r.reconstruct([0])
+        c = r.counts(0, allow_capacity=True)
+        assert c["flags"] & 8 and c["n_verts"] == 0
+    finally:
+        r.close()
+
+
+def test_not_ready_and_bad_slots():
+    from paper_1903_11785_gb300 import fvv
+    rig, fr = make_frame("tiny", 0)
+    r = fvv.Rig(rig, max_slots=2, host_staging=0, max_fine_words=1 << 16)
+    try:
+        with pytest.raises(fvv.FvvError) as e:
+            r.reconstruct([0])
+        assert e.value.status == fvv.FVV_ERR_NOT_READY
+        r.upload_silhouettes(0, fr.masks.cuda())
+        with pytest.raises(fvv.FvvError):
+            r.reconstruct([0, 0])
+        with pytest.raises(fvv.FvvError):
+            r.reconstruct([5])
+        with pytest.raises(fvv.FvvError):       # host masks need staging
+            r.upload_silhouettes(1, fr.masks)
+    finally:
+        r.close()
