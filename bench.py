@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Throughput of the coarse-to-fine visual-hull path on GB300.
+
+One step = one batched pass of the whole path over a batch of consecutive
+volleyball-shaped frames (16 cameras 1920x1080, 400x220x80 coarse voxels of
+5 cm, 1 cm fine voxels in the ROIs, 10 bisection steps): silhouette packing
+from device-resident masks, reconstruction of all frames in one
+fvv_reconstruct call (coarse hull, CCL + Eq. (1) filter + ROIs, fine hull,
+marching cubes with bisection, depth images) and one fvv_colour call.
+
+Printed (rank 0, one JSON line): batched frames/s (`value`), voxel-camera
+tests/s, the plain per-frame path on the same GPU (frames/s and p50/p99
+frame latency), per-stage times, the roofline of the dominant kernel, the
+CPU oracle timed on the host cores (`cpu_baseline`), the end-to-end number
+through the public API with host buffers (`e2e`), clocks and launch count.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--frames F]
+    python bench.py --impl reference ...    # the CPU oracle as the reference arm
+
+Multi-GPU: frames are independent, so N GPUs run N replicas on different
+frames (no collective on the data path); `value` is the total over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "frames/s & G voxel-camera tests/s on 1 GB300, batched vs plain; p50/p99 frame latency"
+CONFIG = "volleyball"
+WORKLOAD = ("volleyball-shaped frames: 16 cameras 1920x1080 (f=1800), 12 players + ball, volume 20x11x4 m, "
+            "coarse 5 cm (400x220x80), fine 1 cm in ROIs, 10 bisection steps, 0.1% silhouette flips")
+# FP32 operations of one camera test by definition: x', y', w' (9 mul + 9 add),
+# u and v (2 divisions), two floors.
+FLOPS_PER_TEST = 22
+# FP32 issue peak of GB300: 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock),
+# counting a multiply or an add as one operation (the path uses no FMA).
+ALU_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 1e12
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--frames", type=int, default=64, help="frames per batched step")
+    ap.add_argument("--plain-frames", type=int, default=16)
+    ap.add_argument("--cpu-frames", type=int, default=4, help="frames in the CPU-oracle sample")
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.rows, self.proc, self.gpu = [], None, gpu_index
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu is not None:
+                cmd[1:1] = ["-i", str(self.gpu)]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return self.summary()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ inputs
+
+def make_batch(n_frames, offset, device):
+    import torch
+    from synth import make_frame, make_rig
+    rig = make_rig(CONFIG)
+    masks, rgbs, vps = [], [], []
+    for i in range(n_frames):
+        _, fr = make_frame(CONFIG, offset + i, device=device, rig=rig)
+        masks.append(fr.masks)
+        rgbs.append(fr.rgb)
+        vps.append(fr.viewpoint)
+    return rig, torch.stack(masks), torch.stack(rgbs), np.stack(vps)
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_frames_per_s(rig, masks_cpu, rgb_cpu, vps):
+    """The oracle as it stands (single thread), full path per frame."""
+    from oracle import Oracle
+    o = Oracle(rig)
+    t0 = time.perf_counter()
+    tests = 0
+    for m, c, vp in zip(masks_cpu, rgb_cpu, vps):
+        ref = o.reconstruct(m)
+        d = o.depth(ref.verts, ref.tris)
+        o.colour(c, vp, d, ref.verts)
+        tests += ref.tests
+    dt = time.perf_counter() - t0
+    return len(masks_cpu) / dt, tests / dt, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from synth import make_frame, make_rig
+    rig = make_rig(CONFIG)
+    n = args.warmup + args.steps
+    frames = [make_frame(CONFIG, i, rig=rig)[1] for i in range(n)]
+    times, tests = [], 0
+    for i, fr in enumerate(frames):
+        fps, tps, dt = oracle_frames_per_s(rig, [fr.masks.numpy()], [fr.rgb.numpy()], [fr.viewpoint])
+        if i >= args.warmup:
+            times.append(dt)
+            tests += tps * dt
+    total = sum(times)
+    value = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "gtests_per_s": tests / total / 1e9,
+            "config": {"workload": WORKLOAD, "frames_per_step": 1, "parallelism": "single host thread"},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed volleyball-shaped frames, one per step, full path "
+                                       "(reconstruct + depth + colour), single thread"},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU path
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    assert torch.cuda.is_available(), "bench.py needs a CUDA GPU"
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1903_11785_gb300.build import build
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+    from paper_1903_11785_gb300 import fvv
+
+    F = args.frames
+    rig, masks, rgb, vps = make_batch(F, rank * F, "cuda")
+    N, H, W = masks.shape[1:]
+    r = fvv.Rig(rig, max_slots=F, host_staging=0 if args.no_e2e else 1)
+    slots = list(range(F))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for i in slots:
+            r.upload_silhouettes(i, masks[i])
+        r.reconstruct(slots)
+        r.colour(slots, rgb, vps)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    counts = [r.counts(i) for i in slots]
+    tests = sum(c["tests_coarse"] + c["tests_fine"] + c["tests_bisect"] for c in counts)
+    tsum = {k: sum(c[k] for c in counts) for k in ("tests_coarse", "tests_fine", "tests_bisect", "n_verts",
+                                                    "n_tris")}
+
+    # ---- timed region (batched)
+    gpu_index = None
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if cvd and cvd.split(",")[0].strip().isdigit():
+        gpu_index = int(cvd.split(",")[local].strip()) if len(cvd.split(",")) > local else None
+    clocks = ClockSampler(gpu_index).start()
+    time.sleep(0.4)
+    r.set_timing(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    stages = r.timing()
+    r.set_timing(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * F / (ms / 1000.0)
+
+    # ---- plain path: one frame per call, per-frame latency by events
+    lat = []
+    P = min(args.plain_frames, F)
+    for i in range(P + 2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r.upload_silhouettes(i % F, masks[i % F])
+        r.reconstruct([i % F])
+        r.colour([i % F], rgb[i % F:i % F + 1], vps[i % F:i % F + 1])
+        b.record(stream)
+        b.synchronize()
+        if i >= 2:
+            lat.append(a.elapsed_time(b))
+    plain_fps = len(lat) / (sum(lat) / 1000.0)
+
+    # ---- per-stage times and roofline of the dominant kernel
+    per_step = {k: v[0] / args.steps for k, v in stages.items()}
+    launches = {k: v[1] / args.steps for k, v in stages.items()}
+    work = {  # algorithmic FP32 operations per step
+        "coarse": tsum["tests_coarse"] * FLOPS_PER_TEST,
+        "fine": tsum["tests_fine"] * FLOPS_PER_TEST,
+        "bisect": tsum["tests_bisect"] * FLOPS_PER_TEST + tsum["n_verts"] * 6 * (rig.bisect_steps + 1),
+    }
+    dom = max(work, key=lambda k: per_step[k])
+    launch_ms = per_step[dom] / max(launches[dom], 1)
+    achieved = work[dom] / max(launches[dom], 1) / (launch_ms / 1000.0) / 1e12
+    roofline = {"bound": "alu", "kernel": {"coarse": "k_coarse_carve", "fine": "k_fine_carve",
+                                           "bisect": "k_bisect"}[dom],
+                "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / ALU_PEAK_TFLOPS,
+                "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (unit counts, max clock)",
+                "launch_ms": launch_ms}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        masks_h = masks.cpu().pin_memory()
+        rgb_h = rgb.cpu().pin_memory()
+        cnt = [r.counts(i) for i in slots]
+        outs = [dict(verts=torch.empty((c["n_verts"], 3), dtype=torch.float32).pin_memory(),
+                     tris=torch.empty((c["n_tris"], 3), dtype=torch.int32).pin_memory(),
+                     rgb=torch.empty((c["n_verts"], 3), dtype=torch.uint8).pin_memory(),
+                     cam=torch.empty((c["n_verts"],), dtype=torch.int32).pin_memory()) for c in cnt]
+        vp_ = fvv._vp
+        h2d = int(masks_h.numel() + rgb_h.numel())
+        d2h = int(sum(sum(t.numel() * t.element_size() for t in o.values()) for o in outs))
+
+        def e2e_step():
+            for i in slots:
+                r.upload_silhouettes(i, masks_h[i])
+            r.reconstruct(slots)
+            r.colour(slots, rgb_h, vps)
+            for i, o in zip(slots, outs):
+                fvv._check(fvv._lib.fvv_get_results(r.ptr, i, None, vp_(o["verts"].data_ptr()),
+                                                   vp_(o["tris"].data_ptr()), vp_(o["rgb"].data_ptr()),
+                                                   vp_(o["cam"].data_ptr()), 0, fvv._stream()), r.ptr)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        ok = all(torch.equal(o["verts"], r.results(i)["verts"].cpu()) for i, o in zip(slots[:2], outs[:2]))
+        ks = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ks):
+            e2e_step()
+        dt = (time.perf_counter() - t0) / ks
+        if world > 1:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * F / dt, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "steps": ks, "results_match_device": bool(ok)}
+
+    # ---- CPU oracle on the host cores (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        S = min(args.cpu_frames, F)
+        fps, tps, dt = oracle_frames_per_s(rig, masks[:S].cpu().numpy(), rgb[:S].cpu().numpy(), vps[:S])
+        cpu = {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle", "gtests_per_s": tps / 1e9,
+               "sample": f"{S} volleyball-shaped frames of the batch, full path (reconstruct + depth + colour), "
+                         f"single thread, {dt:.1f} s"}
+
+    n_launch = args.steps * (F + 16)
+    line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames_per_step": F, "cameras": int(N), "image": [int(W), int(H)],
+                       "l2": f"inputs larger than L2: {masks.numel() / 1e9:.2f} GB masks + "
+                             f"{rgb.numel() / 1e9:.2f} GB RGB per step",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "gtests_per_s": world * tests / (ms / 1000.0) / 1e9,
+            "tests_per_frame": tests / F,
+            "plain": {"frames_per_s": plain_fps, "latency_ms_p50": float(np.percentile(lat, 50)),
+                      "latency_ms_p99": float(np.percentile(lat, 99)), "frames": len(lat)},
+            "stages_ms_per_frame": {k: v / F for k, v in per_step.items()},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    r.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -212,6 +212,30 @@ fvv_status fvv_debug_bytes(fvv_rig *rig, int slot, int what, size_t *bytes);
  * fvv_debug_bytes), enqueued on `stream`. */
 fvv_status fvv_get_debug(fvv_rig *rig, int slot, int what, void *dst, size_t bytes, void *stream);
 
+/* Per-stage device time, the buckets of the paper's Table II (plus packing,
+ * the bisection kernel and colour on their own). */
+enum {
+    FVV_STAGE_PACK = 0,      /* step a0, silhouette packing (fvv_upload_silhouettes) */
+    FVV_STAGE_COARSE = 1,    /* B-1 coarse hull                                       */
+    FVV_STAGE_CCL = 2,       /* B-2 labelling, boxes, Eq. (1) filter, ROIs             */
+    FVV_STAGE_FINE = 3,      /* B-3 fine hull                                          */
+    FVV_STAGE_MC = 4,        /* C   marching cubes: edges, prefix sums, triangles      */
+    FVV_STAGE_BISECT = 5,    /* C   exact intersection by bisection                    */
+    FVV_STAGE_DEPTH = 6,     /* D-1 depth images                                       */
+    FVV_STAGE_COLOUR = 7,    /* D-2 visibility and colour (fvv_colour)                 */
+    FVV_N_STAGES = 8
+};
+
+/* Switch per-stage timing on (1) or off (0).  When on, each call records CUDA
+ * events around its stages on its stream (no synchronisation). */
+fvv_status fvv_set_timing(fvv_rig *rig, int enable);
+
+/* Wait for the recorded events and return, per stage, the summed device
+ * milliseconds (ms[FVV_N_STAGES]) and the number of timed intervals
+ * (calls[FVV_N_STAGES], may be NULL) since the previous fvv_get_timing or
+ * fvv_set_timing; then start a new accumulation. */
+fvv_status fvv_get_timing(fvv_rig *rig, float *ms, int *calls);
+
 /* The marching-cubes table the library built from its face rule: ntri[256]
  * triangle counts and edges[256*12*3] cube-edge numbers (corner c = dx + 2dy
  * + 4dz; cube edge e has axis e/4 and lower corner with the other two

@@ -28,6 +28,12 @@ struct fvv_rig {
     size_t sil_words = 0, npix = 0;
     std::vector<int> state;        // per slot: 0 empty, 1 uploaded, 2 reconstructed
     std::string err;
+    // per-stage timing: CUDA events around each stage, summed on request
+    bool timing = false;
+    std::vector<cudaEvent_t> events;   // pool, reused after every fvv_get_timing
+    size_t events_used = 0;
+    struct Interval { int stage; cudaEvent_t a, b; };
+    std::vector<Interval> intervals;
 };
 
 namespace {
@@ -178,6 +184,30 @@ fvv_status make_plan(const fvv_rig_desc* d, const fvv_recon_params* p, Plan& pl,
 
 bool check_slot(fvv_rig* rig, int slot) { return rig && slot >= 0 && slot < rig->max_slots; }
 
+constexpr size_t kMaxIntervals = 1 << 16;
+
+cudaEvent_t next_event(fvv_rig* rig) {
+    if (rig->events_used == rig->events.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        rig->events.push_back(e);
+    }
+    return rig->events[rig->events_used++];
+}
+
+// Records the start of a timed stage; returns the interval index or -1.
+int stage_begin(fvv_rig* rig, int stage, cudaStream_t st) {
+    if (!rig->timing || rig->intervals.size() >= kMaxIntervals) return -1;
+    cudaEvent_t a = next_event(rig), b = next_event(rig);
+    if (!a || !b || cudaEventRecord(a, st) != cudaSuccess) return -1;
+    rig->intervals.push_back({stage, a, b});
+    return (int)rig->intervals.size() - 1;
+}
+
+void stage_end(fvv_rig* rig, int idx, cudaStream_t st) {
+    if (idx >= 0) cudaEventRecord(rig->intervals[idx].b, st);
+}
+
 __global__ void k_zero_info(const __grid_constant__ Layout L, const __grid_constant__ SlotList sl) {
     uint32_t* p = reinterpret_cast<uint32_t*>(slot_ptr<SlotInfo>(L, sl.s[blockIdx.x], L.info));
     for (unsigned i = threadIdx.x; i < sizeof(SlotInfo) / 4; i += blockDim.x) p[i] = 0u;
@@ -277,6 +307,7 @@ fvv_status fvv_create_rig(const fvv_rig_desc* desc, const fvv_recon_params* para
 fvv_status fvv_destroy_rig(fvv_rig* rig) {
     if (!rig) return FVV_OK;
     cudaError_t e = cudaDeviceSynchronize();
+    for (cudaEvent_t ev : rig->events) cudaEventDestroy(ev);
     if (rig->own_arena) {
         cudaError_t f = cudaFree(rig->arena);
         if (e == cudaSuccess) e = f;
@@ -308,7 +339,9 @@ fvv_status fvv_upload_silhouettes(fvv_rig* rig, int slot, const uint8_t* const* 
             src[n] = stage + c.pix_off;
         }
     }
+    const int t = stage_begin(rig, FVV_STAGE_PACK, st);
     const cudaError_t e = launch_pack(rig->cams, rig->L, slot, src, st);
+    stage_end(rig, t, st);
     if (e != cudaSuccess) return cuda_fail(rig, e, "pack kernel");
     rig->state[slot] = 1;
     return FVV_OK;
@@ -335,14 +368,25 @@ fvv_status fvv_reconstruct(fvv_rig* rig, const int* slots, int n_slots, void* st
     fvv_status s = make_slot_list(rig, slots, n_slots, 1, sl);
     if (s != FVV_OK) return s;
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Grid& g = rig->grid;
+    const McTable mc{rig->mc_ntri, rig->mc_edges};
     k_zero_info<<<sl.n, 32, 0, st>>>(rig->L, sl);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = launch_coarse_carve(rig->cams, rig->grid, rig->L, sl, rig->sms, st);
-    if (e == cudaSuccess) e = launch_ccl(rig->grid, rig->L, sl, rig->sms, st);
-    if (e == cudaSuccess) e = launch_fine_carve(rig->cams, rig->grid, rig->L, sl, rig->sms, st);
-    if (e == cudaSuccess) e = launch_mesh(rig->cams, rig->grid, rig->L, sl, McTable{rig->mc_ntri, rig->mc_edges},
-                                          rig->sms, st);
-    if (e == cudaSuccess) e = launch_depth(rig->cams, rig->grid, rig->L, sl, rig->sms, align_up(rig->npix * 4), st);
+    int t;
+#define FVV_STAGE(stage, call)                  \
+    if (e == cudaSuccess) {                     \
+        t = stage_begin(rig, stage, st);        \
+        e = (call);                             \
+        stage_end(rig, t, st);                  \
+    }
+    FVV_STAGE(FVV_STAGE_COARSE, launch_coarse_carve(rig->cams, g, rig->L, sl, rig->sms, st));
+    FVV_STAGE(FVV_STAGE_CCL, launch_ccl(g, rig->L, sl, rig->sms, st));
+    FVV_STAGE(FVV_STAGE_FINE, launch_fine_carve(rig->cams, g, rig->L, sl, rig->sms, st));
+    FVV_STAGE(FVV_STAGE_MC, launch_mc_prefix(g, rig->L, sl, mc, rig->sms, st));
+    FVV_STAGE(FVV_STAGE_BISECT, launch_bisect(rig->cams, g, rig->L, sl, rig->sms, st));
+    FVV_STAGE(FVV_STAGE_MC, launch_mc_triangles(g, rig->L, sl, mc, rig->sms, st));
+    FVV_STAGE(FVV_STAGE_DEPTH, launch_depth(rig->cams, g, rig->L, sl, rig->sms, align_up(rig->npix * 4), st));
+#undef FVV_STAGE
     if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_reconstruct launch");
     for (int i = 0; i < sl.n; ++i) rig->state[sl.s[i]] = 2;
     return FVV_OK;
@@ -380,8 +424,42 @@ fvv_status fvv_colour(fvv_rig* rig, const int* slots, int n_slots, const uint8_t
             e = cudaMemcpyAsync(slot_ptr<void>(rig->L, sl.s[i], rig->L.rgb_ptrs), ptrs, sizeof(void*) * N,
                                 cudaMemcpyHostToDevice, st);
     }
-    if (e == cudaSuccess) e = launch_colour(rig->cams, rig->grid, rig->L, sl, rig->viewpoints, rig->sms, st);
+    if (e == cudaSuccess) {
+        const int t = stage_begin(rig, FVV_STAGE_COLOUR, st);
+        e = launch_colour(rig->cams, rig->grid, rig->L, sl, rig->viewpoints, rig->sms, st);
+        stage_end(rig, t, st);
+    }
     if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_colour");
+    return FVV_OK;
+}
+
+fvv_status fvv_set_timing(fvv_rig* rig, int enable) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    rig->timing = enable != 0;
+    rig->intervals.clear();
+    rig->events_used = 0;
+    return FVV_OK;
+}
+
+fvv_status fvv_get_timing(fvv_rig* rig, float* ms, int* calls) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    if (!ms) return fail(rig, FVV_ERR_INVALID_ARG, "ms must not be NULL");
+    for (int i = 0; i < FVV_N_STAGES; ++i) {
+        ms[i] = 0.0f;
+        if (calls) calls[i] = 0;
+    }
+    cudaError_t e = cudaSuccess;
+    for (const auto& iv : rig->intervals) {
+        float t = 0.0f;
+        e = cudaEventSynchronize(iv.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, iv.a, iv.b);
+        if (e != cudaSuccess) break;
+        ms[iv.stage] += t;
+        if (calls) calls[iv.stage] += 1;
+    }
+    rig->intervals.clear();
+    rig->events_used = 0;
+    if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_get_timing");
     return FVV_OK;
 }
 

@@ -135,8 +135,12 @@ cudaError_t launch_coarse_carve(const CamSet& cams, const Grid& g, const Layout&
 cudaError_t launch_ccl(const Grid& g, const Layout& L, const SlotList& sl, int sms, cudaStream_t st);
 cudaError_t launch_fine_carve(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
                               int sms, cudaStream_t st);
-cudaError_t launch_mesh(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
-                        const McTable& mc, int sms, cudaStream_t st);
+cudaError_t launch_mc_prefix(const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc, int sms,
+                             cudaStream_t st);
+cudaError_t launch_bisect(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,
+                          cudaStream_t st);
+cudaError_t launch_mc_triangles(const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc, int sms,
+                                cudaStream_t st);
 cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
                          int sms, size_t depth_bytes, cudaStream_t st);
 cudaError_t launch_colour(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,

@@ -441,14 +441,24 @@ __global__ void __launch_bounds__(256) k_mc_triangles(const __grid_constant__ La
 
 }  // namespace
 
-cudaError_t launch_mesh(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc,
-                        int sms, cudaStream_t st) {
+cudaError_t launch_mc_prefix(const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc, int sms,
+                             cudaStream_t st) {
     const int gc = grid_x(sms, sl.n, g.max_chunks, 1);
     k_mc_count<<<dim3(gc, sl.n), kChunk, 0, st>>>(L, sl, mc);
     k_mc_scan<<<sl.n, 1024, 0, st>>>(g, L, sl);
     k_mc_vertices<<<dim3(gc, sl.n), kChunk, 0, st>>>(L, sl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bisect(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,
+                          cudaStream_t st) {
     const int gv = grid_x(sms, sl.n, g.max_verts, 256);
     k_bisect<<<dim3(gv, sl.n), 256, 0, st>>>(cams, g, L, sl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mc_triangles(const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc, int sms,
+                                cudaStream_t st) {
     const int gw = grid_x(sms, sl.n, g.max_fine_words, 256);
     k_mc_triangles<<<dim3(gw, sl.n), 256, 0, st>>>(L, sl, mc);
     return cudaGetLastError();

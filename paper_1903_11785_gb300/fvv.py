@@ -31,6 +31,7 @@ FVV_OOB_STRICT, FVV_OOB_ABSTAIN = 0, 1
 FVV_MAX_CAMS, FVV_MAX_BATCH = 64, 256
 FVV_DEBUG_SIL_BITS, FVV_DEBUG_COARSE_BITS, FVV_DEBUG_LABELS, FVV_DEBUG_FINE_BITS, FVV_DEBUG_DEPTH = range(5)
 FLAG_NAMES = {1: "ROOTS", 2: "ROIS", 4: "FINE", 8: "VERTS", 16: "TRIS", 32: "LOOP"}
+STAGES = ("pack", "coarse", "ccl", "fine", "mc", "bisect", "depth", "colour")
 
 
 class RigDesc(C.Structure):
@@ -76,6 +77,8 @@ _sigs = {
     "fvv_debug_bytes": ([_vp, C.c_int, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
     "fvv_get_debug": ([_vp, C.c_int, C.c_int, _vp, C.c_size_t, _vp], C.c_int),
     "fvv_mc_table": ([_vp, _vp], C.c_int),
+    "fvv_set_timing": ([_vp, C.c_int], C.c_int),
+    "fvv_get_timing": ([_vp, C.POINTER(C.c_float), C.POINTER(C.c_int)], C.c_int),
     "fvv_last_error": ([_vp], C.c_char_p),
     "fvv_status_string": ([C.c_int], C.c_char_p),
     "fvv_version": ([], C.c_int),
@@ -236,6 +239,18 @@ def fvv_get_results(rig_ptr, slot, device="cuda", stream=None) -> dict:
     return dict(counts=c, rois=out_rois, verts=verts, tris=tris, rgb=rgb, cam=cam)
 
 
+def fvv_set_timing(rig_ptr, enable: bool):
+    _check(_lib.fvv_set_timing(rig_ptr, int(enable)), rig_ptr)
+
+
+def fvv_get_timing(rig_ptr):
+    """{stage: (summed ms, intervals)} since the previous call."""
+    ms = (C.c_float * len(STAGES))()
+    calls = (C.c_int * len(STAGES))()
+    _check(_lib.fvv_get_timing(rig_ptr, ms, calls), rig_ptr)
+    return {name: (ms[i], calls[i]) for i, name in enumerate(STAGES)}
+
+
 def fvv_get_debug(rig_ptr, slot, what, stream=None) -> torch.Tensor:
     n = C.c_size_t(0)
     _check(_lib.fvv_debug_bytes(rig_ptr, slot, what, C.byref(n)), rig_ptr)
@@ -288,3 +303,9 @@ class Rig:
 
     def debug(self, slot, what, stream=None):
         return fvv_get_debug(self.ptr, slot, what, stream)
+
+    def set_timing(self, enable=True):
+        fvv_set_timing(self.ptr, enable)
+
+    def timing(self):
+        return fvv_get_timing(self.ptr)

@@ -143,8 +143,10 @@ def _make_rig(name, centres, targets, f, W, H, gen, vol_min, vol_max, coarse, fi
                P64=P64, K64=np.stack(Ks), R64=np.stack(Rs), C64=np.asarray(centres, np.float64))
 
 
-def _gen(config: str, index: int = 0) -> torch.Generator:
-    g = torch.Generator()
+def _gen(config: str, index: int = 0, device="cpu") -> torch.Generator:
+    """Generator seeded from (SEED_BASE, config, index) on `device` (the CPU and
+    CUDA generators give different streams from the same seed)."""
+    g = torch.Generator(device=device)
     code = sum((i + 1) * ord(c) for i, c in enumerate(config))
     g.manual_seed(SEED_BASE * 1000003 + code * 7919 + index)
     return g
@@ -324,52 +326,53 @@ def render(rig: Rig, objects, index: int = 0, flip_prob: float = 1e-3, device="c
     if with_rgb:
         rgb = torch.empty((N, H, W, 3), dtype=torch.uint8, device=device)
         rgb[..., 0] = BACKGROUND_RGB[0]; rgb[..., 1] = BACKGROUND_RGB[1]; rgb[..., 2] = BACKGROUND_RGB[2]
-    g = _gen((config_tag or rig.name) + "/flips", index)
+    g = _gen((config_tag or rig.name) + "/flips", index, device=device)
+    groups = {}
+    for e in objects:
+        groups.setdefault(e.obj, []).append(e)
     for n in range(N):
-        Kinv = np.linalg.inv(rig.K64[n])
-        Rt = rig.R64[n].T
+        M = torch.tensor(rig.R64[n].T @ np.linalg.inv(rig.K64[n]), dtype=torch.float64, device=device)
         C = rig.C64[n]
-        zbest = None
-        if with_rgb:
-            zbest = torch.full((H, W), float("inf"), dtype=torch.float64, device=device)
-        for e in objects:
-            box = _ellipsoid_pixel_box(rig, n, e, W, H)
-            if box is None:
+        zbest = torch.full((H, W), float("inf"), dtype=torch.float64, device=device) if with_rgb else None
+        for es in groups.values():
+            boxes = [b for b in (_ellipsoid_pixel_box(rig, n, e, W, H) for e in es) if b is not None]
+            if not boxes:
                 continue
-            x0, x1, y0, y1 = box
+            x0, x1 = min(b[0] for b in boxes), max(b[1] for b in boxes)
+            y0, y1 = min(b[2] for b in boxes), max(b[3] for b in boxes)
             ys = torch.arange(y0, y1, dtype=torch.float64, device=device)
             xs = torch.arange(x0, x1, dtype=torch.float64, device=device)
             if conservative:
-                Cq = torch.tensor(_conic(rig, n, e), dtype=torch.float64, device=device)
-                hit = _square_meets_conic(Cq, xs, ys)
-                masks[n, y0:y1, x0:x1] |= hit.to(torch.uint8)
+                for e in es:
+                    Cq = torch.tensor(_conic(rig, n, e), dtype=torch.float64, device=device)
+                    masks[n, y0:y1, x0:x1] |= _square_meets_conic(Cq, xs, ys).to(torch.uint8)
                 continue
-            # ray d = R^T K^-1 (u, v, 1) through pixel centres
-            M = torch.tensor(Rt @ Kinv, dtype=torch.float64, device=device)
+            # rays d = R^T K^-1 (u, v, 1) through the pixel centres, in each
+            # ellipsoid's unit-sphere frame: |p + t dq|^2 = 1
             uu = (xs + 0.5)[None, :].expand(len(ys), -1)
             vv = (ys + 0.5)[:, None].expand(-1, len(xs))
-            d = (M[:, 0, None, None] * uu[None] + M[:, 1, None, None] * vv[None] + M[:, 2, None, None])
-            Ainv = torch.tensor((e.rot / e.axes[None, :]).T, dtype=torch.float64, device=device)  # A^-1 R^T
-            p = torch.tensor((e.rot / e.axes[None, :]).T @ (C - e.centre), dtype=torch.float64, device=device)
-            dq = torch.einsum("ij,jhw->ihw", Ainv, d)
-            a = (dq * dq).sum(0)
-            b = (p[:, None, None] * dq).sum(0)
-            c = float(p @ p) - 1.0
+            d = M[:, 0, None, None] * uu[None] + M[:, 1, None, None] * vv[None] + M[:, 2, None, None]
+            S = np.stack([(e.rot / e.axes[None, :]).T for e in es])             # (E,3,3) = A^-1 R^T
+            P0 = np.stack([Si @ (C - e.centre) for Si, e in zip(S, es)])        # (E,3)
+            S_t = torch.tensor(S, dtype=torch.float64, device=device)
+            p_t = torch.tensor(P0, dtype=torch.float64, device=device)
+            dq = torch.einsum("eij,jhw->eihw", S_t, d)
+            a = (dq * dq).sum(1)
+            b = (p_t[:, :, None, None] * dq).sum(1)
+            c = (p_t * p_t).sum(1)[:, None, None] - 1.0
             disc = b * b - a * c
-            hit = disc >= 0
             sq = torch.sqrt(torch.clamp(disc, min=0.0))
-            t_far = (-b + sq) / a
-            t_near = (-b - sq) / a
-            hit &= t_far > 0
-            masks[n, y0:y1, x0:x1] |= hit.to(torch.uint8)
+            hit = (disc >= 0) & ((-b + sq) / a > 0)
+            masks[n, y0:y1, x0:x1] |= hit.any(0).to(torch.uint8)
             if with_rgb:
-                tz = torch.where(hit, torch.clamp(t_near, min=0.0), torch.full_like(t_near, float("inf")))
-                better = tz < zbest[y0:y1, x0:x1]
-                zbest[y0:y1, x0:x1] = torch.where(better, tz, zbest[y0:y1, x0:x1])
-                col = torch.tensor(e.colour, dtype=torch.uint8, device=device)
-                rgb[n, y0:y1, x0:x1] = torch.where(better[..., None], col, rgb[n, y0:y1, x0:x1])
+                tz = torch.where(hit, torch.clamp((-b - sq) / a, min=0.0), torch.full_like(a, float("inf")))
+                tmin, imin = tz.min(0)
+                better = tmin < zbest[y0:y1, x0:x1]
+                zbest[y0:y1, x0:x1] = torch.where(better, tmin, zbest[y0:y1, x0:x1])
+                cols = torch.tensor([e.colour for e in es], dtype=torch.uint8, device=device)
+                rgb[n, y0:y1, x0:x1] = torch.where(better[..., None], cols[imin], rgb[n, y0:y1, x0:x1])
         if flip_prob > 0 and not conservative:
-            r = torch.rand((H, W), generator=g, dtype=torch.float32).to(device)
+            r = torch.rand((H, W), generator=g, dtype=torch.float32, device=device)
             masks[n] ^= (r < flip_prob).to(torch.uint8)
     return Frame(masks=masks, rgb=rgb, ellipsoids=list(objects), viewpoint=default_viewpoint(rig, index))
 

@@ -108,15 +108,19 @@ def test_empty_scene():
     assert np.isinf(g["depth"]).all()
 
 
-def test_noise_only_components_filtered():
-    """Isolated foreground specks in every camera: their hull pieces are tiny
-    components that Eq. (1) removes, and the GPU agrees on all of them."""
+def test_small_components_filtered():
+    """Small floating specks next to the player give hull pieces of a few
+    voxels that Eq. (1) removes (t_np = 8); heavy pixel noise (2% flips) is
+    on top.  The GPU agrees on every component, label and ROI."""
+    from synth import sphere_scene
     rig = make_rig("tiny")
-    rig.t_np = 3
-    fr = render(rig, scene_objects("tiny", 0), flip_prob=0.02, config_tag="tiny-noisy")
+    objs = scene_objects("tiny", 0)
+    for k, rad in enumerate((0.02, 0.035, 0.05, 0.12)):
+        objs += sphere_scene((-1.6 + 0.8 * k, 1.6, 1.8), rad)
+    fr = render(rig, objs, flip_prob=0.02, config_tag="tiny-specks")
     g = run_gpu(rig, [fr])[0]
     ref = compare(rig, fr, g)
-    assert ref.n_components > len(ref.rois)
+    assert ref.n_components > len(ref.rois) >= 2
 
 
 def test_capacity_overflow_is_reported_and_recovers():
