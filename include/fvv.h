@@ -212,6 +212,14 @@ fvv_status fvv_debug_bytes(fvv_rig *rig, int slot, int what, size_t *bytes);
  * fvv_debug_bytes), enqueued on `stream`. */
 fvv_status fvv_get_debug(fvv_rig *rig, int slot, int what, void *dst, size_t bytes, void *stream);
 
+/* Test hook for the projection of Sec. II-B-1: for camera `cam`, the pixel
+ * (px[i], py[i]) = (floor(x'/w'), floor(y'/w')) that world point
+ * pts[3i..3i+2] falls in, exactly as the hull tests compute it, or (-1, -1)
+ * if w' <= 0 or the pixel is outside the image.  pts, px and py are device
+ * arrays of n entries; the work is enqueued on `stream`. */
+fvv_status fvv_debug_pixels(fvv_rig *rig, int cam, long long n, const float *pts, int32_t *px, int32_t *py,
+                            void *stream);
+
 /* Per-stage device time, the buckets of the paper's Table II (plus packing,
  * the bisection kernel and colour on their own). */
 enum {

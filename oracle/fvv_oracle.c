@@ -28,8 +28,10 @@
  * Readings of the paper used here (each is also listed with the design notes):
  *  - A voxel is tested at its centre c = o + (i + 1/2) s (Sec. II-B-1 says
  *    the voxel is projected; the paper does not say which point).
- *  - A camera votes "foreground" iff w' > 0, the pixel floor(u), floor(v) is
- *    inside the image and its silhouette bit is set.  STRICT: a projection
+ *  - A camera votes "foreground" iff w' > 0, the pixel (floor(x'/w'),
+ *    floor(y'/w')) -- the floor of the exact quotient of the homogeneous
+ *    coordinates as computed -- is inside the image and its silhouette bit
+ *    is set.  STRICT: a projection
  *    outside the image votes background (Sec. II-B: a voxel outside the
  *    silhouettes is unoccupied).  ABSTAIN: such a camera does not vote, and a
  *    point no camera votes for is unoccupied.
@@ -113,6 +115,14 @@ static int grid_dim(float lo, float hi, float step)
     return (int)((d + s - 1) / s);
 }
 
+/* Index of the pixel holding the projected coordinate: floor of the exact
+ * quotient x/w of the homogeneous coordinates as computed (w > 0).  For the
+ * binary32 build the quotient is formed in double: a quotient of two binary32
+ * numbers that is not an integer lies at least 2^-41 of its magnitude (for
+ * magnitudes below 2^16) from every integer, far above double rounding, so
+ * the double floor is the exact one. */
+static double pixel_floor(R x, R w) { return floor((double)x / (double)w); }
+
 /* One camera's vote for world point (X,Y,Z): 1 foreground, 0 background,
  * -1 abstain (Sec. II-B-1: project the voxel onto the silhouette). */
 static int camera_vote(const orc_rig *rig, const uint8_t *const *masks, int n,
@@ -124,12 +134,9 @@ static int camera_vote(const orc_rig *rig, const uint8_t *const *masks, int n,
     R wp = (((R)p[8] * X + (R)p[9] * Y) + (R)p[10] * Z) + (R)p[11];
     int off = rig->oob_policy == ORC_ABSTAIN ? -1 : 0;
     if (!(wp > (R)0)) return off;
-    R u = xp / wp;
-    R v = yp / wp;
-    R fu = floor(u);
-    R fv = floor(v);
+    double fu = pixel_floor(xp, wp), fv = pixel_floor(yp, wp);
     int W = rig->width[n], H = rig->height[n];
-    if (!(fu >= (R)0 && fu < (R)W && fv >= (R)0 && fv < (R)H)) return off;
+    if (!(fu >= 0.0 && fu < (double)W && fv >= 0.0 && fv < (double)H)) return off;
     int px = (int)fu, py = (int)fv;
     return masks[n][(size_t)py * (size_t)W + (size_t)px] != 0;
 }
@@ -862,10 +869,9 @@ int orc_colour(const orc_rig *rig, const uint8_t *const *rgb, const float *viewp
             R yp = (((R)p[4] * X + (R)p[5] * Y) + (R)p[6] * Z) + (R)p[7];
             R wp = (((R)p[8] * X + (R)p[9] * Y) + (R)p[10] * Z) + (R)p[11];
             if (!(wp > (R)0)) continue;
-            R u = xp / wp, v = yp / wp;
-            R fu = floor(u), fv = floor(v);
+            double fu = pixel_floor(xp, wp), fv = pixel_floor(yp, wp);
             int W = rig->width[n], H = rig->height[n];
-            if (!(fu >= (R)0 && fu < (R)W && fv >= (R)0 && fv < (R)H)) continue;
+            if (!(fu >= 0.0 && fu < (double)W && fv >= 0.0 && fv < (double)H)) continue;
             size_t pix = (size_t)(int)fv * W + (size_t)(int)fu;
             R dx = X - (R)rig->centre[3 * n], dy = Y - (R)rig->centre[3 * n + 1],
               dz = Z - (R)rig->centre[3 * n + 2];

@@ -90,6 +90,8 @@ fvv_status make_plan(const fvv_rig_desc* d, const fvv_recon_params* p, Plan& pl,
         c.H = d->height[n];
         if (c.W < 1 || c.W > 65535 || c.H < 1 || c.H > 65535) { err = "image sizes must be 1..65535"; return FVV_ERR_INVALID_ARG; }
         c.Wq = (c.W + 31) / 32;
+        c.Wf = (float)c.W;
+        c.Hf = (float)c.H;
         c.bit_off = (uint32_t)words;
         c.pix_off = pix;
         words += (size_t)c.H * c.Wq;
@@ -168,6 +170,7 @@ fvv_status make_plan(const fvv_rig_desc* d, const fvv_recon_params* p, Plan& pl,
     take(L.vrec, (size_t)mv * 8);
     take(L.verts, (size_t)mv * 12);
     take(L.tris, (size_t)mt * 12);
+    take(L.tcen, (size_t)mt * 12);
     take(L.vrgb, (size_t)mv * 3);
     take(L.vcam, (size_t)mv * 4);
     take(L.depth, align_up(pix * 4));
@@ -531,6 +534,17 @@ fvv_status fvv_get_results(fvv_rig* rig, int slot, fvv_roi* rois, float* verts, 
     if (e == cudaSuccess && cam && c.n_verts)
         e = cudaMemcpyAsync(cam, slot_ptr<int32_t>(L, slot, L.vcam), 4 * (size_t)c.n_verts, kind, st);
     if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_get_results");
+    return FVV_OK;
+}
+
+fvv_status fvv_debug_pixels(fvv_rig* rig, int cam, long long n, const float* pts, int32_t* px, int32_t* py,
+                            void* stream) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    if (cam < 0 || cam >= rig->cams.n || n < 0 || (n > 0 && (!pts || !px || !py)))
+        return fail(rig, FVV_ERR_INVALID_ARG, "bad camera, count or NULL buffer");
+    if (n == 0) return FVV_OK;
+    const cudaError_t e = launch_debug_pixels(rig->cams, cam, n, pts, px, py, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_debug_pixels");
     return FVV_OK;
 }
 

@@ -26,6 +26,7 @@ struct Cam {
     float P[12];
     float C[3];
     int W, H, Wq;        // Wq = 32-bit words per silhouette row
+    float Wf, Hf;        // W and H as floats
     uint32_t bit_off;    // first silhouette word of this camera in a slot
     uint64_t pix_off;    // first pixel of this camera in per-slot pixel arrays
 };
@@ -56,6 +57,8 @@ struct SlotInfo {
     int n_rois;
     uint32_t n_words;           // fine words in use
     uint32_t n_chunks;
+    uint32_t n_samples;         // interior fine samples of all ROIs
+    uint32_t pad_;
     uint32_t n_verts, n_tris;
     uint32_t n_on;
     unsigned long long tests_coarse, tests_fine, tests_bisect;
@@ -69,6 +72,7 @@ struct DRoi {
     int nxw;                    // words per padded fine row
     uint32_t word_off;          // first fine word of this ROI in the slot
     uint32_t n_words;
+    uint32_t samp_off;          // first interior fine sample of this ROI in the slot
     uint32_t vert_off, tri_off; // filled after the scans (for fvv_roi)
 };
 
@@ -92,6 +96,7 @@ struct Layout {
     size_t vrec;                // uint64 vertex records, max_verts
     size_t verts;               // float x3, max_verts
     size_t tris;                // uint32 x3, max_tris
+    size_t tcen;                // float x3 triangle centroids, max_tris
     size_t vrgb;                // uint8 x3, max_verts
     size_t vcam;                // int32, max_verts
     size_t depth;               // uint32 per pixel of all cameras
@@ -145,6 +150,8 @@ cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, con
                          int sms, size_t depth_bytes, cudaStream_t st);
 cudaError_t launch_colour(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
                           const float* viewpoints, int sms, cudaStream_t st);
+cudaError_t launch_debug_pixels(const CamSet& cams, int cam, long long n, const float* pts, int32_t* px,
+                                int32_t* py, cudaStream_t st);
 cudaError_t launch_debug_labels(const Grid& g, const Layout& L, int slot, int32_t* dst, cudaStream_t st);
 cudaError_t launch_debug_depth(const CamSet& cams, const Layout& L, int slot, float* dst, size_t npix,
                                cudaStream_t st);

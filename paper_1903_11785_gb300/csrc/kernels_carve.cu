@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CamSet cam
 
 // Sec. II-B-1: the coarse hull over the whole volume.  Occupied voxels also
 // start their union-find tree (parent = own linear index) for Sec. II-B-2.
+template <int NC>
 __global__ void __launch_bounds__(256) k_coarse_carve(const __grid_constant__ CamSet cams,
                                                       const __grid_constant__ Grid g,
                                                       const __grid_constant__ Layout L,
@@ -70,20 +71,10 @@ __global__ void __launch_bounds__(256) k_coarse_carve(const __grid_constant__ Ca
         const int wx = (int)(w - row * (uint32_t)g.nxw);
         const int y = (int)(row % (uint32_t)g.ny), z = (int)(row / (uint32_t)g.ny);
         const int x = wx * 32 + lane;
-        bool alive = x < g.nx, voted = false;
         const float X = fadd(g.o[0], fmul(fadd((float)x, 0.5f), g.sc));
         const float Y = fadd(g.o[1], fmul(fadd((float)y, 0.5f), g.sc));
         const float Z = fadd(g.o[2], fmul(fadd((float)z, 0.5f), g.sc));
-        for (int n = 0; n < cams.n; ++n) {
-            if (!__any_sync(kFull, alive)) break;
-            if (alive) {
-                ++tests;
-                const int v = cam_vote(cams.c[n], cams.oob, sil, X, Y, Z);
-                alive = v != 0;
-                voted |= (v == 1);
-            }
-        }
-        const bool on = alive && voted;
+        const bool on = warp_test<NC>(cams, sil, X, Y, Z, x < g.nx, tests);
         const uint32_t word = __ballot_sync(kFull, on);
         if (on) {
             const int Lin = (int)(row * (uint32_t)g.nx) + x;
@@ -103,12 +94,20 @@ __global__ void __launch_bounds__(256) k_coarse_carve(const __grid_constant__ Ca
     }
 }
 
-// Index of the ROI holding fine word w: the last ROI whose first word <= w.
-__device__ __forceinline__ int roi_of_word(const DRoi* rois, int n, uint32_t w) {
+__global__ void __launch_bounds__(256) k_clear_fine(const __grid_constant__ Layout L,
+                                                    const __grid_constant__ SlotList sl) {
+    const int slot = sl.s[blockIdx.y];
+    const uint32_t nwords = slot_ptr<SlotInfo>(L, slot, L.info)->n_words;
+    uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) fine[w] = 0u;
+}
+
+// The ROI holding interior fine sample s: the last ROI whose first sample <= s.
+__device__ __forceinline__ int roi_of_sample(const DRoi* rois, int n, uint32_t s) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (rois[mid].word_off <= w) lo = mid;
+        if (rois[mid].samp_off <= s) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -116,7 +115,11 @@ __device__ __forceinline__ int roi_of_word(const DRoi* rois, int n, uint32_t w) 
 
 // Sec. II-B-3: the fine hull of every ROI, each treated as its own volume.
 // Fine grids are stored padded by one unoccupied sample per side (index 0
-// and fdim+1), rows of ceil((fdim_x+2)/32) words.
+// and fdim+1), rows of ceil((fdim_x+2)/32) words, cleared beforehand.  Lanes
+// take the interior samples of all ROIs in order (x fastest, rows wrapping),
+// so no lane idles on padding; each warp then ORs its results into the (at
+// most a few) padded words they fall in.
+template <int NC>
 __global__ void __launch_bounds__(256) k_fine_carve(const __grid_constant__ CamSet cams,
                                                     const __grid_constant__ Grid g,
                                                     const __grid_constant__ Layout L,
@@ -124,43 +127,78 @@ __global__ void __launch_bounds__(256) k_fine_carve(const __grid_constant__ CamS
     __shared__ unsigned long long sh_t[32];
     const int slot = sl.s[blockIdx.y];
     const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
-    const uint32_t nwords = info->n_words;
+    const uint32_t nsamp = info->n_words ? info->n_samples : 0u;
     const int nrois = info->n_rois;
     const DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
     const uint32_t* __restrict__ sil = slot_ptr<uint32_t>(L, slot, L.sil);
     uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
     const int lane = threadIdx.x & 31;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t stride = gridDim.x * blockDim.x;
     uint32_t tests = 0;
-    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords; w += nwarps) {
-        const DRoi& r = rois[roi_of_word(rois, nrois, w)];
-        const uint32_t lw = w - r.word_off;
-        const uint32_t row = lw / (uint32_t)r.nxw;
-        const int wx = (int)(lw - row * (uint32_t)r.nxw);
-        const int yp = (int)(row % (uint32_t)(r.fdim[1] + 2)), zp = (int)(row / (uint32_t)(r.fdim[1] + 2));
-        const int xp = wx * 32 + lane;
-        bool alive = xp >= 1 && xp <= r.fdim[0] && yp >= 1 && yp <= r.fdim[1] && zp >= 1 && zp <= r.fdim[2];
-        bool voted = false;
-        const float X = fadd(r.fo[0], fmul(fadd((float)(xp - 1), 0.5f), g.sf));
-        const float Y = fadd(r.fo[1], fmul(fadd((float)(yp - 1), 0.5f), g.sf));
-        const float Z = fadd(r.fo[2], fmul(fadd((float)(zp - 1), 0.5f), g.sf));
-        for (int n = 0; n < cams.n; ++n) {
-            if (!__any_sync(kFull, alive)) break;
-            if (alive) {
-                ++tests;
-                const int v = cam_vote(cams.c[n], cams.oob, sil, X, Y, Z);
-                alive = v != 0;
-                voted |= (v == 1);
-            }
+    // per-lane ROI cursor
+    uint32_t lo = 0, hi = 0, woff = 0;
+    int fx = 1, fy = 1, nxw = 1;
+    float fo0 = 0.f, fo1 = 0.f, fo2 = 0.f;
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nsamp; base += stride) {
+        const uint32_t s = base + lane;
+        const bool act = s < nsamp;
+        if (act && (s >= hi || s < lo)) {
+            const DRoi& r = rois[roi_of_sample(rois, nrois, s)];
+            lo = r.samp_off;
+            fx = r.fdim[0];
+            fy = r.fdim[1];
+            hi = lo + (uint32_t)fx * (uint32_t)fy * (uint32_t)r.fdim[2];
+            woff = r.word_off;
+            nxw = r.nxw;
+            fo0 = r.fo[0];
+            fo1 = r.fo[1];
+            fo2 = r.fo[2];
         }
-        const uint32_t word = __ballot_sync(kFull, alive && voted);
-        if (lane == 0) fine[w] = word;
+        const uint32_t loc = act ? s - lo : 0u;
+        const uint32_t row = loc / (uint32_t)fx;
+        const int x = (int)(loc - row * (uint32_t)fx);
+        const int y = (int)(row % (uint32_t)fy), z = (int)(row / (uint32_t)fy);
+        const float X = fadd(fo0, fmul(fadd((float)x, 0.5f), g.sf));
+        const float Y = fadd(fo1, fmul(fadd((float)y, 0.5f), g.sf));
+        const float Z = fadd(fo2, fmul(fadd((float)z, 0.5f), g.sf));
+        const bool on = warp_test<NC>(cams, sil, X, Y, Z, act, tests);
+        const uint32_t word = woff + ((uint32_t)(z + 1) * (uint32_t)(fy + 2) + (uint32_t)(y + 1)) * (uint32_t)nxw +
+                              (uint32_t)((x + 1) >> 5);
+        const uint32_t bit = on ? 1u << ((x + 1) & 31) : 0u;
+        uint32_t pend = __ballot_sync(kFull, act);
+        while (pend) {
+            const int leader = __ffs(pend) - 1;
+            const uint32_t T = __shfl_sync(kFull, word, leader);
+            const bool mine = act && word == T;
+            const uint32_t ored = __reduce_or_sync(kFull, mine ? bit : 0u);
+            if (lane == leader && ored) atomicOr(fine + T, ored);
+            pend &= ~__ballot_sync(kFull, mine);
+        }
     }
     const unsigned long long t = block_sum<unsigned long long>(tests, sh_t);
     if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_fine, t);
 }
 
+// Test hook: the pixel each point falls in for one camera (-1, -1 if none).
+__global__ void k_debug_pixels(const __grid_constant__ CamSet cams, int cam, long long n,
+                               const float* __restrict__ pts, int32_t* px, int32_t* py) {
+    const Cam& c = cams.c[cam];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int u, v;
+        cam_pixel(c, pts[3 * i], pts[3 * i + 1], pts[3 * i + 2], u, v);
+        px[i] = u;
+        py[i] = v;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_debug_pixels(const CamSet& cams, int cam, long long n, const float* pts, int32_t* px,
+                                int32_t* py, cudaStream_t st) {
+    const unsigned g = (unsigned)std::min<long long>((n + 255) / 256, 8192);
+    k_debug_pixels<<<g, 256, 0, st>>>(cams, cam, n, pts, px, py);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pack(const CamSet& cams, const Layout& L, int slot, const uint8_t* const* src, cudaStream_t st) {
     PackSrc a{};
@@ -178,14 +216,20 @@ cudaError_t launch_coarse_carve(const CamSet& cams, const Grid& g, const Layout&
                                 cudaStream_t st) {
     const long long words = (long long)g.nz * g.ny * g.nxw;
     const int gx = grid_x(sms, sl.n, words * 32, 256);
-    k_coarse_carve<<<dim3(gx, sl.n), 256, 0, st>>>(cams, g, L, sl);
+#define FVV_LAUNCH(NC) k_coarse_carve<NC><<<dim3(gx, sl.n), 256, 0, st>>>(cams, g, L, sl)
+    FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
+#undef FVV_LAUNCH
     return cudaGetLastError();
 }
 
 cudaError_t launch_fine_carve(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,
                               cudaStream_t st) {
+    const int gc = grid_x(sms, sl.n, (long long)g.max_fine_words, 256);
+    k_clear_fine<<<dim3(gc, sl.n), 256, 0, st>>>(L, sl);
     const int gx = grid_x(sms, sl.n, (long long)g.max_fine_words * 32, 256);
-    k_fine_carve<<<dim3(gx, sl.n), 256, 0, st>>>(cams, g, L, sl);
+#define FVV_LAUNCH(NC) k_fine_carve<NC><<<dim3(gx, sl.n), 256, 0, st>>>(cams, g, L, sl)
+    FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
+#undef FVV_LAUNCH
     return cudaGetLastError();
 }
 

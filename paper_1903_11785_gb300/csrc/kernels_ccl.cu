@@ -21,14 +21,24 @@ namespace {
 // FVV_FLAG_LOOP and returns, so no launch can run unbounded.
 constexpr int kStepBudget = 1 << 22;
 
-__device__ __forceinline__ int find_root(const int* parent, int x, int& budget) {
+// Root of x, shortening the path on the way (each visited node is pointed at
+// its grandparent).  Parents only ever point to smaller indices of the same
+// tree, so the plain stores are benign: a store that overwrites a concurrent
+// atomicMin link is made good by that union, which retries from the old
+// parent it got back.
+__device__ __forceinline__ int find_root(int* parent, int x, int& budget) {
+    int cur = __ldcg(parent + x);
+    if (cur == x || cur < 0) return x;
+    int prev = x;
     while (budget > 0) {
         --budget;
-        const int p = __ldcg(parent + x);
-        if (p == x || p < 0) return x;
-        x = p;
+        const int next = __ldcg(parent + cur);
+        if (next == cur || next < 0) return cur;
+        __stcg(parent + prev, next);
+        prev = cur;
+        cur = next;
     }
-    return x;
+    return cur;
 }
 
 __device__ __forceinline__ void unite(int* parent, int a, int b, int& budget) {
@@ -226,6 +236,7 @@ __global__ void __launch_bounds__(256) k_stats(const __grid_constant__ Grid g, c
 __global__ void __launch_bounds__(1024) k_filter(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
                                                  const __grid_constant__ SlotList sl) {
     __shared__ uint32_t sh[33];
+    __shared__ unsigned long long sh64[33];
     __shared__ int s_fail;
     const int slot = sl.s[blockIdx.x];
     SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
@@ -284,24 +295,32 @@ __global__ void __launch_bounds__(1024) k_filter(const __grid_constant__ Grid g,
         }
         return;
     }
-    // pass 2: first fine word of each ROI (exclusive prefix of n_words)
-    unsigned long long wbase = 0;
+    // pass 2: first fine word and first interior sample of each ROI
+    unsigned long long wbase = 0, sbase = 0;
     for (int t0 = 0; t0 < K; t0 += blockDim.x) {
         const int i = t0 + threadIdx.x;
-        const uint32_t nw = i < K ? rois[i].n_words : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan(nw, sh, tot);
-        if (i < K && wbase + ex <= 0xFFFFFFFFull) rois[i].word_off = (uint32_t)(wbase + ex);
-        wbase += tot;
+        const unsigned long long nw = i < K ? rois[i].n_words : 0ull;
+        const unsigned long long ns =
+            i < K ? (unsigned long long)rois[i].fdim[0] * rois[i].fdim[1] * rois[i].fdim[2] : 0ull;
+        unsigned long long tw, ts;
+        const unsigned long long ew = block_exclusive_scan64(nw, sh64, tw);
+        const unsigned long long es = block_exclusive_scan64(ns, sh64, ts);
+        if (i < K) {
+            rois[i].word_off = (uint32_t)min(wbase + ew, 0xFFFFFFFFull);
+            rois[i].samp_off = (uint32_t)min(sbase + es, 0xFFFFFFFFull);
+        }
+        wbase += tw;
+        sbase += ts;
     }
     if (threadIdx.x == 0) {
-        if (wbase > g.max_fine_words) {
+        if (wbase > g.max_fine_words || sbase > 0xFFFFFFFFull) {
             info->flags |= FVV_FLAG_FINE;
             info->n_rois = 0;
             info->n_words = 0;
         } else {
             info->n_rois = K;
             info->n_words = (uint32_t)wbase;
+            info->n_samples = (uint32_t)sbase;
             info->n_chunks = (uint32_t)((wbase + kChunk - 1) / kChunk);
         }
     }

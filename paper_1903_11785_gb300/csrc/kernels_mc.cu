@@ -143,10 +143,9 @@ struct Nbhd {
     uint32_t s[4];   // sample xp + 1
 };
 
-__device__ __forceinline__ void load_nbhd(const uint32_t* fine, const DRoi& r, uint32_t w, int wx, int yp, int zp,
-                                          Nbhd& n) {
+__device__ __forceinline__ void load_nbhd(const uint32_t* fine, const RoiCursor& r, uint32_t w, Nbhd& n) {
     const uint32_t rs = (uint32_t)r.nxw, ps = (uint32_t)r.nxw * (uint32_t)(r.fdim[1] + 2);
-    const bool hx = wx + 1 < r.nxw, hy = yp + 1 < r.fdim[1] + 2, hz = zp + 1 < r.fdim[2] + 2;
+    const bool hx = r.wx + 1 < r.nxw, hy = r.yp + 1 < r.fdim[1] + 2, hz = r.zp + 1 < r.fdim[2] + 2;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const bool dy = k & 1, dz = k >> 1;
@@ -174,32 +173,6 @@ __device__ __forceinline__ int cell_case(const Nbhd& n, int b) {
     return c;
 }
 
-__device__ __forceinline__ int roi_of_word(const DRoi* rois, int n, uint32_t w) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (rois[mid].word_off <= w) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
-struct WordPos {
-    int k, wx, yp, zp;
-};
-
-__device__ __forceinline__ WordPos word_pos(const DRoi* rois, int nrois, uint32_t w) {
-    WordPos p;
-    p.k = roi_of_word(rois, nrois, w);
-    const DRoi& r = rois[p.k];
-    const uint32_t lw = w - r.word_off;
-    const uint32_t row = lw / (uint32_t)r.nxw;
-    p.wx = (int)(lw - row * (uint32_t)r.nxw);
-    p.yp = (int)(row % (uint32_t)(r.fdim[1] + 2));
-    p.zp = (int)(row / (uint32_t)(r.fdim[1] + 2));
-    return p;
-}
-
 __global__ void __launch_bounds__(kChunk) k_mc_count(const __grid_constant__ Layout L, const __grid_constant__ SlotList sl,
                                                      const __grid_constant__ McTable mc) {
     __shared__ uint8_t s_ntri[256];
@@ -216,13 +189,14 @@ __global__ void __launch_bounds__(kChunk) k_mc_count(const __grid_constant__ Lay
     uint32_t* tcnt = slot_ptr<uint32_t>(L, slot, L.tcnt);
     uint32_t* emask = slot_ptr<uint32_t>(L, slot, L.emask);
     uint32_t* cpart = slot_ptr<uint32_t>(L, slot, L.cpart);
+    RoiCursor cur;
     for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const uint32_t w = c * kChunk + threadIdx.x;
         uint32_t vc = 0, tc = 0;
         if (w < nwords) {
-            const WordPos p = word_pos(rois, nrois, w);
+            cur.seek(rois, nrois, w);
             Nbhd n;
-            load_nbhd(fine, rois[p.k], w, p.wx, p.yp, p.zp, n);
+            load_nbhd(fine, cur, w, n);
             const uint32_t xm = n.w[0] ^ n.s[0], ym = n.w[0] ^ n.w[1], zm = n.w[0] ^ n.w[2];
             vc = __popc(xm) + __popc(ym) + __popc(zm);
             uint32_t mx = mixed_cells(n);
@@ -302,6 +276,7 @@ __global__ void __launch_bounds__(kChunk) k_mc_vertices(const __grid_constant__ 
     uint32_t* vpre = slot_ptr<uint32_t>(L, slot, L.vpre);
     uint32_t* tpre = slot_ptr<uint32_t>(L, slot, L.tpre);
     uint64_t* vrec = slot_ptr<uint64_t>(L, slot, L.vrec);
+    RoiCursor p;
     for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const uint32_t w = c * kChunk + threadIdx.x;
         const bool in = w < nwords;
@@ -311,11 +286,10 @@ __global__ void __launch_bounds__(kChunk) k_mc_vertices(const __grid_constant__ 
         if (!in) continue;
         vpre[w] = ev;
         tpre[w] = et;
-        const WordPos p = word_pos(rois, nrois, w);
-        DRoi& r = rois[p.k];
-        if (w == r.word_off) {
-            r.vert_off = ev;
-            r.tri_off = et;
+        p.seek(rois, nrois, w);
+        if (w == p.lo) {
+            rois[p.k].vert_off = ev;
+            rois[p.k].tri_off = et;
         }
         const uint32_t xm = emask[3 * (size_t)w], ym = emask[3 * (size_t)w + 1], zm = emask[3 * (size_t)w + 2];
         const uint32_t own = __ldg(fine + w);
@@ -334,6 +308,7 @@ __global__ void __launch_bounds__(kChunk) k_mc_vertices(const __grid_constant__ 
 // Sec. II-C, exact intersection: between the ON end a and the OFF end b of a
 // bipolar edge, `steps` times m = (a+b)/2, a = m if m is occupied else b = m;
 // the vertex is the final midpoint.
+template <int NC>
 __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
                                                 const __grid_constant__ Layout L, const __grid_constant__ SlotList sl) {
     __shared__ unsigned long long sh_t[32];
@@ -345,8 +320,13 @@ __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet c
     const uint64_t* vrec = slot_ptr<uint64_t>(L, slot, L.vrec);
     float* verts = slot_ptr<float>(L, slot, L.verts);
     uint32_t tests = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
-        const uint64_t rec = vrec[i];
+    // Warps walk the vertices together (the loop bounds are warp-uniform) so
+    // that the camera loop can stop when a ballot shows no lane still needs it.
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nv; base += stride) {
+        const uint32_t i = base + (threadIdx.x & 31u);
+        const bool act = i < nv;
+        const uint64_t rec = act ? vrec[i] : 0ull;
         const int k = (int)(rec & 0x3FFFu), axis = (int)(rec >> 14 & 3u), s0 = (int)(rec >> 16 & 1u);
         const int q[3] = {(int)(rec >> 17 & 0x7FFFu), (int)(rec >> 32 & 0x7FFFu), (int)(rec >> 47 & 0x7FFFu)};
         const DRoi& r = rois[k];
@@ -362,16 +342,17 @@ __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet c
             float m[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) m[d] = fmul(fadd(a[d], b[d]), 0.5f);
-            if (point_on(cams, sil, m[0], m[1], m[2], tests)) {
+            const bool on = warp_test<NC>(cams, sil, m[0], m[1], m[2], act, tests);
 #pragma unroll
-                for (int d = 0; d < 3; ++d) a[d] = m[d];
-            } else {
-#pragma unroll
-                for (int d = 0; d < 3; ++d) b[d] = m[d];
+            for (int d = 0; d < 3; ++d) {
+                a[d] = on ? m[d] : a[d];
+                b[d] = on ? b[d] : m[d];
             }
         }
+        if (act) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) verts[3 * (size_t)i + d] = fmul(fadd(a[d], b[d]), 0.5f);
+            for (int d = 0; d < 3; ++d) verts[3 * (size_t)i + d] = fmul(fadd(a[d], b[d]), 0.5f);
+        }
     }
     const unsigned long long t = block_sum<unsigned long long>(tests, sh_t);
     if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_bisect, t);
@@ -395,11 +376,14 @@ __global__ void __launch_bounds__(256) k_mc_triangles(const __grid_constant__ La
     const uint32_t* vpre = slot_ptr<uint32_t>(L, slot, L.vpre);
     const uint32_t* tpre = slot_ptr<uint32_t>(L, slot, L.tpre);
     uint32_t* tris = slot_ptr<uint32_t>(L, slot, L.tris);
+    const float* verts = slot_ptr<float>(L, slot, L.verts);
+    float* tcen = slot_ptr<float>(L, slot, L.tcen);
+    RoiCursor p;
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) {
-        const WordPos p = word_pos(rois, nrois, w);
-        const DRoi& r = rois[p.k];
+        p.seek(rois, nrois, w);
+        const RoiCursor& r = p;
         Nbhd n;
-        load_nbhd(fine, r, w, p.wx, p.yp, p.zp, n);
+        load_nbhd(fine, r, w, n);
         uint32_t mx = mixed_cells(n);
         uint32_t t = tpre[w];
         const uint32_t rs = (uint32_t)r.nxw, ps = rs * (uint32_t)(r.fdim[1] + 2);
@@ -433,6 +417,13 @@ __global__ void __launch_bounds__(256) k_mc_triangles(const __grid_constant__ La
                 tris[3 * (size_t)t + 0] = id[0];
                 tris[3 * (size_t)t + 1] = id[1];
                 tris[3 * (size_t)t + 2] = id[2];
+                // centroid ((v0 + v1) + v2) / 3 for the depth images (Sec. II-D-1)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float s = fadd(fadd(verts[3 * (size_t)id[0] + d], verts[3 * (size_t)id[1] + d]),
+                                         verts[3 * (size_t)id[2] + d]);
+                    tcen[3 * (size_t)t + d] = __fdiv_rn(s, 3.0f);
+                }
                 ++t;
             }
         }
@@ -453,7 +444,9 @@ cudaError_t launch_mc_prefix(const Grid& g, const Layout& L, const SlotList& sl,
 cudaError_t launch_bisect(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,
                           cudaStream_t st) {
     const int gv = grid_x(sms, sl.n, g.max_verts, 256);
-    k_bisect<<<dim3(gv, sl.n), 256, 0, st>>>(cams, g, L, sl);
+#define FVV_LAUNCH(NC) k_bisect<NC><<<dim3(gv, sl.n), 256, 0, st>>>(cams, g, L, sl)
+    FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
+#undef FVV_LAUNCH
     return cudaGetLastError();
 }
 

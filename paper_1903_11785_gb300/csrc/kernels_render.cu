@@ -1,9 +1,10 @@
 // kernels_render.cu -- Sec. II-D: per-camera depth images (Eq. (4)) and the
 // per-vertex visibility test and colour choice of Sec. II-D-2 and II-E.
 //
-// Depth images hold the binary32 bits of the distance (non-negative, so the
-// unsigned order of the bits is the order of the values) and are merged with
-// atomicMin; 0xFFFFFFFF means no triangle covered the pixel (+infinity).
+// Depth images hold the binary32 bits of the squared distance (non-negative,
+// so the unsigned order of the bits is the order of the values) and are
+// merged with atomicMin; 0xFFFFFFFF means no triangle covered the pixel
+// (+infinity).  Readers take the square root.
 #include "fvv_device.cuh"
 
 namespace fvv {
@@ -18,72 +19,90 @@ __global__ void __launch_bounds__(256) k_clear_depth(const __grid_constant__ Lay
         __stcs(d + i, v);
 }
 
-// One thread per (camera, triangle), camera-major so a warp shares one camera.
-// The triangle is skipped if a vertex is not in front of the camera (w' <= 0)
-// or its projected area is zero.  Its depth is |centroid - C| with the
-// centroid ((v0 + v1) + v2) / 3; it is written into each pixel whose centre
-// lies in the closed box of the projection and on the inner side of (or on)
-// all three edges, for either winding.
+// Eq. (4) for one triangle (world vertices X, Y, Z, squared centroid-camera
+// distance d2 as float bits) in camera c.  The triangle is skipped if a vertex
+// is not in front of the camera (w' <= 0) or its projected area is zero; its
+// value goes into each pixel whose centre lies in the closed box of the
+// projection and on the inner side of (or on) all three edges, either winding.
+// The buffer keeps the minimum of the squared distance: sqrt is monotone, so
+// the square root of that minimum is the minimum distance itself, taken
+// where the depth is read.
+__device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const float* Y, const float* Z, uint32_t d2,
+                                           uint32_t* __restrict__ depth) {
+    float U[3], V[3];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        float xp, yp, wp;
+        project(c.P, X[j], Y[j], Z[j], xp, yp, wp);
+        ok &= wp > 0.0f;
+        U[j] = __fdiv_rn(xp, wp);
+        V[j] = __fdiv_rn(yp, wp);
+    }
+    if (!ok) return;
+    const float area = fsub(fmul(fsub(U[1], U[0]), fsub(V[2], V[0])), fmul(fsub(V[1], V[0]), fsub(U[2], U[0])));
+    if (!(area > 0.0f || area < 0.0f)) return;
+    const float umin = fminf(fminf(U[0], U[1]), U[2]), umax = fmaxf(fmaxf(U[0], U[1]), U[2]);
+    const float vmin = fminf(fminf(V[0], V[1]), V[2]), vmax = fmaxf(fmaxf(V[0], V[1]), V[2]);
+    if (!(umax >= 0.5f) || !(vmax >= 0.5f)) return;
+    if (!(umin <= fsub(c.Wf, 0.5f)) || !(vmin <= fsub(c.Hf, 0.5f))) return;
+    const int x0 = umin < 0.0f ? 0 : (int)floorf(umin);
+    const int y0 = vmin < 0.0f ? 0 : (int)floorf(vmin);
+    const int x1 = umax > c.Wf ? c.W - 1 : min((int)floorf(umax), c.W - 1);
+    const int y1 = vmax > c.Hf ? c.H - 1 : min((int)floorf(vmax), c.H - 1);
+    uint32_t* D = depth + c.pix_off;
+    for (int yy = y0; yy <= y1; ++yy) {
+        const float pcy = fadd((float)yy, 0.5f);
+        if (pcy < vmin || pcy > vmax) continue;
+        for (int xx = x0; xx <= x1; ++xx) {
+            const float pcx = fadd((float)xx, 0.5f);
+            if (pcx < umin || pcx > umax) continue;
+            const float e0 = fsub(fmul(fsub(U[1], U[0]), fsub(pcy, V[0])), fmul(fsub(V[1], V[0]), fsub(pcx, U[0])));
+            const float e1 = fsub(fmul(fsub(U[2], U[1]), fsub(pcy, V[1])), fmul(fsub(V[2], V[1]), fsub(pcx, U[1])));
+            const float e2 = fsub(fmul(fsub(U[0], U[2]), fsub(pcy, V[2])), fmul(fsub(V[0], V[2]), fsub(pcx, U[2])));
+            const bool in = (e0 >= 0.0f && e1 >= 0.0f && e2 >= 0.0f) || (e0 <= 0.0f && e1 <= 0.0f && e2 <= 0.0f);
+            if (in) {
+                uint32_t* p = D + (size_t)yy * (unsigned)c.W + xx;
+                if (__ldcg(p) > d2) atomicMin(p, d2);   // skip the atomic when already nearer
+            }
+        }
+    }
+}
+
+// Grid (blocks, slots, cameras): the camera is uniform over a block, so its
+// matrix is read through uniform registers.  One thread per triangle; the
+// centroid ((v0 + v1) + v2) / 3 was formed once per triangle when the
+// triangle was emitted.
 __global__ void __launch_bounds__(256) k_zbuffer(const __grid_constant__ CamSet cams, const __grid_constant__ Layout L,
                                                  const __grid_constant__ SlotList sl) {
     const int slot = sl.s[blockIdx.y];
+    const Cam& c = cams.c[blockIdx.z];
     const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
     const uint32_t nt = info->n_words ? info->n_tris : 0u;
     const float* verts = slot_ptr<float>(L, slot, L.verts);
     const uint32_t* tris = slot_ptr<uint32_t>(L, slot, L.tris);
+    const float* tcen = slot_ptr<float>(L, slot, L.tcen);
     uint32_t* depth = slot_ptr<uint32_t>(L, slot, L.depth);
-    const uint64_t total = (uint64_t)nt * (uint32_t)cams.n;
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (uint64_t)gridDim.x * blockDim.x) {
-        const int n = (int)(idx / nt);
-        const uint32_t t = (uint32_t)(idx - (uint64_t)n * nt);
-        const Cam& c = cams.c[n];
-        float X[3], Y[3], Z[3], U[3], V[3];
-        bool ok = true;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        float X[3], Y[3], Z[3];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const uint32_t vi = __ldg(tris + 3 * (size_t)t + j);
             X[j] = __ldg(verts + 3 * (size_t)vi);
             Y[j] = __ldg(verts + 3 * (size_t)vi + 1);
             Z[j] = __ldg(verts + 3 * (size_t)vi + 2);
-            float xp, yp, wp;
-            project(c.P, X[j], Y[j], Z[j], xp, yp, wp);
-            ok &= wp > 0.0f;
-            U[j] = __fdiv_rn(xp, wp);
-            V[j] = __fdiv_rn(yp, wp);
         }
-        if (!ok) continue;
-        const float area = fsub(fmul(fsub(U[1], U[0]), fsub(V[2], V[0])), fmul(fsub(V[1], V[0]), fsub(U[2], U[0])));
-        if (!(area > 0.0f || area < 0.0f)) continue;
-        const float umin = fminf(fminf(U[0], U[1]), U[2]), umax = fmaxf(fmaxf(U[0], U[1]), U[2]);
-        const float vmin = fminf(fminf(V[0], V[1]), V[2]), vmax = fmaxf(fmaxf(V[0], V[1]), V[2]);
-        if (!(umax >= 0.5f) || !(vmax >= 0.5f)) continue;
-        if (!(umin <= fsub((float)c.W, 0.5f)) || !(vmin <= fsub((float)c.H, 0.5f))) continue;
-        const int x0 = umin < 0.0f ? 0 : (int)floorf(umin);
-        const int y0 = vmin < 0.0f ? 0 : (int)floorf(vmin);
-        const int x1 = umax > (float)c.W ? c.W - 1 : min((int)floorf(umax), c.W - 1);
-        const int y1 = vmax > (float)c.H ? c.H - 1 : min((int)floorf(vmax), c.H - 1);
-        const float gx = __fdiv_rn(fadd(fadd(X[0], X[1]), X[2]), 3.0f);
-        const float gy = __fdiv_rn(fadd(fadd(Y[0], Y[1]), Y[2]), 3.0f);
-        const float gz = __fdiv_rn(fadd(fadd(Z[0], Z[1]), Z[2]), 3.0f);
-        const float dx = fsub(gx, c.C[0]), dy = fsub(gy, c.C[1]), dz = fsub(gz, c.C[2]);
-        const float d = __fsqrt_rn(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
-        const uint32_t dbits = __float_as_uint(d);
-        uint32_t* D = depth + c.pix_off;
-        for (int yy = y0; yy <= y1; ++yy) {
-            const float pcy = fadd((float)yy, 0.5f);
-            if (pcy < vmin || pcy > vmax) continue;
-            for (int xx = x0; xx <= x1; ++xx) {
-                const float pcx = fadd((float)xx, 0.5f);
-                if (pcx < umin || pcx > umax) continue;
-                const float e0 = fsub(fmul(fsub(U[1], U[0]), fsub(pcy, V[0])), fmul(fsub(V[1], V[0]), fsub(pcx, U[0])));
-                const float e1 = fsub(fmul(fsub(U[2], U[1]), fsub(pcy, V[1])), fmul(fsub(V[2], V[1]), fsub(pcx, U[1])));
-                const float e2 = fsub(fmul(fsub(U[0], U[2]), fsub(pcy, V[2])), fmul(fsub(V[0], V[2]), fsub(pcx, U[2])));
-                const bool in = (e0 >= 0.0f && e1 >= 0.0f && e2 >= 0.0f) || (e0 <= 0.0f && e1 <= 0.0f && e2 <= 0.0f);
-                if (in) atomicMin(D + (size_t)yy * (unsigned)c.W + xx, dbits);
-            }
-        }
+        const float dx = fsub(__ldg(tcen + 3 * (size_t)t), c.C[0]);
+        const float dy = fsub(__ldg(tcen + 3 * (size_t)t + 1), c.C[1]);
+        const float dz = fsub(__ldg(tcen + 3 * (size_t)t + 2), c.C[2]);
+        const uint32_t d2 = __float_as_uint(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
+        raster_tri(c, X, Y, Z, d2, depth);
     }
+}
+
+// Stored squared distance -> distance (+infinity for an empty pixel).
+__device__ __forceinline__ float depth_of(uint32_t bits) {
+    return bits == kEmptyDepth ? __int_as_float(0x7f800000) : __fsqrt_rn(__uint_as_float(bits));
 }
 
 // Sec. II-D-2 and II-E: cameras ranked by squared distance of their centre to
@@ -123,16 +142,14 @@ __global__ void __launch_bounds__(256) k_colour(const __grid_constant__ CamSet c
         for (int k = 0; k < cams.n; ++k) {
             const int n = rank_cam[k];
             const Cam& c = cams.c[n];
-            float xp, yp, wp;
-            project(c.P, X, Y, Z, xp, yp, wp);
-            if (!(wp > 0.0f)) continue;
-            const float fu = floorf(__fdiv_rn(xp, wp)), fv = floorf(__fdiv_rn(yp, wp));
-            if (!(fu >= 0.0f && fu < (float)c.W && fv >= 0.0f && fv < (float)c.H)) continue;
-            const size_t pix = (size_t)(int)fv * (unsigned)c.W + (size_t)(int)fu;
+            int px, py;
+            cam_pixel(c, X, Y, Z, px, py);
+            if (px < 0) continue;
+            const size_t pix = (size_t)py * (unsigned)c.W + (size_t)px;
             const float dx = fsub(X, c.C[0]), dy = fsub(Y, c.C[1]), dz = fsub(Z, c.C[2]);
             const float dist = __fsqrt_rn(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
             const uint32_t db = __ldg(depth + c.pix_off + pix);
-            const float dep = db == kEmptyDepth ? __int_as_float(0x7f800000) : __uint_as_float(db);
+            const float dep = depth_of(db);
             if (!(fsub(dist, dep) <= g.t_v)) continue;
             const uint8_t* src = rgb[n] + 3 * pix;
             col[0] = __ldg(src);
@@ -152,7 +169,7 @@ __global__ void k_debug_depth(const __grid_constant__ Layout L, int slot, float*
     const uint32_t* d = slot_ptr<uint32_t>(L, slot, L.depth);
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (size_t)gridDim.x * blockDim.x) {
         const uint32_t b = d[i];
-        dst[i] = b == kEmptyDepth ? __int_as_float(0x7f800000) : __uint_as_float(b);
+        dst[i] = depth_of(b);
     }
 }
 
@@ -163,8 +180,8 @@ cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, con
     const size_t n16 = depth_bytes / 16;
     const int gc = grid_x(sms, sl.n, (long long)n16, 256);
     k_clear_depth<<<dim3(gc, sl.n), 256, 0, st>>>(L, sl, n16);
-    const int gz = grid_x(sms, sl.n, (long long)g.max_tris * cams.n, 256);
-    k_zbuffer<<<dim3(gz, sl.n), 256, 0, st>>>(cams, L, sl);
+    const int gz = std::max(1, grid_x(sms, sl.n, (long long)g.max_tris, 256) / std::max(1, cams.n / 2));
+    k_zbuffer<<<dim3(gz, sl.n, cams.n), 256, 0, st>>>(cams, L, sl);
     return cudaGetLastError();
 }
 

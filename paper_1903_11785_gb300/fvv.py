@@ -77,6 +77,7 @@ _sigs = {
     "fvv_debug_bytes": ([_vp, C.c_int, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
     "fvv_get_debug": ([_vp, C.c_int, C.c_int, _vp, C.c_size_t, _vp], C.c_int),
     "fvv_mc_table": ([_vp, _vp], C.c_int),
+    "fvv_debug_pixels": ([_vp, C.c_int, C.c_longlong, _vp, _vp, _vp, _vp], C.c_int),
     "fvv_set_timing": ([_vp, C.c_int], C.c_int),
     "fvv_get_timing": ([_vp, C.POINTER(C.c_float), C.POINTER(C.c_int)], C.c_int),
     "fvv_last_error": ([_vp], C.c_char_p),

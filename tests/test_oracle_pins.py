@@ -51,6 +51,34 @@ def test_orthographic_box_is_the_box():
     assert tests == expect
 
 
+def test_pixel_floor_is_exact():
+    """The pixel of a projection is the floor of the exact quotient of two
+    binary32 numbers.  The oracle forms it in double; checked here against
+    exact rational arithmetic on quotients placed within a few ulps of
+    integers (where a rounded binary32 quotient would round up to the
+    integer) and on random ones, so the double floor equals the exact one."""
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    cases = []
+    for _ in range(4000):
+        k = int(rng.integers(0, 4096))
+        w = np.float32(rng.uniform(0.5, 80.0))
+        x = np.float32(k * np.float64(w))
+        for d in range(-3, 4):
+            cases.append((np.nextafter(x, np.float32(np.inf) if d > 0 else np.float32(-np.inf)) if d else x, w))
+            x = cases[-1][0]
+    for _ in range(4000):
+        cases.append((np.float32(rng.uniform(-100, 5000) * rng.uniform(1, 60)), np.float32(rng.uniform(0.1, 60))))
+    hits = 0
+    for x, w in cases:
+        exact = Fraction(float(x)) / Fraction(float(w))
+        fl = exact.numerator // exact.denominator
+        assert np.floor(np.float64(x) / np.float64(w)) == fl
+        q32 = np.float32(x) / np.float32(w)
+        hits += int(np.floor(q32) != fl)
+    assert hits > 0          # binary32 rounding does cross integers on these inputs
+
+
 def test_out_of_image_policy():
     """A view shifted so part of the volume falls outside its image: STRICT
     carves that part, ABSTAIN lets the other views decide."""
