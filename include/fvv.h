@@ -220,6 +220,35 @@ fvv_status fvv_get_debug(fvv_rig *rig, int slot, int what, void *dst, size_t byt
 fvv_status fvv_debug_pixels(fvv_rig *rig, int cam, long long n, const float *pts, int32_t *px, int32_t *py,
                             void *stream);
 
+/* Allocation-free labelling (the paper has no counterpart; it is a service of
+ * this library).  For callers that cannot call cudaMalloc: code that runs
+ * inside a host framework which owns all device memory, or real-time loops
+ * in which an allocation (which may synchronise the device) is not allowed.
+ * It labels the 26-connected components of a coarse occupancy bitset,
+ * numbered by their smallest linear index, and applies the size filter of
+ * Eq. (1) (keep iff t_np <= voxels <= t_nb), exactly as fvv_reconstruct does
+ * for FVV_DEBUG_LABELS.
+ *   coarse_bits  device, nz*ny rows of ceil(nx/32) uint32, bit x%32 of word
+ *                x/32 (the FVV_DEBUG_COARSE_BITS layout); bits past nx ignored
+ *   labels       device, nz*ny*nx int32 written in full: canonical label of
+ *                every voxel, 0 for empty voxels and removed components
+ *   counts       device int32[3]: components before the filter, components
+ *                kept, FVV_FLAG_* bits (ROOTS if more than 8192 components,
+ *                in which case every label is 0; LOOP if a union-find bound
+ *                was hit)
+ * Work is enqueued on `stream`; nothing is allocated.  Its scratch is one
+ * static device array inside the library (about 32.4 MB, held on every GPU
+ * that loads the library until the process exits), which limits the grid to
+ * nx*ny*nz <= 8,388,608 voxels: larger grids, non-positive sizes or NULL
+ * pointers give FVV_ERR_INVALID_ARG without launching anything.  The first
+ * call on each device looks up the array's device address with that device
+ * current, so make that first call before any stream capture.  All calls
+ * share the array and each clears what it needs: calls whose work overlaps
+ * on the GPU (different streams or host threads without ordering) race and
+ * give wrong labels. */
+fvv_status fvv_label_components_noalloc(const uint32_t *coarse_bits, int nx, int ny, int nz, int t_np, int t_nb,
+                                        int32_t *labels, int32_t *counts, void *stream);
+
 /* Per-stage device time, the buckets of the paper's Table II (plus packing,
  * the bisection kernel and colour on their own). */
 enum {

@@ -78,6 +78,7 @@ _sigs = {
     "fvv_get_debug": ([_vp, C.c_int, C.c_int, _vp, C.c_size_t, _vp], C.c_int),
     "fvv_mc_table": ([_vp, _vp], C.c_int),
     "fvv_debug_pixels": ([_vp, C.c_int, C.c_longlong, _vp, _vp, _vp, _vp], C.c_int),
+    "fvv_label_components_noalloc": ([_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp], C.c_int),
     "fvv_set_timing": ([_vp, C.c_int], C.c_int),
     "fvv_get_timing": ([_vp, C.POINTER(C.c_float), C.POINTER(C.c_int)], C.c_int),
     "fvv_last_error": ([_vp], C.c_char_p),
