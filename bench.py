@@ -47,6 +47,11 @@ FLOPS_PER_TEST = 22
 # FP32 issue peak of GB300: 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock),
 # counting a multiply or an add as one operation (the path uses no FMA).
 ALU_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 1e12
+# DRAM bytes (read + write) per frame of each hull kernel, from one ncu capture
+# of a 4-frame launch of the current kernels (profiles/k_fine_carve_volleyball_batch4.md,
+# profiles/hull_and_depth_kernels_volleyball_batch4.md), scaled to a launch by
+# its frame count.  None for a kernel changed since that capture.
+DRAM_BYTES_PER_FRAME = {"fine": 6.898432e6 / 4, "bisect": (17.21728e6 + 18944) / 4, "coarse": (4.320512e6 + 12032) / 4}
 
 
 def parse_args():
@@ -58,6 +63,9 @@ def parse_args():
     ap.add_argument("--plain-frames", type=int, default=16)
     ap.add_argument("--cpu-frames", type=int, default=4, help="frames in the CPU-oracle sample")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--serve-requests", type=int, default=1200,
+                    help="requests of the serving leg (4 rigs at 30 Hz each; 0 skips it)")
+    ap.add_argument("--serve-pool", type=int, default=8, help="frames per rig in the serving pool")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -178,6 +186,49 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ serving
+
+SERVE_RIGS = (("volleyball", 1000), ("volleyball", 2000), ("judo", 0), ("hd720", 0))   # (config, first frame)
+
+
+def run_serving(args, rank):
+    """Requests from four rigs (two volleyball-shaped 16x1080p, one judo-shaped
+    12x4K, one 8x720p), Poisson arrivals at 30 Hz per rig, admitted under a
+    40 GB memory budget and served with continuous batching.  Run once at the
+    offered rate and once with all arrivals compressed 1000x (saturation)."""
+    import torch
+    from paper_1903_11785_gb300.serve import RigPool, Server, poisson_schedule, summarize
+    from synth import make_frame, make_rig
+    pools = []
+    for cfg, first in SERVE_RIGS:
+        rig = make_rig(cfg)
+        frames = [make_frame(cfg, first + rank * 100 + i, device="cuda", rig=rig)[1] for i in range(args.serve_pool)]
+        pools.append(RigPool(scene_rig=rig, masks=[f.masks.cpu().pin_memory() for f in frames],
+                             rgb=[f.rgb.cpu().pin_memory() for f in frames],
+                             viewpoints=np.stack([f.viewpoint for f in frames])))
+        del frames
+        torch.cuda.empty_cache()
+    srv = Server(pools, budget_bytes=40 << 30)
+    try:
+        out = {"rigs": [c for c, _ in SERVE_RIGS], "slots": srv.slots, "budget_gb": 40, "offered_fps": 4 * 30.0}
+        warm = poisson_schedule(len(pools), 30.0, 40, seed=7, pool_sizes=[args.serve_pool] * len(pools))
+        srv.run(warm, time_scale=1000.0)
+        reqs = poisson_schedule(len(pools), 30.0, args.serve_requests, seed=1903,
+                                pool_sizes=[args.serve_pool] * len(pools))
+        out.update(summarize(srv.run(reqs)))
+        reqs = poisson_schedule(len(pools), 30.0, args.serve_requests, seed=1904,
+                                pool_sizes=[args.serve_pool] * len(pools))
+        out["saturated"] = summarize(srv.run(reqs, time_scale=1000.0), time_scale=1000.0)
+        per_rig = {}
+        for k, (cfg, _) in enumerate(SERVE_RIGS):
+            lat = [(q.t_done - q.t_arrival) * 1000 for q in reqs if q.rig == k]
+            per_rig[f"{k}:{cfg}"] = {"frames": len(lat)}
+        out["saturated"]["per_rig_frames"] = per_rig
+        return out
+    finally:
+        srv.close()
+
+
 # ------------------------------------------------------------------ GPU path
 
 def run_ours(args):
@@ -197,6 +248,7 @@ def run_ours(args):
 
     F = args.frames
     rig, masks, rgb, vps = make_batch(F, rank * F, "cuda")
+    mask_bytes, rgb_bytes = masks.numel(), rgb.numel()
     N, H, W = masks.shape[1:]
     r = fvv.Rig(rig, max_slots=F, host_staging=0 if args.no_e2e else 1)
     slots = list(range(F))
@@ -271,11 +323,14 @@ def run_ours(args):
     dom = max(work, key=lambda k: per_step[k])
     launch_ms = per_step[dom] / max(launches[dom], 1)
     achieved = work[dom] / max(launches[dom], 1) / (launch_ms / 1000.0) / 1e12
+    traffic = DRAM_BYTES_PER_FRAME.get(dom)
     roofline = {"bound": "alu", "kernel": {"coarse": "k_coarse_carve", "fine": "k_fine_carve",
                                            "bisect": "k_bisect"}[dom],
                 "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / ALU_PEAK_TFLOPS,
-                "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (unit counts, max clock)",
-                "launch_ms": launch_ms}
+                "traffic": traffic * F if traffic is not None else None,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (unit counts, max clock)",
+                "launch_ms": launch_ms, "tests_per_launch": tsum["tests_" + dom] if dom != "bisect" else
+                tsum["tests_bisect"], "flops_per_test": FLOPS_PER_TEST}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -317,11 +372,23 @@ def run_ours(args):
         e2e = {"value": world * F / dt, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": ks, "results_match_device": bool(ok)}
 
+    S = min(args.cpu_frames, F)
+    cpu_sample = (masks[:S].cpu().numpy(), rgb[:S].cpu().numpy(), vps[:S])
+
+    # ---- serving: 4 rigs, Poisson arrivals, continuous batching under a memory budget
+    serving = None
+    if args.serve_requests > 0:
+        r.close()
+        del masks, rgb
+        torch.cuda.empty_cache()
+        serving = run_serving(args, rank)
+        r = None
+
     # ---- CPU oracle on the host cores (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         S = min(args.cpu_frames, F)
-        fps, tps, dt = oracle_frames_per_s(rig, masks[:S].cpu().numpy(), rgb[:S].cpu().numpy(), vps[:S])
+        fps, tps, dt = oracle_frames_per_s(rig, *cpu_sample)
         cpu = {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle", "gtests_per_s": tps / 1e9,
                "sample": f"{S} volleyball-shaped frames of the batch, full path (reconstruct + depth + colour), "
                          f"single thread, {dt:.1f} s"}
@@ -331,18 +398,20 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "frames_per_step": F, "cameras": int(N), "image": [int(W), int(H)],
-                       "l2": f"inputs larger than L2: {masks.numel() / 1e9:.2f} GB masks + "
-                             f"{rgb.numel() / 1e9:.2f} GB RGB per step",
+                       "l2": f"inputs larger than L2: {mask_bytes / 1e9:.2f} GB masks + "
+                             f"{rgb_bytes / 1e9:.2f} GB RGB per step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "gtests_per_s": world * tests / (ms / 1000.0) / 1e9,
             "tests_per_frame": tests / F,
             "plain": {"frames_per_s": plain_fps, "latency_ms_p50": float(np.percentile(lat, 50)),
                       "latency_ms_p99": float(np.percentile(lat, 99)), "frames": len(lat)},
             "stages_ms_per_frame": {k: v / F for k, v in per_step.items()},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clk}
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "gpu_launches": n_launch,
+            "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    r.close()
+    if r is not None:
+        r.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

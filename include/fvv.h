@@ -30,9 +30,12 @@
  * valid until that slot is uploaded to or reconstructed again.
  *
  * Streams.  Every call that takes `void* stream` (a cudaStream_t; NULL is the
- * legacy default stream) only enqueues work on it and returns; calls on one
- * rig must be ordered on one stream (or by the caller's events), because they
- * share the rig's slots.  fvv_get_counts synchronises the stream it is given.
+ * legacy default stream) only enqueues work on it and returns (host inputs in
+ * pageable memory are the exception: CUDA copies those before returning).
+ * Everything a call touches on the device belongs to the slots it names, so
+ * calls on disjoint slots may run concurrently on different streams; calls
+ * on the same slot must be ordered (one stream, or the caller's events).
+ * fvv_get_counts synchronises the stream it is given.
  *
  * Errors.  Every call returns an fvv_status and never throws.  A NULL or
  * inconsistent argument gives FVV_ERR_INVALID_ARG; a failed CUDA call gives

@@ -24,7 +24,6 @@ struct fvv_rig {
     bool own_arena = false;
     uint8_t* mc_ntri = nullptr;    // device
     uint8_t* mc_edges = nullptr;   // device
-    float* viewpoints = nullptr;   // device, FVV_MAX_BATCH x 3
     size_t sil_words = 0, npix = 0;
     std::vector<int> state;        // per slot: 0 empty, 1 uploaded, 2 reconstructed
     std::string err;
@@ -178,7 +177,6 @@ fvv_status make_plan(const fvv_rig_desc* d, const fvv_recon_params* p, Plan& pl,
         take(L.mask_stage, pix);
         take(L.rgb_stage, pix * 3);
     }
-    take(L.rgb_ptrs, (size_t)FVV_MAX_CAMS * sizeof(void*));
     L.stride = o;
     pl.common = align_up(256) + align_up(256 * kMaxTriPerCell * 3) + align_up(FVV_MAX_BATCH * 3 * sizeof(float));
     pl.total = pl.common + (size_t)d->max_slots * L.stride;
@@ -293,7 +291,6 @@ fvv_status fvv_create_rig(const fvv_rig_desc* desc, const fvv_recon_params* para
     rig->state.assign(desc->max_slots, 0);
     rig->mc_ntri = reinterpret_cast<uint8_t*>(rig->arena);
     rig->mc_edges = reinterpret_cast<uint8_t*>(rig->arena + align_up(256));
-    rig->viewpoints = reinterpret_cast<float*>(rig->arena + align_up(256) + align_up(256 * kMaxTriPerCell * 3));
     std::vector<uint8_t> ntri(256), edges(256 * kMaxTriPerCell * 3, 0);
     build_mc_table(ntri.data(), edges.data());
     e = cudaMemcpy(rig->mc_ntri, ntri.data(), ntri.size(), cudaMemcpyHostToDevice);
@@ -406,32 +403,36 @@ fvv_status fvv_colour(fvv_rig* rig, const int* slots, int n_slots, const uint8_t
     for (int i = 0; i < 3 * n_slots; ++i)
         if (!std::isfinite(viewpoints[i])) return fail(rig, FVV_ERR_INVALID_ARG, "viewpoints must be finite");
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemcpyAsync(rig->viewpoints, viewpoints, sizeof(float) * 3 * n_slots, cudaMemcpyHostToDevice, st);
     const int N = rig->cams.n;
-    for (int i = 0; i < n_slots && e == cudaSuccess; ++i) {
-        const uint8_t* ptrs[FVV_MAX_CAMS];
-        for (int n = 0; n < N; ++n) {
-            const uint8_t* src = rgb[(size_t)i * N + n];
-            if (!src) return fail(rig, FVV_ERR_INVALID_ARG, "an rgb pointer is NULL");
-            if (rgb_on_device) {
-                ptrs[n] = src;
-            } else {
-                const Cam& c = rig->cams.c[n];
-                uint8_t* dst = slot_ptr<uint8_t>(rig->L, sl.s[i], rig->L.rgb_stage) + 3 * c.pix_off;
-                e = cudaMemcpyAsync(dst, src, (size_t)3 * c.W * c.H, cudaMemcpyHostToDevice, st);
-                if (e != cudaSuccess) break;
-                ptrs[n] = dst;
+    for (size_t i = 0; i < (size_t)n_slots * N; ++i)
+        if (!rgb[i]) return fail(rig, FVV_ERR_INVALID_ARG, "an rgb pointer is NULL");
+    cudaError_t e = cudaSuccess;
+    const int t = stage_begin(rig, FVV_STAGE_COLOUR, st);
+    // slots go to the kernel in groups of kColourBatch, with their RGB sources
+    // and viewpoints as kernel parameters
+    for (int i0 = 0; i0 < n_slots && e == cudaSuccess; i0 += kColourBatch) {
+        ColourBatch cb;
+        cb.n = std::min(kColourBatch, n_slots - i0);
+        for (int j = 0; j < cb.n && e == cudaSuccess; ++j) {
+            const int i = i0 + j;
+            cb.slot[j] = sl.s[i];
+            for (int k = 0; k < 3; ++k) cb.view[j][k] = viewpoints[3 * i + k];
+            for (int n = 0; n < N; ++n) {
+                const uint8_t* src = rgb[(size_t)i * N + n];
+                if (rgb_on_device) {
+                    cb.rgb[j][n] = src;
+                } else {
+                    const Cam& c = rig->cams.c[n];
+                    uint8_t* dst = slot_ptr<uint8_t>(rig->L, sl.s[i], rig->L.rgb_stage) + 3 * c.pix_off;
+                    e = cudaMemcpyAsync(dst, src, (size_t)3 * c.W * c.H, cudaMemcpyHostToDevice, st);
+                    if (e != cudaSuccess) break;
+                    cb.rgb[j][n] = dst;
+                }
             }
         }
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(slot_ptr<void>(rig->L, sl.s[i], rig->L.rgb_ptrs), ptrs, sizeof(void*) * N,
-                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = launch_colour(rig->cams, rig->grid, rig->L, cb, rig->sms, n_slots, st);
     }
-    if (e == cudaSuccess) {
-        const int t = stage_begin(rig, FVV_STAGE_COLOUR, st);
-        e = launch_colour(rig->cams, rig->grid, rig->L, sl, rig->viewpoints, rig->sms, st);
-        stage_end(rig, t, st);
-    }
+    stage_end(rig, t, st);
     if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_colour");
     return FVV_OK;
 }

@@ -102,7 +102,6 @@ struct Layout {
     size_t depth;               // uint32 per pixel of all cameras
     size_t mask_stage;          // uint8 per pixel (host uploads), or 0
     size_t rgb_stage;           // uint8 x3 per pixel (host uploads), or 0
-    size_t rgb_ptrs;            // const uint8_t* per camera: colour sources
 };
 
 template <typename T>
@@ -148,8 +147,18 @@ cudaError_t launch_mc_triangles(const Grid& g, const Layout& L, const SlotList& 
                                 cudaStream_t st);
 cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
                          int sms, size_t depth_bytes, cudaStream_t st);
-cudaError_t launch_colour(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
-                          const float* viewpoints, int sms, cudaStream_t st);
+// Colour-call arguments of up to kColourBatch slots, passed by value as a
+// kernel parameter (so nothing is copied from host memory).
+constexpr int kColourBatch = 48;
+struct ColourBatch {
+    int n;
+    int slot[kColourBatch];
+    float view[kColourBatch][3];
+    const uint8_t* rgb[kColourBatch][FVV_MAX_CAMS];
+};
+
+cudaError_t launch_colour(const CamSet& cams, const Grid& g, const Layout& L, const ColourBatch& cb, int sms,
+                          int total_slots, cudaStream_t st);
 cudaError_t launch_debug_pixels(const CamSet& cams, int cam, long long n, const float* pts, int32_t* px,
                                 int32_t* py, cudaStream_t st);
 cudaError_t launch_debug_labels(const Grid& g, const Layout& L, int slot, int32_t* dst, cudaStream_t st);

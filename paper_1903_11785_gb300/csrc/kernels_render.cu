@@ -110,12 +110,12 @@ __device__ __forceinline__ float depth_of(uint32_t bits) {
 // rank order that has it in front, inside the image and with
 // |v - C| - depth <= t_v, and that camera's RGB at the vertex's pixel.
 __global__ void __launch_bounds__(256) k_colour(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
-                                                const __grid_constant__ Layout L, const __grid_constant__ SlotList sl,
-                                                const float* __restrict__ viewpoints) {
+                                                const __grid_constant__ Layout L,
+                                                const __grid_constant__ ColourBatch cb) {
     __shared__ int rank_cam[FVV_MAX_CAMS];
-    const int slot = sl.s[blockIdx.y];
+    const int slot = cb.slot[blockIdx.y];
     if (threadIdx.x < (unsigned)cams.n) {
-        const float* vp = viewpoints + 3 * blockIdx.y;
+        const float* vp = cb.view[blockIdx.y];
         float d2[FVV_MAX_CAMS];
         const int me = threadIdx.x;
         int r = 0;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256) k_colour(const __grid_constant__ CamSet c
     const uint32_t nv = info->n_words ? info->n_verts : 0u;
     const float* verts = slot_ptr<float>(L, slot, L.verts);
     const uint32_t* depth = slot_ptr<uint32_t>(L, slot, L.depth);
-    const uint8_t* const* rgb = slot_ptr<const uint8_t* const>(L, slot, L.rgb_ptrs);
+    const uint8_t* const* rgb = cb.rgb[blockIdx.y];
     uint8_t* out = slot_ptr<uint8_t>(L, slot, L.vrgb);
     int* ocam = slot_ptr<int>(L, slot, L.vcam);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
@@ -185,10 +185,10 @@ cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_colour(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
-                          const float* viewpoints, int sms, cudaStream_t st) {
-    const int gv = grid_x(sms, sl.n, g.max_verts, 256);
-    k_colour<<<dim3(gv, sl.n), 256, 0, st>>>(cams, g, L, sl, viewpoints);
+cudaError_t launch_colour(const CamSet& cams, const Grid& g, const Layout& L, const ColourBatch& cb, int sms,
+                          int total_slots, cudaStream_t st) {
+    const int gv = grid_x(sms, total_slots, g.max_verts, 256);
+    k_colour<<<dim3(gv, cb.n), 256, 0, st>>>(cams, g, L, cb);
     return cudaGetLastError();
 }
 
