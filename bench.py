@@ -67,6 +67,7 @@ def parse_args():
                     help="requests of the serving leg (4 rigs at 30 Hz each; 0 skips it)")
     ap.add_argument("--serve-pool", type=int, default=8, help="frames per rig in the serving pool")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -263,6 +264,11 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    tuning = None
+    if not args.no_tune:
+        tuning = r.autotune(slots)          # launch shapes picked on this batch
+        step()
+        torch.cuda.synchronize()
     counts = [r.counts(i) for i in slots]
     tests = sum(c["tests_coarse"] + c["tests_fine"] + c["tests_bisect"] for c in counts)
     tsum = {k: sum(c[k] for c in counts) for k in ("tests_coarse", "tests_fine", "tests_bisect", "n_verts",
@@ -297,19 +303,25 @@ def run_ours(args):
         ms = float(t.item())
     value = world * F / (ms / 1000.0)
 
-    # ---- plain path: one frame per call, per-frame latency by events
+    # ---- plain path: one frame per call (slot 0, reconstruction replayed as a
+    # CUDA graph on a side stream), per-frame latency by events
     lat = []
     P = min(args.plain_frames, F)
-    for i in range(P + 2):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        r.upload_silhouettes(i % F, masks[i % F])
-        r.reconstruct([i % F])
-        r.colour([i % F], rgb[i % F:i % F + 1], vps[i % F:i % F + 1])
-        b.record(stream)
-        b.synchronize()
-        if i >= 2:
-            lat.append(a.elapsed_time(b))
+    r.set_graphs(True)
+    ps = torch.cuda.Stream()
+    with torch.cuda.stream(ps):
+        for i in range(P + 2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(ps)
+            r.upload_silhouettes(0, masks[i % F])
+            r.reconstruct([0])
+            r.colour([0], rgb[i % F:i % F + 1], vps[i % F:i % F + 1])
+            b.record(ps)
+            b.synchronize()
+            if i >= 2:
+                lat.append(a.elapsed_time(b))
+    r.set_graphs(False)
+    torch.cuda.synchronize()
     plain_fps = len(lat) / (sum(lat) / 1000.0)
 
     # ---- per-stage times and roofline of the dominant kernel
@@ -337,6 +349,8 @@ def run_ours(args):
     if not args.no_e2e:
         masks_h = masks.cpu().pin_memory()
         rgb_h = rgb.cpu().pin_memory()
+        step()                      # the plain path reused slot 0: put the batch back before sizing outputs
+        torch.cuda.synchronize()
         cnt = [r.counts(i) for i in slots]
         outs = [dict(verts=torch.empty((c["n_verts"], 3), dtype=torch.float32).pin_memory(),
                      tris=torch.empty((c["n_tris"], 3), dtype=torch.int32).pin_memory(),
@@ -404,7 +418,8 @@ def run_ours(args):
             "gtests_per_s": world * tests / (ms / 1000.0) / 1e9,
             "tests_per_frame": tests / F,
             "plain": {"frames_per_s": plain_fps, "latency_ms_p50": float(np.percentile(lat, 50)),
-                      "latency_ms_p99": float(np.percentile(lat, 99)), "frames": len(lat)},
+                      "latency_ms_p99": float(np.percentile(lat, 99)), "frames": len(lat), "cuda_graph": True},
+            "tuning": tuning,
             "stages_ms_per_frame": {k: v / F for k, v in per_step.items()},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "gpu_launches": n_launch,
             "clocks": clk}

@@ -276,6 +276,37 @@ fvv_status fvv_set_timing(fvv_rig *rig, int enable);
  * fvv_set_timing; then start a new accumulation. */
 fvv_status fvv_get_timing(fvv_rig *rig, float *ms, int *calls);
 
+/* Launch shapes of the five heaviest kernels, chosen per rig by fvv_autotune
+ * (results never depend on them). */
+enum {
+    FVV_TUNE_COARSE = 0,     /* coarse hull                     */
+    FVV_TUNE_FINE = 1,       /* fine hull                       */
+    FVV_TUNE_BISECT = 2,     /* bisection                       */
+    FVV_TUNE_ZBUFFER = 3,    /* depth images                    */
+    FVV_TUNE_TRIANGLES = 4,  /* marching-cubes triangles        */
+    FVV_N_TUNE = 5
+};
+
+/* Time candidate launch shapes (threads per block 64/128/256 x resident
+ * blocks per SM 2/4/8/16/32) of each tunable kernel on the given slots, which
+ * must hold reconstructed frames, keep the fastest, then reconstruct the
+ * slots once more with it so that their results and counts are those of one
+ * reconstruction.  Synchronises `stream`.  config (may be NULL) receives
+ * 2*FVV_N_TUNE ints: threads per block of each kernel, then blocks per SM. */
+fvv_status fvv_autotune(fvv_rig *rig, const int *slots, int n_slots, void *stream, int *config);
+
+/* Read or set the launch shapes (2*FVV_N_TUNE ints as for fvv_autotune);
+ * threads must be 32..256 in steps of 32 and blocks per SM 1..64. */
+fvv_status fvv_get_tuning(fvv_rig *rig, int *config);
+fvv_status fvv_set_tuning(fvv_rig *rig, const int *config);
+
+/* With graphs on (1), fvv_reconstruct records its launch sequence for each
+ * distinct slot list into a CUDA graph the first time it sees the list and
+ * replays that graph afterwards (up to 16 lists are kept).  Graphs are not
+ * used on the legacy default stream (NULL), nor while per-stage timing is on;
+ * a change of tuning drops them. */
+fvv_status fvv_set_graphs(fvv_rig *rig, int enable);
+
 /* The marching-cubes table the library built from its face rule: ntri[256]
  * triangle counts and edges[256*12*3] cube-edge numbers (corner c = dx + 2dy
  * + 4dz; cube edge e has axis e/4 and lower corner with the other two

@@ -33,6 +33,12 @@ struct fvv_rig {
     size_t events_used = 0;
     struct Interval { int stage; cudaEvent_t a, b; };
     std::vector<Interval> intervals;
+    Tuning tune = default_tuning();
+    // CUDA graphs of fvv_reconstruct, one per slot list (least recently used dropped)
+    bool graphs = false;
+    struct Graph { std::vector<int> slots; cudaGraphExec_t exec; unsigned long long used; };
+    std::vector<Graph> graph_cache;
+    unsigned long long graph_clock = 0;
 };
 
 namespace {
@@ -308,6 +314,7 @@ fvv_status fvv_destroy_rig(fvv_rig* rig) {
     if (!rig) return FVV_OK;
     cudaError_t e = cudaDeviceSynchronize();
     for (cudaEvent_t ev : rig->events) cudaEventDestroy(ev);
+    for (auto& gr : rig->graph_cache) cudaGraphExecDestroy(gr.exec);
     if (rig->own_arena) {
         cudaError_t f = cudaFree(rig->arena);
         if (e == cudaSuccess) e = f;
@@ -362,13 +369,10 @@ static fvv_status make_slot_list(fvv_rig* rig, const int* slots, int n_slots, in
     return FVV_OK;
 }
 
-fvv_status fvv_reconstruct(fvv_rig* rig, const int* slots, int n_slots, void* stream) {
-    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
-    SlotList sl;
-    fvv_status s = make_slot_list(rig, slots, n_slots, 1, sl);
-    if (s != FVV_OK) return s;
-    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+// The launch sequence of one reconstruction of the slots in `sl`.
+static cudaError_t enqueue_reconstruct(fvv_rig* rig, const SlotList& sl, cudaStream_t st) {
     const Grid& g = rig->grid;
+    const Tuning& tu = rig->tune;
     const McTable mc{rig->mc_ntri, rig->mc_edges};
     k_zero_info<<<sl.n, 32, 0, st>>>(rig->L, sl);
     cudaError_t e = cudaGetLastError();
@@ -379,16 +383,162 @@ fvv_status fvv_reconstruct(fvv_rig* rig, const int* slots, int n_slots, void* st
         e = (call);                             \
         stage_end(rig, t, st);                  \
     }
-    FVV_STAGE(FVV_STAGE_COARSE, launch_coarse_carve(rig->cams, g, rig->L, sl, rig->sms, st));
+    FVV_STAGE(FVV_STAGE_COARSE, launch_coarse_carve(rig->cams, g, rig->L, sl, rig->sms, tu, st));
     FVV_STAGE(FVV_STAGE_CCL, launch_ccl(g, rig->L, sl, rig->sms, st));
-    FVV_STAGE(FVV_STAGE_FINE, launch_fine_carve(rig->cams, g, rig->L, sl, rig->sms, st));
+    FVV_STAGE(FVV_STAGE_FINE, launch_fine_carve(rig->cams, g, rig->L, sl, rig->sms, tu, st));
     FVV_STAGE(FVV_STAGE_MC, launch_mc_prefix(g, rig->L, sl, mc, rig->sms, st));
-    FVV_STAGE(FVV_STAGE_BISECT, launch_bisect(rig->cams, g, rig->L, sl, rig->sms, st));
-    FVV_STAGE(FVV_STAGE_MC, launch_mc_triangles(g, rig->L, sl, mc, rig->sms, st));
-    FVV_STAGE(FVV_STAGE_DEPTH, launch_depth(rig->cams, g, rig->L, sl, rig->sms, align_up(rig->npix * 4), st));
+    FVV_STAGE(FVV_STAGE_BISECT, launch_bisect(rig->cams, g, rig->L, sl, rig->sms, tu, st));
+    FVV_STAGE(FVV_STAGE_MC, launch_mc_triangles(g, rig->L, sl, mc, rig->sms, tu, st));
+    FVV_STAGE(FVV_STAGE_DEPTH, launch_depth(rig->cams, g, rig->L, sl, rig->sms, align_up(rig->npix * 4), tu, st));
 #undef FVV_STAGE
+    return e;
+}
+
+static void drop_graphs(fvv_rig* rig) {
+    for (auto& gr : rig->graph_cache) cudaGraphExecDestroy(gr.exec);
+    rig->graph_cache.clear();
+}
+
+// Replay (or first record) the graph of this slot list on `st`.
+static cudaError_t launch_graph(fvv_rig* rig, const SlotList& sl, cudaStream_t st) {
+    std::vector<int> key(sl.s, sl.s + sl.n);
+    for (auto& gr : rig->graph_cache)
+        if (gr.slots == key) {
+            gr.used = ++rig->graph_clock;
+            return cudaGraphLaunch(gr.exec, st);
+        }
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t le = enqueue_reconstruct(rig, sl, st);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(st, &graph);
+    if (le != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return le != cudaSuccess ? le : e;
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    if (rig->graph_cache.size() >= 16) {
+        size_t lru = 0;
+        for (size_t i = 1; i < rig->graph_cache.size(); ++i)
+            if (rig->graph_cache[i].used < rig->graph_cache[lru].used) lru = i;
+        cudaGraphExecDestroy(rig->graph_cache[lru].exec);
+        rig->graph_cache.erase(rig->graph_cache.begin() + (long)lru);
+    }
+    rig->graph_cache.push_back({key, exec, ++rig->graph_clock});
+    return cudaGraphLaunch(exec, st);
+}
+
+fvv_status fvv_reconstruct(fvv_rig* rig, const int* slots, int n_slots, void* stream) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    SlotList sl;
+    fvv_status s = make_slot_list(rig, slots, n_slots, 1, sl);
+    if (s != FVV_OK) return s;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool use_graph = rig->graphs && !rig->timing && st != nullptr;
+    const cudaError_t e = use_graph ? launch_graph(rig, sl, st) : enqueue_reconstruct(rig, sl, st);
     if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_reconstruct launch");
     for (int i = 0; i < sl.n; ++i) rig->state[sl.s[i]] = 2;
+    return FVV_OK;
+}
+
+fvv_status fvv_set_graphs(fvv_rig* rig, int enable) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    rig->graphs = enable != 0;
+    if (!rig->graphs) {
+        cudaDeviceSynchronize();
+        drop_graphs(rig);
+    }
+    return FVV_OK;
+}
+
+fvv_status fvv_get_tuning(fvv_rig* rig, int* config) {
+    if (!rig || !config) return fail(rig, FVV_ERR_INVALID_ARG, "rig and config must not be NULL");
+    for (int k = 0; k < FVV_N_TUNE; ++k) {
+        config[k] = rig->tune.threads[k];
+        config[FVV_N_TUNE + k] = rig->tune.waves[k];
+    }
+    return FVV_OK;
+}
+
+fvv_status fvv_set_tuning(fvv_rig* rig, const int* config) {
+    if (!rig || !config) return fail(rig, FVV_ERR_INVALID_ARG, "rig and config must not be NULL");
+    for (int k = 0; k < FVV_N_TUNE; ++k) {
+        const int th = config[k], wv = config[FVV_N_TUNE + k];
+        if (th < 32 || th > 256 || th % 32 || wv < 1 || wv > 64)
+            return fail(rig, FVV_ERR_INVALID_ARG, "threads must be 32..256 in steps of 32, blocks per SM 1..64");
+    }
+    for (int k = 0; k < FVV_N_TUNE; ++k) {
+        rig->tune.threads[k] = config[k];
+        rig->tune.waves[k] = config[FVV_N_TUNE + k];
+    }
+    cudaDeviceSynchronize();
+    drop_graphs(rig);
+    return FVV_OK;
+}
+
+fvv_status fvv_autotune(fvv_rig* rig, const int* slots, int n_slots, void* stream, int* config) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    SlotList sl;
+    fvv_status s = make_slot_list(rig, slots, n_slots, 2, sl);
+    if (s != FVV_OK) return s;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool timing = rig->timing;
+    rig->timing = false;
+    const Grid& g = rig->grid;
+    const McTable mc{rig->mc_ntri, rig->mc_edges};
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    // one stage on its own, on the inputs the last reconstruction left
+    auto run = [&](int knob, const Tuning& tu) -> cudaError_t {
+        switch (knob) {
+            case FVV_TUNE_COARSE: return launch_coarse_carve(rig->cams, g, rig->L, sl, rig->sms, tu, st);
+            case FVV_TUNE_FINE: return launch_fine_carve(rig->cams, g, rig->L, sl, rig->sms, tu, st);
+            case FVV_TUNE_BISECT: return launch_bisect(rig->cams, g, rig->L, sl, rig->sms, tu, st);
+            case FVV_TUNE_ZBUFFER:
+                return launch_depth(rig->cams, g, rig->L, sl, rig->sms, align_up(rig->npix * 4), tu, st);
+            default: return launch_mc_triangles(g, rig->L, sl, mc, rig->sms, tu, st);
+        }
+    };
+    const int threads[] = {64, 128, 256};
+    const int waves[] = {2, 4, 8, 16, 32};
+    for (int knob = 0; knob < FVV_N_TUNE && e == cudaSuccess; ++knob) {
+        float best = 1e30f;
+        Tuning keep = rig->tune;
+        for (int th : threads)
+            for (int wv : waves) {
+                Tuning tu = rig->tune;
+                tu.threads[knob] = th;
+                tu.waves[knob] = wv;
+                e = run(knob, tu);  // warm
+                if (e == cudaSuccess) e = cudaEventRecord(a, st);
+                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = run(knob, tu);
+                if (e == cudaSuccess) e = cudaEventRecord(b, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                float ms = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+                if (e != cudaSuccess) break;
+                if (ms < best) {
+                    best = ms;
+                    keep.threads[knob] = th;
+                    keep.waves[knob] = wv;
+                }
+            }
+        rig->tune = keep;
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e == cudaSuccess) {
+        drop_graphs(rig);
+        e = enqueue_reconstruct(rig, sl, st);   // consistent results and counts again
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    rig->timing = timing;
+    if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_autotune");
+    if (config) fvv_get_tuning(rig, config);
     return FVV_OK;
 }
 

@@ -128,6 +128,31 @@ inline int grid_x(int sms, int n_slots, long long work_items, int per_block) {
     return (int)std::max(1LL, std::min(want, cap));
 }
 
+// Launch shape of the tunable kernels (index FVV_TUNE_*): threads per block
+// (a multiple of 32, <= 256) and resident blocks per SM over the whole batch.
+struct Tuning {
+    int threads[FVV_N_TUNE];
+    int waves[FVV_N_TUNE];
+};
+
+inline Tuning default_tuning() {
+    Tuning t;
+    for (int k = 0; k < FVV_N_TUNE; ++k) {
+        t.threads[k] = 256;
+        t.waves[k] = 8;
+    }
+    t.waves[FVV_TUNE_ZBUFFER] = 16;
+    return t;
+}
+
+// Blocks per slot of a tuned grid-stride kernel.
+inline int tuned_grid(const Tuning& tu, int knob, int sms, int n_slots, long long work_items, int parts = 1) {
+    const long long per_block = tu.threads[knob];
+    const long long want = (work_items + per_block - 1) / per_block;
+    const long long cap = std::max(1LL, (long long)sms * tu.waves[knob] / std::max(1, n_slots * parts));
+    return (int)std::max(1LL, std::min(want, cap));
+}
+
 // Builds the 256-case table from the face rule (host).
 void build_mc_table(uint8_t ntri[256], uint8_t edges[256 * kMaxTriPerCell * 3]);
 
@@ -135,18 +160,18 @@ void build_mc_table(uint8_t ntri[256], uint8_t edges[256 * kMaxTriPerCell * 3]);
 cudaError_t launch_pack(const CamSet& cams, const Layout& L, int slot, const uint8_t* const* src,
                         cudaStream_t st);
 cudaError_t launch_coarse_carve(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
-                                int sms, cudaStream_t st);
+                                int sms, const Tuning& tu, cudaStream_t st);
 cudaError_t launch_ccl(const Grid& g, const Layout& L, const SlotList& sl, int sms, cudaStream_t st);
 cudaError_t launch_fine_carve(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
-                              int sms, cudaStream_t st);
+                              int sms, const Tuning& tu, cudaStream_t st);
 cudaError_t launch_mc_prefix(const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc, int sms,
                              cudaStream_t st);
 cudaError_t launch_bisect(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,
-                          cudaStream_t st);
+                          const Tuning& tu, cudaStream_t st);
 cudaError_t launch_mc_triangles(const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc, int sms,
-                                cudaStream_t st);
+                                const Tuning& tu, cudaStream_t st);
 cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
-                         int sms, size_t depth_bytes, cudaStream_t st);
+                         int sms, size_t depth_bytes, const Tuning& tu, cudaStream_t st);
 // Colour-call arguments of up to kColourBatch slots, passed by value as a
 // kernel parameter (so nothing is copied from host memory).
 constexpr int kColourBatch = 48;

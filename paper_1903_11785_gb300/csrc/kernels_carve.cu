@@ -213,21 +213,23 @@ cudaError_t launch_pack(const CamSet& cams, const Layout& L, int slot, const uin
 }
 
 cudaError_t launch_coarse_carve(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,
-                                cudaStream_t st) {
+                                const Tuning& tu, cudaStream_t st) {
     const long long words = (long long)g.nz * g.ny * g.nxw;
-    const int gx = grid_x(sms, sl.n, words * 32, 256);
-#define FVV_LAUNCH(NC) k_coarse_carve<NC><<<dim3(gx, sl.n), 256, 0, st>>>(cams, g, L, sl)
+    const int th = tu.threads[FVV_TUNE_COARSE];
+    const int gx = tuned_grid(tu, FVV_TUNE_COARSE, sms, sl.n, words * 32);
+#define FVV_LAUNCH(NC) k_coarse_carve<NC><<<dim3(gx, sl.n), th, 0, st>>>(cams, g, L, sl)
     FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
     return cudaGetLastError();
 }
 
 cudaError_t launch_fine_carve(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,
-                              cudaStream_t st) {
+                              const Tuning& tu, cudaStream_t st) {
     const int gc = grid_x(sms, sl.n, (long long)g.max_fine_words, 256);
     k_clear_fine<<<dim3(gc, sl.n), 256, 0, st>>>(L, sl);
-    const int gx = grid_x(sms, sl.n, (long long)g.max_fine_words * 32, 256);
-#define FVV_LAUNCH(NC) k_fine_carve<NC><<<dim3(gx, sl.n), 256, 0, st>>>(cams, g, L, sl)
+    const int th = tu.threads[FVV_TUNE_FINE];
+    const int gx = tuned_grid(tu, FVV_TUNE_FINE, sms, sl.n, (long long)g.max_fine_words * 32);
+#define FVV_LAUNCH(NC) k_fine_carve<NC><<<dim3(gx, sl.n), th, 0, st>>>(cams, g, L, sl)
     FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
     return cudaGetLastError();

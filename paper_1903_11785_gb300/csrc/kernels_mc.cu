@@ -442,18 +442,19 @@ cudaError_t launch_mc_prefix(const Grid& g, const Layout& L, const SlotList& sl,
 }
 
 cudaError_t launch_bisect(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,
-                          cudaStream_t st) {
-    const int gv = grid_x(sms, sl.n, g.max_verts, 256);
-#define FVV_LAUNCH(NC) k_bisect<NC><<<dim3(gv, sl.n), 256, 0, st>>>(cams, g, L, sl)
+                          const Tuning& tu, cudaStream_t st) {
+    const int th = tu.threads[FVV_TUNE_BISECT];
+    const int gv = tuned_grid(tu, FVV_TUNE_BISECT, sms, sl.n, g.max_verts);
+#define FVV_LAUNCH(NC) k_bisect<NC><<<dim3(gv, sl.n), th, 0, st>>>(cams, g, L, sl)
     FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
     return cudaGetLastError();
 }
 
 cudaError_t launch_mc_triangles(const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc, int sms,
-                                cudaStream_t st) {
-    const int gw = grid_x(sms, sl.n, g.max_fine_words, 256);
-    k_mc_triangles<<<dim3(gw, sl.n), 256, 0, st>>>(L, sl, mc);
+                                const Tuning& tu, cudaStream_t st) {
+    const int gw = tuned_grid(tu, FVV_TUNE_TRIANGLES, sms, sl.n, g.max_fine_words);
+    k_mc_triangles<<<dim3(gw, sl.n), tu.threads[FVV_TUNE_TRIANGLES], 0, st>>>(L, sl, mc);
     return cudaGetLastError();
 }
 

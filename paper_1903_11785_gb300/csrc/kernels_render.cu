@@ -176,12 +176,12 @@ __global__ void k_debug_depth(const __grid_constant__ Layout L, int slot, float*
 }  // namespace
 
 cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,
-                         size_t depth_bytes, cudaStream_t st) {
+                         size_t depth_bytes, const Tuning& tu, cudaStream_t st) {
     const size_t n16 = depth_bytes / 16;
     const int gc = grid_x(sms, sl.n, (long long)n16, 256);
     k_clear_depth<<<dim3(gc, sl.n), 256, 0, st>>>(L, sl, n16);
-    const int gz = std::max(1, grid_x(sms, sl.n, (long long)g.max_tris, 256) / std::max(1, cams.n / 2));
-    k_zbuffer<<<dim3(gz, sl.n, cams.n), 256, 0, st>>>(cams, L, sl);
+    const int gz = tuned_grid(tu, FVV_TUNE_ZBUFFER, sms, sl.n, (long long)g.max_tris, cams.n);
+    k_zbuffer<<<dim3(gz, sl.n, cams.n), tu.threads[FVV_TUNE_ZBUFFER], 0, st>>>(cams, L, sl);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,13 @@ FVV_MAX_CAMS, FVV_MAX_BATCH = 64, 256
 FVV_DEBUG_SIL_BITS, FVV_DEBUG_COARSE_BITS, FVV_DEBUG_LABELS, FVV_DEBUG_FINE_BITS, FVV_DEBUG_DEPTH = range(5)
 FLAG_NAMES = {1: "ROOTS", 2: "ROIS", 4: "FINE", 8: "VERTS", 16: "TRIS", 32: "LOOP"}
 STAGES = ("pack", "coarse", "ccl", "fine", "mc", "bisect", "depth", "colour")
+TUNE_KNOBS = ("coarse", "fine", "bisect", "zbuffer", "triangles")
+N_TUNE = len(TUNE_KNOBS)
+
+
+def tuning_dict(cfg):
+    """{kernel: (threads per block, blocks per SM)} from the flat C layout."""
+    return {k: (cfg[i], cfg[N_TUNE + i]) for i, k in enumerate(TUNE_KNOBS)}
 
 
 class RigDesc(C.Structure):
@@ -80,6 +87,10 @@ _sigs = {
     "fvv_debug_pixels": ([_vp, C.c_int, C.c_longlong, _vp, _vp, _vp, _vp], C.c_int),
     "fvv_label_components_noalloc": ([_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp], C.c_int),
     "fvv_set_timing": ([_vp, C.c_int], C.c_int),
+    "fvv_autotune": ([_vp, C.POINTER(C.c_int), C.c_int, _vp, C.POINTER(C.c_int)], C.c_int),
+    "fvv_get_tuning": ([_vp, C.POINTER(C.c_int)], C.c_int),
+    "fvv_set_tuning": ([_vp, C.POINTER(C.c_int)], C.c_int),
+    "fvv_set_graphs": ([_vp, C.c_int], C.c_int),
     "fvv_get_timing": ([_vp, C.POINTER(C.c_float), C.POINTER(C.c_int)], C.c_int),
     "fvv_last_error": ([_vp], C.c_char_p),
     "fvv_status_string": ([C.c_int], C.c_char_p),
@@ -311,3 +322,22 @@ class Rig:
 
     def timing(self):
         return fvv_get_timing(self.ptr)
+
+    def autotune(self, slots, stream=None):
+        """Pick the fastest launch shapes on reconstructed slots; returns them."""
+        arr = (C.c_int * len(slots))(*slots)
+        cfg = (C.c_int * (2 * N_TUNE))()
+        _check(_lib.fvv_autotune(self.ptr, arr, len(slots), _stream(stream), cfg), self.ptr)
+        return tuning_dict(list(cfg))
+
+    def get_tuning(self):
+        cfg = (C.c_int * (2 * N_TUNE))()
+        _check(_lib.fvv_get_tuning(self.ptr, cfg), self.ptr)
+        return tuning_dict(list(cfg))
+
+    def set_tuning(self, tuning):
+        cfg = [tuning[k][0] for k in TUNE_KNOBS] + [tuning[k][1] for k in TUNE_KNOBS]
+        _check(_lib.fvv_set_tuning(self.ptr, (C.c_int * len(cfg))(*cfg)), self.ptr)
+
+    def set_graphs(self, enable=True):
+        _check(_lib.fvv_set_graphs(self.ptr, int(enable)), self.ptr)
