@@ -31,50 +31,89 @@ __device__ __forceinline__ float rcp_approx(float w) {
     return r;
 }
 
-// floor(x / w) of the exact quotient, clamped to [-1, n] (w > 0, n < 2^22):
-// k0 = trunc(clamp(x * rcp(w), 0, n)) is within one of the answer whenever
-// the answer is in [0, n]; the signs of the residuals x - k0 w and
-// x - (k0 + 1) w, each formed by one FMA and so exact in sign, move it to
-// the answer (or out of [0, n) when the quotient is outside).  No branch and
-// no conversion instruction: the integer part is taken by a round-toward-zero
+// floor(x / w) of the exact quotient, clamped to [-1, n + 1] (w > 0,
+// n < 2^22): k0 = trunc(clamp(x * rcp(w), 0, n)) is within one of the answer
+// whenever the answer is in [0, n]; the residual r0 = x - k0 w, formed by one
+// FMA, is exact when |r0| < w and rounds monotonically otherwise, so r0 < 0
+// means k0 is one too big and r0 >= w means one too small (or the quotient
+// is outside [0, n), which the result then shows).  No branch and no
+// conversion instruction: the integer part comes from a round-toward-zero
 // add of 2^23.
 __device__ __forceinline__ int pixel_floor(float x, float w, float r, float n) {
     const float q = fminf(fmaxf(fmul(x, r), 0.0f), n);
     const float t = __fadd_rz(q, 8388608.0f);   // 2^23 + trunc(q)
     const float k0 = fsub(t, 8388608.0f);
     const float r0 = __fmaf_rn(-k0, w, x);
-    const float r1 = __fmaf_rn(-fadd(k0, 1.0f), w, x);
-    return (__float_as_int(t) - 0x4B000000) - (r0 < 0.0f ? 1 : 0) + (r1 >= 0.0f ? 1 : 0);
+    return (__float_as_int(t) - 0x4B000000) - (r0 < 0.0f ? 1 : 0) + (r0 >= w ? 1 : 0);
 }
 
-// One camera's vote for a world point (Sec. II-B-1: project the voxel onto
-// the silhouette): 1 foreground, 0 background, -1 abstain.  The pixel is
+// Silhouette bit of camera c at the pixel holding world point (X,Y,Z)
+// (Sec. II-B-1: project the voxel onto the silhouette): the pixel is
 // (floor(x'/w'), floor(y'/w')) of the exact quotients of the binary32
-// homogeneous coordinates; a point behind the camera or outside the image
-// votes background under FVV_OOB_STRICT and abstains otherwise.
-__device__ __forceinline__ int cam_vote(const Cam& c, int oob, const uint32_t* __restrict__ sil, float X,
-                                        float Y, float Z) {
+// homogeneous coordinates.  `in` says whether the point is in front of the
+// camera and inside its image; the bit is 0 when it is not.
+__device__ __forceinline__ uint32_t cam_bit(const Cam& c, const uint32_t* __restrict__ sil, float X, float Y,
+                                            float Z, bool& in) {
     float xp, yp, wp;
     project(c.P, X, Y, Z, xp, yp, wp);
     const float r = rcp_approx(wp);
     const int px = pixel_floor(xp, wp, r, c.Wf);
     const int py = pixel_floor(yp, wp, r, c.Hf);
-    const bool in = wp > 0.0f && px >= 0 && px < c.W && py >= 0 && py < c.H;
-    const unsigned ix = in ? (unsigned)px : 0u, iy = in ? (unsigned)py : 0u;
-    const uint32_t word = in ? __ldg(sil + c.bit_off + iy * (unsigned)c.Wq + (ix >> 5)) : 0u;
-    const int off = oob == FVV_OOB_ABSTAIN ? -1 : 0;
-    return in ? (int)((word >> (ix & 31)) & 1u) : off;
+    in = wp > 0.0f && (unsigned)px < (unsigned)c.W && (unsigned)py < (unsigned)c.H;
+    const uint32_t word = in ? __ldg(sil + c.bit_off + (unsigned)py * (unsigned)c.Wq + ((unsigned)px >> 5)) : 0u;
+    return (word >> (px & 31)) & 1u;
 }
 
 // The pixel a point falls in for camera c, or -1 in px/py if none (behind the
-// camera or outside the image).  Same arithmetic as cam_vote.
+// camera or outside the image).  Same arithmetic as cam_bit.
 __device__ __forceinline__ void cam_pixel(const Cam& c, float X, float Y, float Z, int& px, int& py) {
     float xp, yp, wp;
     project(c.P, X, Y, Z, xp, yp, wp);
     const float r = rcp_approx(wp);
     px = pixel_floor(xp, wp, r, c.Wf);
     py = pixel_floor(yp, wp, r, c.Hf);
-    if (!(wp > 0.0f && px >= 0 && px < c.W && py >= 0 && py < c.H)) px = py = -1;
+    if (!(wp > 0.0f && (unsigned)px < (unsigned)c.W && (unsigned)py < (unsigned)c.H)) px = py = -1;
+}
+
+// One camera's test of a live lane.  STRICT: a camera that does not see the
+// point votes background, so the lane stays alive only on a foreground bit.
+// ABSTAIN: such a camera does not vote; the lane must see one foreground vote.
+template <bool ABSTAIN>
+__device__ __forceinline__ void test_cam(const Cam& c, const uint32_t* __restrict__ sil, float X, float Y, float Z,
+                                         bool& alive, bool& voted) {
+    bool in;
+    const uint32_t bit = cam_bit(c, sil, X, Y, Z, in);
+    if constexpr (ABSTAIN) {
+        alive = !in || bit;
+        voted |= in && bit;
+    } else {
+        alive = bit != 0u;
+    }
+}
+
+template <int NC, bool ABSTAIN>
+__device__ __forceinline__ bool warp_test_p(const CamSet& cams, const uint32_t* __restrict__ sil, float X, float Y,
+                                            float Z, bool alive, uint32_t& tests) {
+    bool voted = !ABSTAIN;
+    if constexpr (NC > 0) {
+#pragma unroll
+        for (int n = 0; n < NC; ++n) {
+            if (!__any_sync(kFull, alive)) break;
+            if (alive) {
+                ++tests;
+                test_cam<ABSTAIN>(cams.c[n], sil, X, Y, Z, alive, voted);
+            }
+        }
+    } else {
+        for (int n = 0; n < cams.n; ++n) {
+            if (!__any_sync(kFull, alive)) break;
+            if (alive) {
+                ++tests;
+                test_cam<ABSTAIN>(cams.c[n], sil, X, Y, Z, alive, voted);
+            }
+        }
+    }
+    return alive && voted;
 }
 
 // Occupancy of the 32 points of a warp (one per lane; lanes with alive ==
@@ -86,30 +125,8 @@ __device__ __forceinline__ void cam_pixel(const Cam& c, float X, float Y, float 
 template <int NC>
 __device__ __forceinline__ bool warp_test(const CamSet& cams, const uint32_t* __restrict__ sil, float X, float Y,
                                           float Z, bool alive, uint32_t& tests) {
-    bool voted = false;
-    if constexpr (NC > 0) {
-#pragma unroll
-        for (int n = 0; n < NC; ++n) {
-            if (!__any_sync(kFull, alive)) break;
-            if (alive) {
-                ++tests;
-                const int v = cam_vote(cams.c[n], cams.oob, sil, X, Y, Z);
-                alive = v != 0;
-                voted |= (v == 1);
-            }
-        }
-    } else {
-        for (int n = 0; n < cams.n; ++n) {
-            if (!__any_sync(kFull, alive)) break;
-            if (alive) {
-                ++tests;
-                const int v = cam_vote(cams.c[n], cams.oob, sil, X, Y, Z);
-                alive = v != 0;
-                voted |= (v == 1);
-            }
-        }
-    }
-    return alive && voted;
+    return cams.oob == FVV_OOB_ABSTAIN ? warp_test_p<NC, true>(cams, sil, X, Y, Z, alive, tests)
+                                       : warp_test_p<NC, false>(cams, sil, X, Y, Z, alive, tests);
 }
 
 // Camera counts with an unrolled instantiation of the hull-test kernels
@@ -124,20 +141,6 @@ __device__ __forceinline__ bool warp_test(const CamSet& cams, const uint32_t* __
         case 16: F(16); break;  \
         default: F(0); break;   \
     }
-
-// Occupancy of one point, cameras in index order with exit at the first
-// background vote; `tests` counts the camera tests made.
-__device__ __forceinline__ bool point_on(const CamSet& cams, const uint32_t* __restrict__ sil, float X,
-                                         float Y, float Z, uint32_t& tests) {
-    bool voted = false;
-    for (int n = 0; n < cams.n; ++n) {
-        ++tests;
-        const int v = cam_vote(cams.c[n], cams.oob, sil, X, Y, Z);
-        if (v == 0) return false;
-        voted |= (v == 1);
-    }
-    return voted;
-}
 
 // The ROI holding fine word w: the last ROI whose first word is <= w.
 __device__ __forceinline__ int roi_of_word(const DRoi* rois, int n, uint32_t w) {
