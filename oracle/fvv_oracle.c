@@ -749,11 +749,19 @@ int orc_mesh_one(const orc_rig *rig, const uint8_t *const *masks, const orc_roi 
 
 /* For camera n, every triangle whose three vertices are in front of it
  * (w' > 0) and whose projected area is non-zero writes, into each pixel whose
- * centre (px+1/2, py+1/2) lies inside or on it (the three edge functions all
- * >= 0 or all <= 0), the distance from its centroid ((v0+v1)+v2)/3 to the
- * camera centre; each pixel keeps the minimum (Eq. (4)); a pixel no triangle
- * covers stays +infinity.  Only pixel centres inside the closed box
- * [min u, max u] x [min v, max v] of the projected triangle are tested. */
+ * centre p = (px+1/2, py+1/2) lies inside or on it, the distance from its
+ * centroid ((v0+v1)+v2)/3 to the camera centre; each pixel keeps the minimum
+ * (Eq. (4)); a pixel no triangle covers stays +infinity.
+ * The test is made on the homogeneous image points (x', y', w') of the
+ * vertices, without dividing: for edge (i, j) the edge function at p is
+ * (p_x a - p_y b) + c with a = y_i w_j - w_i y_j, b = x_i w_j - w_i x_j,
+ * c = x_i y_j - y_i x_j (binary32, in that order) -- the determinant of the
+ * two vertices and p, whose sign for w > 0 is that of the image-plane edge
+ * function.  p is inside or on the triangle iff the three are all >= 0 or
+ * all <= 0.  The projected area is zero iff (x_0 a_12 - y_0 b_12) + w_0 c_12
+ * is.  Only pixel centres inside the closed box spanned by the projected
+ * vertices are tested; that box is decided exactly, by the signs of
+ * p_x w_j - x_j (and p_y w_j - y_j) formed with one fma each. */
 int orc_depth(const orc_rig *rig, long long n_verts, const double *verts,
               long long n_tris, const uint32_t *tris, R *depth)
 {
@@ -766,53 +774,62 @@ int orc_depth(const orc_rig *rig, long long n_verts, const double *verts,
         const float *p = rig->P + 12 * n;
         R Cx = (R)rig->centre[3 * n], Cy = (R)rig->centre[3 * n + 1], Cz = (R)rig->centre[3 * n + 2];
         for (long long t = 0; t < n_tris; ++t) {
-            R U[3], V[3], X[3], Y[3], Z[3];
+            R X[3], Y[3], Z[3], xh[3], yh[3], wh[3];
             int ok = 1;
             for (int j = 0; j < 3; ++j) {
                 uint32_t vi = tris[3 * t + j];
                 if ((long long)vi >= n_verts) return -1;
                 X[j] = (R)verts[3 * vi]; Y[j] = (R)verts[3 * vi + 1]; Z[j] = (R)verts[3 * vi + 2];
-                R xp = (((R)p[0] * X[j] + (R)p[1] * Y[j]) + (R)p[2] * Z[j]) + (R)p[3];
-                R yp = (((R)p[4] * X[j] + (R)p[5] * Y[j]) + (R)p[6] * Z[j]) + (R)p[7];
-                R wp = (((R)p[8] * X[j] + (R)p[9] * Y[j]) + (R)p[10] * Z[j]) + (R)p[11];
-                if (!(wp > (R)0)) { ok = 0; break; }
-                U[j] = xp / wp;
-                V[j] = yp / wp;
+                xh[j] = (((R)p[0] * X[j] + (R)p[1] * Y[j]) + (R)p[2] * Z[j]) + (R)p[3];
+                yh[j] = (((R)p[4] * X[j] + (R)p[5] * Y[j]) + (R)p[6] * Z[j]) + (R)p[7];
+                wh[j] = (((R)p[8] * X[j] + (R)p[9] * Y[j]) + (R)p[10] * Z[j]) + (R)p[11];
+                if (!(wh[j] > (R)0)) { ok = 0; break; }
             }
             if (!ok) continue;
-            R area = (U[1] - U[0]) * (V[2] - V[0]) - (V[1] - V[0]) * (U[2] - U[0]);
-            if (!(area > (R)0 || area < (R)0)) continue;
+            /* homogeneous edge functions of edges (0,1), (1,2), (2,0) */
+            R ea[3], eb[3], ec[3];
+            for (int e = 0; e < 3; ++e) {
+                int i = e, j = (e + 1) % 3;
+                ea[e] = yh[i] * wh[j] - wh[i] * yh[j];
+                eb[e] = xh[i] * wh[j] - wh[i] * xh[j];
+                ec[e] = xh[i] * yh[j] - yh[i] * xh[j];
+            }
+            R det = (xh[0] * ea[1] - yh[0] * eb[1]) + wh[0] * ec[1];
+            if (!(det > (R)0 || det < (R)0)) continue;
             R gx = ((X[0] + X[1]) + X[2]) / (R)3;
             R gy = ((Y[0] + Y[1]) + Y[2]) / (R)3;
             R gz = ((Z[0] + Z[1]) + Z[2]) / (R)3;
             R dx = gx - Cx, dy = gy - Cy, dz = gz - Cz;
             R d = sqrt((dx * dx + dy * dy) + dz * dz);
-            R umin = U[0], umax = U[0], vmin = V[0], vmax = V[0];
-            for (int j = 1; j < 3; ++j) {
-                if (U[j] < umin) umin = U[j];
-                if (U[j] > umax) umax = U[j];
-                if (V[j] < vmin) vmin = V[j];
-                if (V[j] > vmax) vmax = V[j];
+            /* candidate pixels: the projected box widened by one pixel (any
+             * superset of the box gives the same image) */
+            double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
+            for (int j = 0; j < 3; ++j) {
+                double u = (double)xh[j] / (double)wh[j], v = (double)yh[j] / (double)wh[j];
+                if (u < umin) umin = u;
+                if (u > umax) umax = u;
+                if (v < vmin) vmin = v;
+                if (v > vmax) vmax = v;
             }
-            /* candidate pixels: a generous integer range, each then checked
-             * against the closed box with exact comparisons */
-            if (!(umax >= (R)0.5) || !(vmax >= (R)0.5)) continue;
-            if (!(umin <= (R)W - (R)0.5) || !(vmin <= (R)H - (R)0.5)) continue;
-            int x0 = umin < (R)0 ? 0 : (int)floor(umin);
-            int y0 = vmin < (R)0 ? 0 : (int)floor(vmin);
-            int x1 = umax > (R)W ? W - 1 : (int)floor(umax);
-            int y1 = vmax > (R)H ? H - 1 : (int)floor(vmax);
-            if (x1 > W - 1) x1 = W - 1;
-            if (y1 > H - 1) y1 = H - 1;
+            if (umax < 0.0 || vmax < 0.0 || umin > (double)W || vmin > (double)H) continue;
+            int x0 = umin < 1.0 ? 0 : (int)floor(umin) - 1;
+            int y0 = vmin < 1.0 ? 0 : (int)floor(vmin) - 1;
+            int x1 = umax > (double)W - 2.0 ? W - 1 : (int)floor(umax) + 1;
+            int y1 = vmax > (double)H - 2.0 ? H - 1 : (int)floor(vmax) + 1;
             for (int yy = y0; yy <= y1; ++yy) {
                 R pcy = (R)yy + (R)0.5;
-                if (pcy < vmin || pcy > vmax) continue;
+                /* pcy within [min v_j, max v_j]: signs of pcy*w_j - y_j, exact by one fma */
+                R s0 = fma(pcy, wh[0], -yh[0]), s1 = fma(pcy, wh[1], -yh[1]), s2 = fma(pcy, wh[2], -yh[2]);
+                if (!((s0 >= (R)0 || s1 >= (R)0 || s2 >= (R)0) && (s0 <= (R)0 || s1 <= (R)0 || s2 <= (R)0)))
+                    continue;
                 for (int xx = x0; xx <= x1; ++xx) {
                     R pcx = (R)xx + (R)0.5;
-                    if (pcx < umin || pcx > umax) continue;
-                    R e0 = (U[1] - U[0]) * (pcy - V[0]) - (V[1] - V[0]) * (pcx - U[0]);
-                    R e1 = (U[2] - U[1]) * (pcy - V[1]) - (V[2] - V[1]) * (pcx - U[1]);
-                    R e2 = (U[0] - U[2]) * (pcy - V[2]) - (V[0] - V[2]) * (pcx - U[2]);
+                    R r0 = fma(pcx, wh[0], -xh[0]), r1 = fma(pcx, wh[1], -xh[1]), r2 = fma(pcx, wh[2], -xh[2]);
+                    if (!((r0 >= (R)0 || r1 >= (R)0 || r2 >= (R)0) && (r0 <= (R)0 || r1 <= (R)0 || r2 <= (R)0)))
+                        continue;
+                    R e0 = (pcx * ea[0] - pcy * eb[0]) + ec[0];
+                    R e1 = (pcx * ea[1] - pcy * eb[1]) + ec[1];
+                    R e2 = (pcx * ea[2] - pcy * eb[2]) + ec[2];
                     int inside = (e0 >= (R)0 && e1 >= (R)0 && e2 >= (R)0) ||
                                  (e0 <= (R)0 && e1 <= (R)0 && e2 <= (R)0);
                     if (!inside) continue;

@@ -22,44 +22,69 @@ __global__ void __launch_bounds__(256) k_clear_depth(const __grid_constant__ Lay
 // Eq. (4) for one triangle (world vertices X, Y, Z, squared centroid-camera
 // distance d2 as float bits) in camera c.  The triangle is skipped if a vertex
 // is not in front of the camera (w' <= 0) or its projected area is zero; its
-// value goes into each pixel whose centre lies in the closed box of the
+// value goes into each pixel whose centre p lies in the closed box of the
 // projection and on the inner side of (or on) all three edges, either winding.
+// Everything is decided on the homogeneous image points (x', y', w') without
+// dividing: the edge function of edge (i, j) at p is (p_x a - p_y b) + c with
+// a = y_i w_j - w_i y_j, b = x_i w_j - w_i x_j, c = x_i y_j - y_i x_j (its
+// sign is the image-plane one for w > 0), the area is zero iff
+// (x_0 a_12 - y_0 b_12) + w_0 c_12 is, and the box test uses the exact signs
+// of p w_j - x_j from one FMA each.
 // The buffer keeps the minimum of the squared distance: sqrt is monotone, so
 // the square root of that minimum is the minimum distance itself, taken
 // where the depth is read.
 __device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const float* Y, const float* Z, uint32_t d2,
                                            uint32_t* __restrict__ depth) {
-    float U[3], V[3];
+    float xh[3], yh[3], wh[3];
     bool ok = true;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        float xp, yp, wp;
-        project(c.P, X[j], Y[j], Z[j], xp, yp, wp);
-        ok &= wp > 0.0f;
-        U[j] = __fdiv_rn(xp, wp);
-        V[j] = __fdiv_rn(yp, wp);
+        project(c.P, X[j], Y[j], Z[j], xh[j], yh[j], wh[j]);
+        ok &= wh[j] > 0.0f;
     }
     if (!ok) return;
-    const float area = fsub(fmul(fsub(U[1], U[0]), fsub(V[2], V[0])), fmul(fsub(V[1], V[0]), fsub(U[2], U[0])));
-    if (!(area > 0.0f || area < 0.0f)) return;
-    const float umin = fminf(fminf(U[0], U[1]), U[2]), umax = fmaxf(fmaxf(U[0], U[1]), U[2]);
-    const float vmin = fminf(fminf(V[0], V[1]), V[2]), vmax = fmaxf(fmaxf(V[0], V[1]), V[2]);
-    if (!(umax >= 0.5f) || !(vmax >= 0.5f)) return;
-    if (!(umin <= fsub(c.Wf, 0.5f)) || !(vmin <= fsub(c.Hf, 0.5f))) return;
-    const int x0 = umin < 0.0f ? 0 : (int)floorf(umin);
-    const int y0 = vmin < 0.0f ? 0 : (int)floorf(vmin);
-    const int x1 = umax > c.Wf ? c.W - 1 : min((int)floorf(umax), c.W - 1);
-    const int y1 = vmax > c.Hf ? c.H - 1 : min((int)floorf(vmax), c.H - 1);
+    // homogeneous edge functions of edges (0,1), (1,2), (2,0): no division
+    float ea[3], eb[3], ec[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int i = e, j = (e + 1) % 3;
+        ea[e] = fsub(fmul(yh[i], wh[j]), fmul(wh[i], yh[j]));
+        eb[e] = fsub(fmul(xh[i], wh[j]), fmul(wh[i], xh[j]));
+        ec[e] = fsub(fmul(xh[i], yh[j]), fmul(yh[i], xh[j]));
+    }
+    const float det = fadd(fsub(fmul(xh[0], ea[1]), fmul(yh[0], eb[1])), fmul(wh[0], ec[1]));
+    if (!(det > 0.0f || det < 0.0f)) return;
+    // candidate pixels: centres within 1/64 px of the box of the approximate
+    // projections (their error is below 1e-3 px for images up to 65535 px;
+    // the exact box test below decides)
+    float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float r = rcp_approx(wh[j]);
+        const float u = fmul(xh[j], r), v = fmul(yh[j], r);
+        umin = fminf(umin, u); umax = fmaxf(umax, u);
+        vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
+    }
+    constexpr float kSlack = 0.5f + 1.0f / 64.0f;
+    if (!(umax >= 0.0f && vmax >= 0.0f && umin <= c.Wf && vmin <= c.Hf)) return;
+    const int x0 = max(0, (int)ceilf(fsub(umin, kSlack)));
+    const int y0 = max(0, (int)ceilf(fsub(vmin, kSlack)));
+    const int x1 = umax > c.Wf ? c.W - 1 : min(c.W - 1, (int)floorf(fsub(fadd(umax, 1.0f / 64.0f), 0.5f)));
+    const int y1 = vmax > c.Hf ? c.H - 1 : min(c.H - 1, (int)floorf(fsub(fadd(vmax, 1.0f / 64.0f), 0.5f)));
     uint32_t* D = depth + c.pix_off;
     for (int yy = y0; yy <= y1; ++yy) {
         const float pcy = fadd((float)yy, 0.5f);
-        if (pcy < vmin || pcy > vmax) continue;
+        const float s0 = __fmaf_rn(pcy, wh[0], -yh[0]), s1 = __fmaf_rn(pcy, wh[1], -yh[1]),
+                    s2 = __fmaf_rn(pcy, wh[2], -yh[2]);
+        if (!((s0 >= 0.0f || s1 >= 0.0f || s2 >= 0.0f) && (s0 <= 0.0f || s1 <= 0.0f || s2 <= 0.0f))) continue;
         for (int xx = x0; xx <= x1; ++xx) {
             const float pcx = fadd((float)xx, 0.5f);
-            if (pcx < umin || pcx > umax) continue;
-            const float e0 = fsub(fmul(fsub(U[1], U[0]), fsub(pcy, V[0])), fmul(fsub(V[1], V[0]), fsub(pcx, U[0])));
-            const float e1 = fsub(fmul(fsub(U[2], U[1]), fsub(pcy, V[1])), fmul(fsub(V[2], V[1]), fsub(pcx, U[1])));
-            const float e2 = fsub(fmul(fsub(U[0], U[2]), fsub(pcy, V[2])), fmul(fsub(V[0], V[2]), fsub(pcx, U[2])));
+            const float r0 = __fmaf_rn(pcx, wh[0], -xh[0]), r1 = __fmaf_rn(pcx, wh[1], -xh[1]),
+                        r2 = __fmaf_rn(pcx, wh[2], -xh[2]);
+            if (!((r0 >= 0.0f || r1 >= 0.0f || r2 >= 0.0f) && (r0 <= 0.0f || r1 <= 0.0f || r2 <= 0.0f))) continue;
+            const float e0 = fadd(fsub(fmul(pcx, ea[0]), fmul(pcy, eb[0])), ec[0]);
+            const float e1 = fadd(fsub(fmul(pcx, ea[1]), fmul(pcy, eb[1])), ec[1]);
+            const float e2 = fadd(fsub(fmul(pcx, ea[2]), fmul(pcy, eb[2])), ec[2]);
             const bool in = (e0 >= 0.0f && e1 >= 0.0f && e2 >= 0.0f) || (e0 <= 0.0f && e1 <= 0.0f && e2 <= 0.0f);
             if (in) {
                 uint32_t* p = D + (size_t)yy * (unsigned)c.W + xx;
@@ -69,14 +94,15 @@ __device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const f
     }
 }
 
-// Grid (blocks, slots, cameras): the camera is uniform over a block, so its
-// matrix is read through uniform registers.  One thread per triangle; the
-// centroid ((v0 + v1) + v2) / 3 was formed once per triangle when the
-// triangle was emitted.
+// Grid (blocks, cameras, slots): the camera is uniform over a block, so its
+// matrix is read through uniform registers, and blocks are issued frame by
+// frame, so one frame's depth images are worked on together.  One thread per
+// triangle; the centroid ((v0 + v1) + v2) / 3 was formed once per triangle
+// when the triangle was emitted.
 __global__ void __launch_bounds__(256) k_zbuffer(const __grid_constant__ CamSet cams, const __grid_constant__ Layout L,
                                                  const __grid_constant__ SlotList sl) {
-    const int slot = sl.s[blockIdx.y];
-    const Cam& c = cams.c[blockIdx.z];
+    const int slot = sl.s[blockIdx.z];
+    const Cam& c = cams.c[blockIdx.y];
     const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
     const uint32_t nt = info->n_words ? info->n_tris : 0u;
     const float* verts = slot_ptr<float>(L, slot, L.verts);
@@ -181,7 +207,7 @@ cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, con
     const int gc = grid_x(sms, sl.n, (long long)n16, 256);
     k_clear_depth<<<dim3(gc, sl.n), 256, 0, st>>>(L, sl, n16);
     const int gz = tuned_grid(tu, FVV_TUNE_ZBUFFER, sms, sl.n, (long long)g.max_tris, cams.n);
-    k_zbuffer<<<dim3(gz, sl.n, cams.n), tu.threads[FVV_TUNE_ZBUFFER], 0, st>>>(cams, L, sl);
+    k_zbuffer<<<dim3(gz, cams.n, sl.n), tu.threads[FVV_TUNE_ZBUFFER], 0, st>>>(cams, L, sl);
     return cudaGetLastError();
 }
 

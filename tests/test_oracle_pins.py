@@ -468,6 +468,53 @@ def test_depth_matches_brute_force():
     assert np.isfinite(D).sum() > 50
 
 
+def test_depth_perspective_matches_exact_geometry():
+    """Perspective view, random triangles of a few pixels: the binary32
+    homogeneous coverage test agrees with exact (float64) image-plane
+    geometry except at pixel centres within 1e-3 px of a triangle edge."""
+    rig = make_rig("tiny")
+    rng = np.random.default_rng(3)
+    n = 0
+    C = rig.C64[n]
+    base = np.array([0.2, -0.3, 1.0])
+    tris = []
+    verts = []
+    for t in range(300):
+        c = base + rng.normal(0, 0.5, 3)
+        for k in range(3):
+            verts.append(c + rng.normal(0, 0.02, 3))
+        tris.append([3 * t, 3 * t + 1, 3 * t + 2])
+    verts = np.array(verts, np.float32).astype(np.float64)
+    tris = np.array(tris, np.uint32)
+    D = Oracle(rig).depth(verts, tris)[n]
+    W, H = int(rig.width[n]), int(rig.height[n])
+    P = rig.P[n].astype(np.float64)
+    hv = np.concatenate([verts, np.ones((len(verts), 1))], 1) @ P.T
+    uv = hv[:, :2] / hv[:, 2:3]
+    cover = np.zeros((H, W), bool)
+    near_edge = np.zeros((H, W), bool)
+    for t in tris:
+        q = uv[t]
+        x0, x1 = int(max(0, np.floor(q[:, 0].min()) - 1)), int(min(W - 1, np.ceil(q[:, 0].max()) + 1))
+        y0, y1 = int(max(0, np.floor(q[:, 1].min()) - 1)), int(min(H - 1, np.ceil(q[:, 1].max()) + 1))
+        ys, xs = np.mgrid[y0:y1 + 1, x0:x1 + 1]
+        px, py = xs + 0.5, ys + 0.5
+        e, dist = [], []
+        for i in range(3):
+            a, b = q[i], q[(i + 1) % 3]
+            ei = (b[0] - a[0]) * (py - a[1]) - (b[1] - a[1]) * (px - a[0])
+            e.append(ei)
+            dist.append(np.abs(ei) / max(np.hypot(*(b - a)), 1e-12))
+        inside = ((e[0] >= 0) & (e[1] >= 0) & (e[2] >= 0)) | ((e[0] <= 0) & (e[1] <= 0) & (e[2] <= 0))
+        cover[y0:y1 + 1, x0:x1 + 1] |= inside
+        near_edge[y0:y1 + 1, x0:x1 + 1] |= np.min(np.stack(dist), 0) < 1e-3
+    got = np.isfinite(D)
+    assert cover.sum() > 500
+    diff = got != cover
+    assert np.all(near_edge[diff])
+    assert diff.sum() <= max(3, cover.sum() // 1000)
+
+
 def test_depth_perspective_behind_camera_skipped():
     rig = make_rig("tiny")
     C = rig.C64[0]
