@@ -115,7 +115,8 @@ typedef struct {
     int oob_policy;        /* FVV_OOB_STRICT or FVV_OOB_ABSTAIN                */
     int max_components;    /* raw components per frame (<= 8192)              */
     int max_rois;          /* kept components per frame (<= 4096)             */
-    long long max_fine_words;  /* 32-sample words of all padded fine grids    */
+    long long max_fine_words;  /* 32-sample words of all padded fine grids,
+                                  <= 2^26                                    */
     long long max_verts;   /* mesh vertices per frame                          */
     long long max_tris;    /* mesh triangles per frame                         */
 } fvv_recon_params;
@@ -312,6 +313,21 @@ fvv_status fvv_set_graphs(fvv_rig *rig, int enable);
  * + 4dz; cube edge e has axis e/4 and lower corner with the other two
  * coordinates (e%4 & 1, e%4 >> 1) in axis order).  Host memory; no GPU needed. */
 fvv_status fvv_mc_table(uint8_t *ntri, uint8_t *edges);
+
+/* L2 micro-benchmark (no counterpart in the paper): the memory side of the
+ * roofline of the hull tests, each of which gathers one 32-bit silhouette
+ * word.  Launches `blocks` x `threads` threads on `stream`; every load is
+ * ld.global.cg (L2, not L1).
+ *   mode 0: coalesced read of the `bytes` at buf (16-byte aligned, a multiple
+ *           of 16), `reps` times over: bytes*reps bytes read;
+ *   mode 1: `reps` random 32-bit gathers per thread from the bytes/4 words at
+ *           buf (a power of two): blocks*threads*reps gathers.
+ * buf and out are device pointers; out receives blocks*threads uint32 (an
+ * XOR of what each thread read, so that the loads are not dropped).  Bad
+ * arguments give FVV_ERR_INVALID_ARG with nothing launched.  Time it with
+ * events on `stream`. */
+fvv_status fvv_probe_l2(int mode, const void *buf, size_t bytes, int reps, uint32_t *out, int blocks, int threads,
+                        void *stream);
 
 /* Message of the last failure on rig (or of the last failed create if rig is
  * NULL).  The string stays valid until the next call on the rig. */

@@ -19,7 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfvv.so")
-SOURCES = ["fvv_api.cu", "kernels_carve.cu", "kernels_ccl.cu", "kernels_mc.cu", "kernels_render.cu", "noalloc.cu"]
+SOURCES = ["fvv_api.cu", "kernels_carve.cu", "kernels_ccl.cu", "kernels_mc.cu", "kernels_render.cu", "noalloc.cu",
+           "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE]

@@ -146,7 +146,10 @@ fvv_status make_plan(const fvv_rig_desc* d, const fvv_recon_params* p, Plan& pl,
     }
     long long mv = p->max_verts > 0 ? p->max_verts : 2 * fw;
     long long mt = p->max_tris > 0 ? p->max_tris : 2 * mv;
-    if (fw > (1ll << 30) || mv > (1ll << 30) || mt > (1ll << 30)) { err = "capacities must be <= 2^30"; return FVV_ERR_INVALID_ARG; }
+    if (fw > (1ll << 26) || mv > (1ll << 30) || mt > (1ll << 30)) {
+        err = "max_fine_words must be <= 2^26, max_verts and max_tris <= 2^30";
+        return FVV_ERR_INVALID_ARG;
+    }
     g.max_fine_words = (uint32_t)fw;
     g.max_chunks = (uint32_t)((fw + kChunk - 1) / kChunk);
     g.max_verts = (uint32_t)mv;

@@ -113,17 +113,80 @@ __device__ __forceinline__ int roi_of_sample(const DRoi* rois, int n, uint32_t s
     return lo;
 }
 
+// Levels of the fine carve: a sample at level j has passed cameras
+// [0, lvb(j)) and tests cameras [lvb(j), lvb(j + 1)) next: [0,2), [2,4),
+// [4,8), [8,N).
+constexpr int kLevels = 4;
+__host__ __device__ constexpr int lvb(int n, int j) {
+    return j == 0 ? 0 : (j < kLevels && (1 << j) < n ? (1 << j) : n);
+}
+
+// Cameras [C0, C1) of the test (Sec. II-B-1) for the live lanes of a warp,
+// in index order, each lane stopping at its first background vote and the
+// warp at the first camera where no lane is left.
+template <bool ABSTAIN, int C0, int C1>
+__device__ __forceinline__ void test_span(const CamSet& cams, const uint32_t* __restrict__ sil, float X, float Y,
+                                          float Z, bool& alive, bool& voted, uint32_t& tests) {
+#pragma unroll
+    for (int n = C0; n < C1; ++n) {
+        if (!__any_sync(kFull, alive)) break;
+        if (alive) {
+            ++tests;
+            test_cam<ABSTAIN>(cams.c[n], sil, X, Y, Z, alive, voted);
+        }
+    }
+}
+
+template <bool ABSTAIN>
+__device__ __forceinline__ void test_span_rt(const CamSet& cams, const uint32_t* __restrict__ sil, int c0, int c1,
+                                             float X, float Y, float Z, bool& alive, bool& voted, uint32_t& tests) {
+    for (int n = c0; n < c1; ++n) {
+        if (!__any_sync(kFull, alive)) break;
+        if (alive) {
+            ++tests;
+            test_cam<ABSTAIN>(cams.c[n], sil, X, Y, Z, alive, voted);
+        }
+    }
+}
+
+template <int NC, bool ABSTAIN>
+__device__ __forceinline__ void test_level(const CamSet& cams, const uint32_t* __restrict__ sil, int lv, float X,
+                                           float Y, float Z, bool& alive, bool& voted, uint32_t& tests) {
+    if constexpr (NC > 0) {
+        switch (lv) {
+            case 0: test_span<ABSTAIN, lvb(NC, 0), lvb(NC, 1)>(cams, sil, X, Y, Z, alive, voted, tests); break;
+            case 1: test_span<ABSTAIN, lvb(NC, 1), lvb(NC, 2)>(cams, sil, X, Y, Z, alive, voted, tests); break;
+            case 2: test_span<ABSTAIN, lvb(NC, 2), lvb(NC, 3)>(cams, sil, X, Y, Z, alive, voted, tests); break;
+            default: test_span<ABSTAIN, lvb(NC, 3), NC>(cams, sil, X, Y, Z, alive, voted, tests); break;
+        }
+    } else {
+        test_span_rt<ABSTAIN>(cams, sil, lvb(cams.n, lv), lvb(cams.n, lv + 1), X, Y, Z, alive, voted, tests);
+    }
+}
+
 // Sec. II-B-3: the fine hull of every ROI, each treated as its own volume.
 // Fine grids are stored padded by one unoccupied sample per side (index 0
-// and fdim+1), rows of ceil((fdim_x+2)/32) words, cleared beforehand.  Lanes
-// take the interior samples of all ROIs in order (x fastest, rows wrapping),
-// so no lane idles on padding; each warp then ORs its results into the (at
-// most a few) padded words they fall in.
+// and fdim+1), rows of ceil((fdim_x+2)/32) words, cleared beforehand; only
+// occupied samples are written, by OR into their word.
+//
+// Most samples are rejected by the first camera or two while the points
+// inside the hull take every camera, so a warp that kept its 32 samples to
+// the end would idle most lanes.  Each warp therefore moves samples through
+// levels (cameras [0,2), [2,4), [4,8), [8,N)): a step takes 32 samples at
+// one level (fresh interior samples of all ROIs, in order, at level 0),
+// tests that level's cameras and queues the survivors in the warp's part of
+// shared memory for the next level; the deepest level holding 32 goes
+// first, so each queue stays under 64 entries.  The queue counts are the
+// same in every lane (they follow from ballots), so the warp needs no
+// shared counters and the block no barrier.  Each sample still tests the
+// cameras in index order and stops at its first background vote, so
+// occupancy and test counts are those of the plain per-sample loop.
 template <int NC>
 __global__ void __launch_bounds__(256) k_fine_carve(const __grid_constant__ CamSet cams,
                                                     const __grid_constant__ Grid g,
                                                     const __grid_constant__ Layout L,
                                                     const __grid_constant__ SlotList sl) {
+    extern __shared__ float4 fq_all[];       // per warp: levels 1..3, 64 entries each
     __shared__ unsigned long long sh_t[32];
     const int slot = sl.s[blockIdx.y];
     const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
@@ -133,47 +196,97 @@ __global__ void __launch_bounds__(256) k_fine_carve(const __grid_constant__ CamS
     const uint32_t* __restrict__ sil = slot_ptr<uint32_t>(L, slot, L.sil);
     uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
     const int lane = threadIdx.x & 31;
-    const uint32_t stride = gridDim.x * blockDim.x;
+    const unsigned lt = (1u << lane) - 1u;
+    float4* fq = fq_all + (threadIdx.x >> 5) * (kLevels - 1) * 64;
+    const int ncam = NC > 0 ? NC : cams.n;
+    const bool abstain = cams.oob == FVV_OOB_ABSTAIN;
+    const uint32_t fresh_step = gridDim.x * blockDim.x;
+    uint32_t fresh = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    int qn[kLevels] = {0, 0, 0, 0};          // entries queued per level (level 0 unused)
     uint32_t tests = 0;
-    // per-lane ROI cursor
+    // per-lane ROI cursor for fresh samples
     uint32_t lo = 0, hi = 0, woff = 0;
     int fx = 1, fy = 1, nxw = 1;
     float fo0 = 0.f, fo1 = 0.f, fo2 = 0.f;
-    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nsamp; base += stride) {
-        const uint32_t s = base + lane;
-        const bool act = s < nsamp;
-        if (act && (s >= hi || s < lo)) {
-            const DRoi& r = rois[roi_of_sample(rois, nrois, s)];
-            lo = r.samp_off;
-            fx = r.fdim[0];
-            fy = r.fdim[1];
-            hi = lo + (uint32_t)fx * (uint32_t)fy * (uint32_t)r.fdim[2];
-            woff = r.word_off;
-            nxw = r.nxw;
-            fo0 = r.fo[0];
-            fo1 = r.fo[1];
-            fo2 = r.fo[2];
+    for (;;) {
+        int lv = -1;
+#pragma unroll
+        for (int j = 1; j < kLevels; ++j)
+            if (qn[j] >= 32) lv = j;
+        if (lv < 0 && fresh < nsamp) lv = 0;
+        if (lv < 0) {
+#pragma unroll
+            for (int j = kLevels - 1; j >= 1; --j)
+                if (qn[j] > 0) lv = j;
         }
-        const uint32_t loc = act ? s - lo : 0u;
-        const uint32_t row = loc / (uint32_t)fx;
-        const int x = (int)(loc - row * (uint32_t)fx);
-        const int y = (int)(row % (uint32_t)fy), z = (int)(row / (uint32_t)fy);
-        const float X = fadd(fo0, fmul(fadd((float)x, 0.5f), g.sf));
-        const float Y = fadd(fo1, fmul(fadd((float)y, 0.5f), g.sf));
-        const float Z = fadd(fo2, fmul(fadd((float)z, 0.5f), g.sf));
-        const bool on = warp_test<NC>(cams, sil, X, Y, Z, act, tests);
-        const uint32_t word = woff + ((uint32_t)(z + 1) * (uint32_t)(fy + 2) + (uint32_t)(y + 1)) * (uint32_t)nxw +
-                              (uint32_t)((x + 1) >> 5);
-        const uint32_t bit = on ? 1u << ((x + 1) & 31) : 0u;
-        uint32_t pend = __ballot_sync(kFull, act);
-        while (pend) {
-            const int leader = __ffs(pend) - 1;
-            const uint32_t T = __shfl_sync(kFull, word, leader);
-            const bool mine = act && word == T;
-            const uint32_t ored = __reduce_or_sync(kFull, mine ? bit : 0u);
-            if (lane == leader && ored) atomicOr(fine + T, ored);
-            pend &= ~__ballot_sync(kFull, mine);
+        if (lv < 0) break;
+        float X = 0.f, Y = 0.f, Z = 0.f;
+        uint32_t wb = 0;                     // word << 6 | voted << 5 | bit
+        bool act;
+        if (lv == 0) {
+            const uint32_t s = fresh + lane;
+            fresh += fresh_step;
+            act = s < nsamp;
+            if (act && (s >= hi || s < lo)) {
+                const DRoi& r = rois[roi_of_sample(rois, nrois, s)];
+                lo = r.samp_off;
+                fx = r.fdim[0];
+                fy = r.fdim[1];
+                hi = lo + (uint32_t)fx * (uint32_t)fy * (uint32_t)r.fdim[2];
+                woff = r.word_off;
+                nxw = r.nxw;
+                fo0 = r.fo[0];
+                fo1 = r.fo[1];
+                fo2 = r.fo[2];
+            }
+            const uint32_t loc = act ? s - lo : 0u;
+            const uint32_t row = loc / (uint32_t)fx;
+            const int x = (int)(loc - row * (uint32_t)fx);
+            const int y = (int)(row % (uint32_t)fy), z = (int)(row / (uint32_t)fy);
+            X = fadd(fo0, fmul(fadd((float)x, 0.5f), g.sf));
+            Y = fadd(fo1, fmul(fadd((float)y, 0.5f), g.sf));
+            Z = fadd(fo2, fmul(fadd((float)z, 0.5f), g.sf));
+            const uint32_t word = woff + ((uint32_t)(z + 1) * (uint32_t)(fy + 2) + (uint32_t)(y + 1)) * (uint32_t)nxw +
+                                  (uint32_t)((x + 1) >> 5);
+            wb = (word << 6) | (uint32_t)((x + 1) & 31);
+        } else {
+            const int take = min(qn[lv], 32);
+            qn[lv] -= take;
+            act = lane < take;
+            if (act) {
+                const float4 e = fq[(lv - 1) * 64 + qn[lv] + lane];
+                X = e.x;
+                Y = e.y;
+                Z = e.z;
+                wb = __float_as_uint(e.w);
+            }
         }
+        bool alive = act, voted = !abstain || ((wb >> 5) & 1u);
+        if (abstain) test_level<NC, true>(cams, sil, lv, X, Y, Z, alive, voted, tests);
+        else test_level<NC, false>(cams, sil, lv, X, Y, Z, alive, voted, tests);
+        if (lvb(ncam, lv + 1) == ncam) {
+            // every camera done: OR the occupied samples into their words,
+            // one atomic per distinct word of the warp
+            const bool on = alive && voted;
+            const uint32_t word = wb >> 6, bit = 1u << (wb & 31u);
+            uint32_t pend = __ballot_sync(kFull, on);
+            while (pend) {
+                const int leader = __ffs(pend) - 1;
+                const uint32_t T = __shfl_sync(kFull, word, leader);
+                const bool mine = on && word == T;
+                const uint32_t ored = __reduce_or_sync(kFull, mine ? bit : 0u);
+                if (lane == leader) atomicOr(fine + T, ored);
+                pend &= ~__ballot_sync(kFull, mine);
+            }
+        } else {
+            // the popped entries were read above, before any lane writes
+            const uint32_t m = __ballot_sync(kFull, alive);
+            if (alive)
+                fq[lv * 64 + qn[lv + 1] + __popc(m & lt)] =
+                    make_float4(X, Y, Z, __uint_as_float((wb & ~32u) | (voted ? 32u : 0u)));
+            qn[lv + 1] += __popc(m);
+        }
+        __syncwarp();
     }
     const unsigned long long t = block_sum<unsigned long long>(tests, sh_t);
     if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_fine, t);
@@ -229,7 +342,7 @@ cudaError_t launch_fine_carve(const CamSet& cams, const Grid& g, const Layout& L
     k_clear_fine<<<dim3(gc, sl.n), 256, 0, st>>>(L, sl);
     const int th = tu.threads[FVV_TUNE_FINE];
     const int gx = tuned_grid(tu, FVV_TUNE_FINE, sms, sl.n, (long long)g.max_fine_words * 32);
-#define FVV_LAUNCH(NC) k_fine_carve<NC><<<dim3(gx, sl.n), th, 0, st>>>(cams, g, L, sl)
+#define FVV_LAUNCH(NC) k_fine_carve<NC><<<dim3(gx, sl.n), th, (size_t)th / 32 * 3 * 64 * sizeof(float4), st>>>(cams, g, L, sl)
     FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
     return cudaGetLastError();

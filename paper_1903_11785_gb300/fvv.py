@@ -92,6 +92,7 @@ _sigs = {
     "fvv_set_tuning": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "fvv_set_graphs": ([_vp, C.c_int], C.c_int),
     "fvv_get_timing": ([_vp, C.POINTER(C.c_float), C.POINTER(C.c_int)], C.c_int),
+    "fvv_probe_l2": ([C.c_int, _vp, C.c_size_t, C.c_int, _vp, C.c_int, C.c_int, _vp], C.c_int),
     "fvv_last_error": ([_vp], C.c_char_p),
     "fvv_status_string": ([C.c_int], C.c_char_p),
     "fvv_version": ([], C.c_int),
@@ -262,6 +263,17 @@ def fvv_get_timing(rig_ptr):
     calls = (C.c_int * len(STAGES))()
     _check(_lib.fvv_get_timing(rig_ptr, ms, calls), rig_ptr)
     return {name: (ms[i], calls[i]) for i, name in enumerate(STAGES)}
+
+
+def fvv_probe_l2(mode: int, buf: torch.Tensor, reps: int, out: torch.Tensor, blocks: int, threads: int,
+                 stream=None):
+    """L2 micro-benchmark: mode 0 reads `buf` coalesced `reps` times, mode 1
+    does `reps` random 32-bit gathers per thread from it; `out` (int32 or
+    uint32, blocks*threads elements) receives each thread's XOR."""
+    if buf.device.type != "cuda" or out.device.type != "cuda" or out.numel() < blocks * threads:
+        raise ValueError("fvv_probe_l2: device buffers, out of blocks*threads words")
+    nbytes = buf.numel() * buf.element_size()
+    _check(_lib.fvv_probe_l2(mode, buf.data_ptr(), nbytes, reps, out.data_ptr(), blocks, threads, _stream(stream)))
 
 
 def fvv_get_debug(rig_ptr, slot, what, stream=None) -> torch.Tensor:

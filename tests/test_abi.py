@@ -18,7 +18,7 @@ HEADER = os.path.join(ROOT, "include", "fvv.h")
 def _declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(fvv_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(fvv_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -71,6 +71,9 @@ def test_query_arena_and_validation(fvv):
         fvv.fvv_query_arena(d, bad)
     bad = fvv.make_params(rig)
     bad.max_components = 9000
+    with pytest.raises(fvv.FvvError):
+        fvv.fvv_query_arena(d, bad)
+    bad = fvv.make_params(rig, max_fine_words=(1 << 26) + 1)   # fine words are packed in 26 bits
     with pytest.raises(fvv.FvvError):
         fvv.fvv_query_arena(d, bad)
     d0 = fvv.make_desc(rig, max_slots=0)
