@@ -158,6 +158,69 @@ def oracle_frames_per_s(rig, masks_cpu, rgb_cpu, vps):
     return len(masks_cpu) / dt, tests / dt, dt
 
 
+def _oracle_worker(job):
+    """One frame of the full oracle path in a worker process (frame-parallel
+    CPU baseline); inputs are read from .npy files written by the parent."""
+    path, i = job
+    from oracle import Oracle
+    from synth import make_rig
+    masks = np.load(os.path.join(path, "masks.npy"), mmap_mode="r")
+    rgb = np.load(os.path.join(path, "rgb.npy"), mmap_mode="r")
+    vps = np.load(os.path.join(path, "vps.npy"))
+    o = Oracle(make_rig(CONFIG))
+    j = i % len(masks)
+    t0 = time.perf_counter()
+    ref = o.reconstruct(np.asarray(masks[j]))
+    d = o.depth(ref.verts, ref.tris)
+    o.colour(np.asarray(rgb[j]), vps[j], d, ref.verts)
+    return time.perf_counter() - t0, ref.tests
+
+
+def oracle_all_cores(masks_cpu, rgb_cpu, vps):
+    """The same oracle as independent processes, one frame per host core
+    (frames are independent, so this needs no change to the oracle).
+    Returns (frames/s, processes, seconds)."""
+    import multiprocessing as mp
+    import shutil
+    import tempfile
+    from oracle import build as build_oracle
+    build_oracle()
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    tmp = tempfile.mkdtemp(prefix="fvv_oracle_")
+    try:
+        np.save(os.path.join(tmp, "masks.npy"), masks_cpu)
+        np.save(os.path.join(tmp, "rgb.npy"), rgb_cpu)
+        np.save(os.path.join(tmp, "vps.npy"), np.asarray(vps))
+        with mp.get_context("spawn").Pool(n) as pool:
+            pool.map(_oracle_worker, [(tmp, i) for i in range(n)], chunksize=1)      # imports, page-in
+            t0 = time.perf_counter()
+            pool.map(_oracle_worker, [(tmp, i) for i in range(n)], chunksize=1)
+            dt = time.perf_counter() - t0
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+    return n / dt, n, dt
+
+
+def oracle_configs_single_core(frames):
+    """Per-frame milliseconds of the single-threaded oracle (full path) on
+    each scene configuration: {config: (masks list, rgb list, viewpoints)}."""
+    from oracle import Oracle
+    from synth import make_rig
+    out = {}
+    for cfg, (ms, cs, vps) in frames.items():
+        o = Oracle(make_rig(cfg))
+        t0 = time.perf_counter()
+        tests = 0
+        for m, c, vp in zip(ms, cs, vps):
+            ref = o.reconstruct(m)
+            d = o.depth(ref.verts, ref.tris)
+            o.colour(c, vp, d, ref.verts)
+            tests += ref.tests
+        dt = time.perf_counter() - t0
+        out[cfg] = {"ms_per_frame": 1000 * dt / len(ms), "frames": len(ms), "tests_per_frame": tests / len(ms)}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -430,6 +493,16 @@ def run_ours(args):
 
     S = min(args.cpu_frames, F)
     cpu_sample = (masks[:S].cpu().numpy(), rgb[:S].cpu().numpy(), vps[:S])
+    cfg_frames = {}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from synth import make_frame
+        from synth import make_rig as _make_rig
+        for cfg, n_cfg in (("tiny", 4), ("judo", 1), ("hd720", 2)):
+            rg = _make_rig(cfg)
+            frs = [make_frame(cfg, i, device="cuda", rig=rg)[1] for i in range(n_cfg)]
+            cfg_frames[cfg] = ([f.masks.cpu().numpy() for f in frs], [f.rgb.cpu().numpy() for f in frs],
+                               [f.viewpoint for f in frs])
+            del frs
 
     # ---- serving: 4 rigs, Poisson arrivals, continuous batching under a memory budget
     serving = None
@@ -448,6 +521,13 @@ def run_ours(args):
         cpu = {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle", "gtests_per_s": tps / 1e9,
                "sample": f"{S} volleyball-shaped frames of the batch, full path (reconstruct + depth + colour), "
                          f"single thread, {dt:.1f} s"}
+        pfps, nproc, pdt = oracle_all_cores(*cpu_sample)
+        cpu["all_cores"] = {"value": pfps, "unit": "frames/s", "cores": nproc, "kind": "oracle",
+                            "sample": f"{nproc} processes, one volleyball-shaped frame each (cycling over the "
+                                      f"{S} sampled frames), full path, {pdt:.1f} s"}
+        per_cfg = oracle_configs_single_core(cfg_frames)
+        per_cfg["volleyball"] = {"ms_per_frame": 1000 * dt / S, "frames": S, "tests_per_frame": tps * dt / S}
+        cpu["single_core_per_config"] = per_cfg
 
     n_launch = args.steps * (F + 16)
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,

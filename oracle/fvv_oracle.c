@@ -43,7 +43,9 @@
  *    unoccupied samples so that every mesh is closed.
  *  - The exact intersection of Eqs. (2)-(3) is computed as a fixed number of
  *    3D bisection steps of the same all-cameras predicate; 0 steps gives the
- *    edge midpoint (isovalue 0.5).
+ *    edge midpoint (isovalue 0.5).  The paper's own form (a pixel walk along
+ *    each projected edge, Eq. (2) per camera, the minimum of Eq. (3)) is the
+ *    alternative surface rule, edge_lambda below.
  *  - MC faces with two diagonal ON corners separate the ON corners.
  *  - The triangle depth is the distance from the triangle centroid to the
  *    camera centre (Sec. II-D-1), also used for the occlusion test of
@@ -74,7 +76,11 @@ typedef struct {
     int t_np, t_nb;
     float t_v;
     int oob_policy;
+    int surface_rule;    /* ORC_SURFACE_BISECT or ORC_SURFACE_LAMBDA */
 } orc_rig;
+
+#define ORC_SURFACE_BISECT 0
+#define ORC_SURFACE_LAMBDA 1
 
 typedef struct {
     int cmin[3], cmax[3]; /* inclusive coarse box of the component          */
@@ -156,6 +162,102 @@ static int point_on(const orc_rig *rig, const uint8_t *const *masks,
         if (v == 1) voted = 1;
     }
     return voted;
+}
+
+/* Pixel index of a Bresenham end point: the floor of the exact quotient,
+ * clamped to [-1, n + 1] (n = image width or height), so that an end point
+ * far outside the image keeps the walk short. */
+static long long end_pixel(R x, R w, int n)
+{
+    double f = pixel_floor(x, w);
+    if (f < -1.0) return -1;
+    if (f > (double)n + 1.0) return (long long)n + 1;
+    return (long long)f;
+}
+
+/* Sec. II-C, Eq. (2), camera n, for the grid edge from the ON sample a to
+ * the OFF sample b.  The end points project to the image positions
+ * p_on = (x'/w', y'/w') and p_off (binary32 quotients) and to the pixels A
+ * and B holding them.  The pixels of the line from A to B are visited in
+ * Bresenham order starting at A; the walk stops at the first pixel that is
+ * outside the image or not in the silhouette, and P_n is the last pixel
+ * before it.  lambda_n = |c(P_n) - p_on| / |p_off - p_on| with c(P_n) the
+ * pixel centre, clamped to at most 1.  A camera that has an end point behind
+ * it, that does not see A in its silhouette (only possible under ABSTAIN),
+ * whose walk reaches B, or for which p_on = p_off, bounds nothing: 1.
+ * Every pixel visited counts as one test. */
+static R camera_lambda(const orc_rig *rig, const uint8_t *const *masks, int n, const R *a, const R *b,
+                       long long *tests)
+{
+    const float *p = rig->P + 12 * n;
+    R xa = (((R)p[0] * a[0] + (R)p[1] * a[1]) + (R)p[2] * a[2]) + (R)p[3];
+    R ya = (((R)p[4] * a[0] + (R)p[5] * a[1]) + (R)p[6] * a[2]) + (R)p[7];
+    R wa = (((R)p[8] * a[0] + (R)p[9] * a[1]) + (R)p[10] * a[2]) + (R)p[11];
+    R xb = (((R)p[0] * b[0] + (R)p[1] * b[1]) + (R)p[2] * b[2]) + (R)p[3];
+    R yb = (((R)p[4] * b[0] + (R)p[5] * b[1]) + (R)p[6] * b[2]) + (R)p[7];
+    R wb = (((R)p[8] * b[0] + (R)p[9] * b[1]) + (R)p[10] * b[2]) + (R)p[11];
+    if (!(wa > (R)0 && wb > (R)0)) return (R)1;
+    int W = rig->width[n], H = rig->height[n];
+    long long x = end_pixel(xa, wa, W), y = end_pixel(ya, wa, H);
+    long long x1 = end_pixel(xb, wb, W), y1 = end_pixel(yb, wb, H);
+    long long dx = x1 > x ? x1 - x : x - x1, dy = y1 > y ? y - y1 : y1 - y; /* dy <= 0 */
+    long long sx = x < x1 ? 1 : -1, sy = y < y1 ? 1 : -1, err = dx + dy;
+    int have = 0;
+    long long lx = 0, ly = 0;
+    for (;;) {
+        ++*tests;
+        int fg = x >= 0 && x < W && y >= 0 && y < H && masks[n][(size_t)y * (size_t)W + (size_t)x] != 0;
+        if (!fg) break;
+        have = 1;
+        lx = x;
+        ly = y;
+        if (x == x1 && y == y1) return (R)1;
+        long long e2 = 2 * err;
+        if (e2 >= dy) { err += dy; x += sx; }
+        if (e2 <= dx) { err += dx; y += sy; }
+    }
+    if (!have) return (R)1;
+    R ua = xa / wa, va = ya / wa, ub = xb / wb, vb = yb / wb;
+    R cx = (R)lx + (R)0.5, cy = (R)ly + (R)0.5;
+    R num = sqrt((cx - ua) * (cx - ua) + (cy - va) * (cy - va));
+    R den = sqrt((ub - ua) * (ub - ua) + (vb - va) * (vb - va));
+    if (!(den > (R)0)) return (R)1;
+    R l = num / den;
+    return l < (R)1 ? l : (R)1;
+}
+
+/* Sec. II-C, Eq. (3): lambda = the minimum of Eq. (2) over all cameras, in
+ * index order; the vertex is a + lambda (b - a). */
+static R edge_lambda(const orc_rig *rig, const uint8_t *const *masks, const R *a, const R *b, R *lam_n,
+                     long long *tests)
+{
+    R lam = (R)1;
+    for (int n = 0; n < rig->n_cams; ++n) {
+        R l = camera_lambda(rig, masks, n, a, b, tests);
+        if (lam_n) lam_n[n] = l;
+        if (l < lam) lam = l;
+    }
+    return lam;
+}
+
+/* Public: Eqs. (2)-(3) for a list of edges (end points as double values of
+ * type R); lam_n (may be NULL) receives n_edges x n_cams per-camera values. */
+int orc_edge_lambda(const orc_rig *rig, const uint8_t *const *masks, long long n_edges, const double *a,
+                    const double *b, double *lam, double *lam_n, long long *tests)
+{
+    long long t = 0;
+    R *ln = (R *)malloc(sizeof(R) * (size_t)(rig->n_cams > 0 ? rig->n_cams : 1));
+    if (!ln) return -1;
+    for (long long i = 0; i < n_edges; ++i) {
+        R ra[3] = {(R)a[3 * i], (R)a[3 * i + 1], (R)a[3 * i + 2]};
+        R rb[3] = {(R)b[3 * i], (R)b[3 * i + 1], (R)b[3 * i + 2]};
+        lam[i] = (double)edge_lambda(rig, masks, ra, rb, ln, &t);
+        if (lam_n)
+            for (int n = 0; n < rig->n_cams; ++n) lam_n[i * rig->n_cams + n] = (double)ln[n];
+    }
+    free(ln);
+    if (tests) *tests = t;
+    return 0;
 }
 
 /* Public: occupancy of a list of points (values of type R, given as double). */
@@ -613,14 +715,19 @@ static int mesh_roi(const orc_rig *rig, const uint8_t *const *masks, const orc_r
                         sample_centre(r, s, q[0], q[1], q[2], ca);
                         sample_centre(r, s, xp, yp, zp, cb);
                     }
-                    for (int it = 0; it < rig->bisect_steps; ++it) {
+                    if (rig->surface_rule == ORC_SURFACE_LAMBDA) {
+                        R lam = edge_lambda(rig, masks, ca, cb, NULL, tests);
+                        for (int k = 0; k < 3; ++k) m[k] = ca[k] + lam * (cb[k] - ca[k]);
+                    } else {
+                        for (int it = 0; it < rig->bisect_steps; ++it) {
+                            for (int k = 0; k < 3; ++k) m[k] = (ca[k] + cb[k]) * (R)0.5;
+                            if (point_on(rig, masks, m[0], m[1], m[2], tests))
+                                for (int k = 0; k < 3; ++k) ca[k] = m[k];
+                            else
+                                for (int k = 0; k < 3; ++k) cb[k] = m[k];
+                        }
                         for (int k = 0; k < 3; ++k) m[k] = (ca[k] + cb[k]) * (R)0.5;
-                        if (point_on(rig, masks, m[0], m[1], m[2], tests))
-                            for (int k = 0; k < 3; ++k) ca[k] = m[k];
-                        else
-                            for (int k = 0; k < 3; ++k) cb[k] = m[k];
                     }
-                    for (int k = 0; k < 3; ++k) m[k] = (ca[k] + cb[k]) * (R)0.5;
                     vid[3 * L + a] = (int32_t)(vb->n - vstart);
                     if (vpush(vb, m, ca, cb, 3ull * (uint64_t)L + (uint64_t)a)) { free(vid); return -1; }
                 }

@@ -45,7 +45,8 @@ class OrcRig(C.Structure):
                 ("width", C.POINTER(C.c_int)), ("height", C.POINTER(C.c_int)),
                 ("vol_min", C.c_float * 3), ("vol_max", C.c_float * 3),
                 ("coarse_m", C.c_float), ("fine_m", C.c_float), ("bisect_steps", C.c_int),
-                ("t_np", C.c_int), ("t_nb", C.c_int), ("t_v", C.c_float), ("oob_policy", C.c_int)]
+                ("t_np", C.c_int), ("t_nb", C.c_int), ("t_v", C.c_float), ("oob_policy", C.c_int),
+                ("surface_rule", C.c_int)]
 
 
 class OrcRoi(C.Structure):
@@ -145,6 +146,7 @@ class Oracle:
         r.t_nb = rig.t_nb
         r.t_v = rig.t_v
         r.oob_policy = rig.oob_policy
+        r.surface_rule = getattr(rig, "surface_rule", 0)
         self._rig = r
 
     # -- helpers
@@ -163,6 +165,22 @@ class Oracle:
         self.lib.orc_points_on(C.byref(self._rig), ptrs, C.c_longlong(len(pts)), _p(pts, C.c_double),
                                _p(out, C.c_uint8), C.byref(tests))
         return out, tests.value
+
+    # -- Sec. II-C, Eqs. (2)-(3)
+    def edge_lambda(self, masks, a, b):
+        """The paper's isovalue of grid edges from ON ends a (M,3) to OFF ends
+        b (M,3): per camera the Bresenham walk ratio of Eq. (2), and their
+        minimum, Eq. (3).  Returns (lambda (M,), per camera (M,N), pixels read)."""
+        arrs, ptrs = self._images(masks)
+        a = np.ascontiguousarray(np.asarray(a, np.float64).reshape(-1, 3))
+        b = np.ascontiguousarray(np.asarray(b, np.float64).reshape(-1, 3))
+        lam = np.zeros(len(a), np.float64)
+        lam_n = np.zeros((len(a), self.rig.n_cams), np.float64)
+        t = C.c_longlong(0)
+        rc = self.lib.orc_edge_lambda(C.byref(self._rig), ptrs, C.c_longlong(len(a)), _p(a, C.c_double),
+                                      _p(b, C.c_double), _p(lam, C.c_double), _p(lam_n, C.c_double), C.byref(t))
+        assert rc == 0
+        return lam.astype(self.real), lam_n.astype(self.real), int(t.value)
 
     def grid_dims(self):
         d = (C.c_int * 3)()

@@ -76,6 +76,7 @@ class Rig:
     t_nb: int = 2**31 - 1
     t_v: float = 0.5
     oob_policy: int = STRICT
+    surface_rule: int = 0   # 0: bisection, 1: the paper's pixel walk and minimum ratio (Eqs. (2)-(3))
     P64: np.ndarray = field(default=None, repr=False)       # float64 originals
     K64: np.ndarray = field(default=None, repr=False)
     R64: np.ndarray = field(default=None, repr=False)
