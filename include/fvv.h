@@ -79,6 +79,23 @@ typedef enum {
  * ABSTAIN: it does not vote; a point no camera votes for is unoccupied. */
 enum { FVV_OOB_STRICT = 0, FVV_OOB_ABSTAIN = 1 };
 
+/* How a surface vertex is placed on a grid edge between an occupied sample
+ * a and an unoccupied one b (Sec. II-C).
+ * BISECT: bisect_steps times m = (a+b)/2, a = m if m is occupied else b = m;
+ *   the vertex is the final midpoint (0 steps: the edge midpoint, the
+ *   isovalue 0.5 of conventional marching cubes).
+ * LAMBDA: the paper's form, Eqs. (2)-(3).  Per camera the pixels of the line
+ *   from the pixel of a to the pixel of b (both clamped to [-1, W+1] x
+ *   [-1, H+1]) are walked in Bresenham order from a's end; P_n is the last
+ *   silhouette pixel before the first that is outside the image or not in
+ *   the silhouette, lambda_n = |c(P_n) - p_a| / |p_b - p_a| in the image
+ *   plane (c = pixel centre, p = x'/w', y'/w' in binary32), at most 1; a
+ *   camera with an end behind it, whose walk reaches b's pixel, that does
+ *   not see a (ABSTAIN only), or with p_a = p_b gives 1.  lambda is the
+ *   minimum over the cameras and the vertex is a + lambda (b - a).  Every
+ *   pixel visited counts as one test (fvv_counts.tests_bisect). */
+enum { FVV_SURFACE_BISECT = 0, FVV_SURFACE_LAMBDA = 1 };
+
 /* Bits of fvv_counts.flags: which capacity a reconstruction exceeded. */
 enum {
     FVV_FLAG_ROOTS = 1u << 0,      /* raw 26-connected components > max_components */
@@ -119,6 +136,7 @@ typedef struct {
                                   <= 2^26                                    */
     long long max_verts;   /* mesh vertices per frame                          */
     long long max_tris;    /* mesh triangles per frame                         */
+    int surface_rule;      /* FVV_SURFACE_BISECT or FVV_SURFACE_LAMBDA         */
 } fvv_recon_params;
 
 /* One kept object and its 3D ROI (Sec. II-B-2, II-B-3). */

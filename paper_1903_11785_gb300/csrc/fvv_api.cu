@@ -130,6 +130,11 @@ fvv_status make_plan(const fvv_rig_desc* d, const fvv_recon_params* p, Plan& pl,
     g.sf = p->fine_m;
     if (p->bisect_steps < 0 || p->bisect_steps > 30) { err = "bisect_steps must be 0..30"; return FVV_ERR_INVALID_ARG; }
     g.steps = p->bisect_steps;
+    if (p->surface_rule != FVV_SURFACE_BISECT && p->surface_rule != FVV_SURFACE_LAMBDA) {
+        err = "bad surface_rule";
+        return FVV_ERR_INVALID_ARG;
+    }
+    g.rule = p->surface_rule;
     g.t_np = p->t_np;
     g.t_nb = p->t_nb;
     g.t_v = p->t_v;

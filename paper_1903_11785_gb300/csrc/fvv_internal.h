@@ -43,6 +43,7 @@ struct Grid {
     int nx, ny, nz, nxw; // coarse dims, words per coarse row
     long long coarse_um, fine_um;
     int steps;           // bisection steps
+    int rule;            // FVV_SURFACE_*
     int t_np, t_nb;
     float t_v;
     int max_comp, max_rois;

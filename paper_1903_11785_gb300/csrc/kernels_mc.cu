@@ -358,6 +358,105 @@ __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet c
     if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_bisect, t);
 }
 
+// Sec. II-C, Eq. (2), camera c, for the edge from the occupied end a to the
+// unoccupied end b: walk the pixels of the line between their pixels in
+// Bresenham order from a's end and stop at the first one outside the image
+// or not in the silhouette; lambda = |centre of the last silhouette pixel -
+// p_a| / |p_b - p_a| in the image plane, at most 1.  Cameras that bound
+// nothing (an end behind the camera, the walk reaching b's pixel, a not
+// seen, p_a = p_b) give 1.  `tests` counts the pixels visited.
+__device__ __forceinline__ float cam_lambda(const Cam& c, const uint32_t* __restrict__ sil, const float* a,
+                                           const float* b, uint32_t& tests) {
+    float xa, ya, wa, xb, yb, wb;
+    project(c.P, a[0], a[1], a[2], xa, ya, wa);
+    project(c.P, b[0], b[1], b[2], xb, yb, wb);
+    if (!(wa > 0.0f && wb > 0.0f)) return 1.0f;
+    // end pixels: floor of the exact quotient, clamped to [-1, n + 1]
+    const float ra = rcp_approx(wa), rb = rcp_approx(wb);
+    int x = pixel_floor(xa, wa, ra, c.Wf), y = pixel_floor(ya, wa, ra, c.Hf);
+    const int x1 = pixel_floor(xb, wb, rb, c.Wf), y1 = pixel_floor(yb, wb, rb, c.Hf);
+    const int dx = abs(x1 - x), dy = -abs(y1 - y);
+    const int sx = x < x1 ? 1 : -1, sy = y < y1 ? 1 : -1;
+    int err = dx + dy;
+    bool have = false;
+    int lx = 0, ly = 0;
+    for (;;) {   // at most max(dx, -dy) + 1 <= 65537 pixels
+        ++tests;
+        const bool in = (unsigned)x < (unsigned)c.W && (unsigned)y < (unsigned)c.H;
+        const uint32_t word = in ? __ldg(sil + c.bit_off + (unsigned)y * (unsigned)c.Wq + ((unsigned)x >> 5)) : 0u;
+        if (!((word >> (x & 31)) & 1u)) break;
+        have = true;
+        lx = x;
+        ly = y;
+        if (x == x1 && y == y1) return 1.0f;
+        const int e2 = 2 * err;
+        if (e2 >= dy) {
+            err += dy;
+            x += sx;
+        }
+        if (e2 <= dx) {
+            err += dx;
+            y += sy;
+        }
+    }
+    if (!have) return 1.0f;
+    const float ua = __fdiv_rn(xa, wa), va = __fdiv_rn(ya, wa), ub = __fdiv_rn(xb, wb), vb = __fdiv_rn(yb, wb);
+    const float ex = fsub(fadd((float)lx, 0.5f), ua), ey = fsub(fadd((float)ly, 0.5f), va);
+    const float fx = fsub(ub, ua), fy = fsub(vb, va);
+    const float num = __fsqrt_rn(fadd(fmul(ex, ex), fmul(ey, ey)));
+    const float den = __fsqrt_rn(fadd(fmul(fx, fx), fmul(fy, fy)));
+    if (!(den > 0.0f)) return 1.0f;
+    const float l = __fdiv_rn(num, den);
+    return l < 1.0f ? l : 1.0f;
+}
+
+// Sec. II-C, Eq. (3): lambda = the minimum of Eq. (2) over the cameras; the
+// vertex is a + lambda (b - a).  One vertex per thread.
+template <int NC>
+__global__ void __launch_bounds__(256) k_lambda(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
+                                                const __grid_constant__ Layout L, const __grid_constant__ SlotList sl) {
+    __shared__ unsigned long long sh_t[32];
+    const int slot = sl.s[blockIdx.y];
+    const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const uint32_t nv = info->n_words ? info->n_verts : 0u;
+    const DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
+    const uint32_t* __restrict__ sil = slot_ptr<uint32_t>(L, slot, L.sil);
+    const uint64_t* vrec = slot_ptr<uint64_t>(L, slot, L.vrec);
+    float* verts = slot_ptr<float>(L, slot, L.verts);
+    uint32_t tests = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
+        const uint64_t rec = vrec[i];
+        const int k = (int)(rec & 0x3FFFu), axis = (int)(rec >> 14 & 3u), s0 = (int)(rec >> 16 & 1u);
+        const int q[3] = {(int)(rec >> 17 & 0x7FFFu), (int)(rec >> 32 & 0x7FFFu), (int)(rec >> 47 & 0x7FFFu)};
+        const DRoi& r = rois[k];
+        float a[3], b[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float c0 = fadd(r.fo[d], fmul(fadd((float)(q[d] - 1), 0.5f), g.sf));
+            const float c1 = fadd(r.fo[d], fmul(fadd((float)(q[d] - 1 + (d == axis)), 0.5f), g.sf));
+            a[d] = s0 ? c0 : c1;
+            b[d] = s0 ? c1 : c0;
+        }
+        float lam = 1.0f;
+        if constexpr (NC > 0) {
+#pragma unroll
+            for (int n = 0; n < NC; ++n) {
+                const float l = cam_lambda(cams.c[n], sil, a, b, tests);
+                if (l < lam) lam = l;
+            }
+        } else {
+            for (int n = 0; n < cams.n; ++n) {
+                const float l = cam_lambda(cams.c[n], sil, a, b, tests);
+                if (l < lam) lam = l;
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) verts[3 * (size_t)i + d] = fadd(a[d], fmul(lam, fsub(b[d], a[d])));
+    }
+    const unsigned long long t = block_sum<unsigned long long>(tests, sh_t);
+    if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_bisect, t);
+}
+
 __global__ void __launch_bounds__(256) k_mc_triangles(const __grid_constant__ Layout L,
                                                       const __grid_constant__ SlotList sl,
                                                       const __grid_constant__ McTable mc) {
@@ -445,9 +544,15 @@ cudaError_t launch_bisect(const CamSet& cams, const Grid& g, const Layout& L, co
                           const Tuning& tu, cudaStream_t st) {
     const int th = tu.threads[FVV_TUNE_BISECT];
     const int gv = tuned_grid(tu, FVV_TUNE_BISECT, sms, sl.n, g.max_verts);
-#define FVV_LAUNCH(NC) k_bisect<NC><<<dim3(gv, sl.n), th, 0, st>>>(cams, g, L, sl)
-    FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
+    if (g.rule == FVV_SURFACE_LAMBDA) {
+#define FVV_LAUNCH(NC) k_lambda<NC><<<dim3(gv, sl.n), th, 0, st>>>(cams, g, L, sl)
+        FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
+    } else {
+#define FVV_LAUNCH(NC) k_bisect<NC><<<dim3(gv, sl.n), th, 0, st>>>(cams, g, L, sl)
+        FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
+#undef FVV_LAUNCH
+    }
     return cudaGetLastError();
 }
 

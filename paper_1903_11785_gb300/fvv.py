@@ -28,6 +28,7 @@ _lib = C.CDLL(LIB_PATH)
 FVV_OK, FVV_ERR_INVALID_ARG, FVV_ERR_OUT_OF_MEMORY, FVV_ERR_CAPACITY, FVV_ERR_NOT_READY, FVV_ERR_TIMEOUT, \
     FVV_ERR_CUDA = range(7)
 FVV_OOB_STRICT, FVV_OOB_ABSTAIN = 0, 1
+FVV_SURFACE_BISECT, FVV_SURFACE_LAMBDA = 0, 1
 FVV_MAX_CAMS, FVV_MAX_BATCH = 64, 256
 FVV_DEBUG_SIL_BITS, FVV_DEBUG_COARSE_BITS, FVV_DEBUG_LABELS, FVV_DEBUG_FINE_BITS, FVV_DEBUG_DEPTH = range(5)
 FLAG_NAMES = {1: "ROOTS", 2: "ROIS", 4: "FINE", 8: "VERTS", 16: "TRIS", 32: "LOOP"}
@@ -51,7 +52,8 @@ class ReconParams(C.Structure):
     _fields_ = [("vol_min", C.c_float * 3), ("vol_max", C.c_float * 3), ("coarse_m", C.c_float),
                 ("fine_m", C.c_float), ("bisect_steps", C.c_int), ("t_np", C.c_int), ("t_nb", C.c_int),
                 ("t_v", C.c_float), ("oob_policy", C.c_int), ("max_components", C.c_int), ("max_rois", C.c_int),
-                ("max_fine_words", C.c_longlong), ("max_verts", C.c_longlong), ("max_tris", C.c_longlong)]
+                ("max_fine_words", C.c_longlong), ("max_verts", C.c_longlong), ("max_tris", C.c_longlong),
+                ("surface_rule", C.c_int)]
 
 
 class Roi(C.Structure):
@@ -166,6 +168,7 @@ def make_params(rig, **caps):
     p.t_nb = rig.t_nb
     p.t_v = rig.t_v
     p.oob_policy = rig.oob_policy
+    p.surface_rule = getattr(rig, "surface_rule", FVV_SURFACE_BISECT)
     for k, v in caps.items():
         setattr(p, k, v)
     return p

@@ -73,6 +73,10 @@ def test_query_arena_and_validation(fvv):
     bad.max_components = 9000
     with pytest.raises(fvv.FvvError):
         fvv.fvv_query_arena(d, bad)
+    bad = fvv.make_params(rig)
+    bad.surface_rule = 2
+    with pytest.raises(fvv.FvvError):
+        fvv.fvv_query_arena(d, bad)
     bad = fvv.make_params(rig, max_fine_words=(1 << 26) + 1)   # fine words are packed in 26 bits
     with pytest.raises(fvv.FvvError):
         fvv.fvv_query_arena(d, bad)

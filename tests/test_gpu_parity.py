@@ -85,6 +85,32 @@ def test_abstain_policy_and_zero_steps():
     assert ref.tests_bisect == 0
 
 
+@pytest.mark.parametrize("config,index", [("tiny", 4), ("volleyball", 1), ("judo", 1)])
+def test_paper_surface_rule_bit_exact(config, index):
+    """Sec. II-C as printed: vertices from the pixel walks and the minimum
+    ratio of Eqs. (2)-(3) (the lambda kernel) equal the oracle's, and so do
+    the pixel counts, depth images and colours that follow."""
+    rig, fr = make_frame(config, index)
+    rig.surface_rule = 1
+    g = run_gpu(rig, [fr])[0]
+    ref = compare(rig, fr, g)
+    assert ref.tests_bisect >= len(ref.verts) * rig.n_cams
+
+
+def test_paper_surface_rule_abstain_ragged():
+    """The lambda kernel under ABSTAIN (cameras that do not see the ON end
+    bound nothing) on images 630 px wide, the walks crossing partial words."""
+    n, r, h = 6, 6.0, 3.0
+    cs = [(r * math.cos(2 * math.pi * k / n), r * math.sin(2 * math.pi * k / n), h) for k in range(n)]
+    rig = _make_rig("ragged", cs, [(0, 0, 0.9)] * n, 480.0, 630, 349, _gen("ragged/rig"),
+                    (-2.0, -2.0, 0.0), (2.0, 2.0, 2.5), 0.05, 0.01, 6)
+    rig.oob_policy = ABSTAIN
+    rig.surface_rule = 1
+    fr = render(rig, scene_objects("tiny", 5), index=5, config_tag="ragged")
+    g = run_gpu(rig, [fr])[0]
+    compare(rig, fr, g)
+
+
 def test_ragged_image_width():
     """Images whose width is not a multiple of 32 (scalar packing path, partial
     last word of every silhouette row)."""
