@@ -69,6 +69,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--study", choices=("surface", "fig10", "table1"), default=None,
+                    help="instead of the benchmark line: surface-rule errors (Sec. II-C), the coarse/fine "
+                         "voxel-size sweeps of Fig. 10, or the Table I capture shapes")
+    ap.add_argument("--study-frames", type=int, default=4)
     return ap.parse_args()
 
 
@@ -554,8 +558,199 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------ studies
+
+PAPER_STAGES = (("B-1", ("coarse",)), ("B-2", ("ccl",)), ("B-3", ("fine",)), ("C", ("mc", "bisect")),
+                ("D-1", ("depth",)), ("D-2", ("colour",)))
+
+
+def _timed_reconstruction(fvv, torch, rig, frames, reps=3, keep_results=False):
+    """Reconstruct and colour `frames` (one slot each, one batched call) on
+    the default launch shapes; per-stage device ms per frame (Table II
+    buckets) over `reps` timed repetitions, frames/s, counts and results."""
+    F = len(frames)
+    r = fvv.Rig(rig, max_slots=F, host_staging=0)
+    try:
+        slots = list(range(F))
+        masks = [f.masks.cuda() for f in frames]
+        rgb = torch.stack([f.rgb.cuda() for f in frames])
+        vps = np.stack([f.viewpoint for f in frames])
+
+        def step():
+            for i in slots:
+                r.upload_silhouettes(i, masks[i])
+            r.reconstruct(slots)
+            r.colour(slots, rgb, vps)
+        step()
+        torch.cuda.synchronize()
+        r.set_timing(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            step()
+        b.record()
+        torch.cuda.synchronize()
+        st = r.timing()
+        r.set_timing(False)
+        ms = a.elapsed_time(b) / reps
+        counts = [r.counts(i) for i in slots]
+        res = [r.results(i) for i in slots] if keep_results else None
+        stages = {k: v[0] / reps / F for k, v in st.items()}
+        paper = {name: sum(stages[k] for k in ks) for name, ks in PAPER_STAGES}
+        return {"frames_per_s": F / (ms / 1000.0), "ms_per_frame": ms / F, "stages_ms_per_frame": stages,
+                "paper_buckets_ms_per_frame": paper,
+                "per_frame": {k: sum(c[k] for c in counts) / F for k in
+                              ("n_rois", "n_verts", "n_tris", "tests_coarse", "tests_fine", "tests_bisect")}}, res
+    finally:
+        r.close()
+
+
+def _ellipsoid_distance(torch, p, e):
+    """Euclidean distance from points p (M,3, float64 tensor) to the surface
+    of ellipsoid e, and whether each point is inside it.  The closest point
+    of an ellipsoid with semi-axes a to a local point y is a^2 y / (t + a^2)
+    where t solves sum (a_i y_i / (t + a_i^2))^2 = 1 (t > -min a_i^2); t is
+    found by bisection."""
+    dev = p.device
+    c = torch.as_tensor(e.centre, dtype=torch.float64, device=dev)
+    rot = torch.as_tensor(e.rot, dtype=torch.float64, device=dev)
+    a = torch.as_tensor(e.axes, dtype=torch.float64, device=dev)
+    y = ((p - c) @ rot).abs().clamp_min(1e-12)     # an exact zero would leave the root unbracketed
+    g0 = ((y / a) ** 2).sum(1)
+    inside = g0 <= 1.0
+    amin2 = float(a.min()) ** 2
+    lo = torch.where(inside, torch.full_like(g0, -amin2), torch.zeros_like(g0))
+    hi = torch.where(inside, torch.zeros_like(g0), (a * y).norm(dim=1))
+    a2 = a * a
+    for _ in range(100):
+        t = 0.5 * (lo + hi)
+        f = ((a * y / (t[:, None] + a2)) ** 2).sum(1) - 1.0
+        lo = torch.where(f > 0, t, lo)
+        hi = torch.where(f > 0, hi, t)
+    t = 0.5 * (lo + hi)
+    x = torch.nan_to_num(a2 * y / (t[:, None] + a2))
+    return (y - x).norm(dim=1), inside
+
+
+def _surface_error(torch, verts, ellipsoids):
+    """Unsigned distance (m) from each vertex to the surface of the union of
+    the ellipsoids: outside all of them, the nearest surface; inside some,
+    the largest distance to the surface of one that holds it (a lower bound
+    of the distance to the union's boundary)."""
+    p = torch.as_tensor(np.asarray(verts, np.float64), device="cuda")
+    out_d = torch.full((len(p),), float("inf"), dtype=torch.float64, device="cuda")
+    in_d = torch.zeros(len(p), dtype=torch.float64, device="cuda")
+    any_in = torch.zeros(len(p), dtype=torch.bool, device="cuda")
+    for e in ellipsoids:
+        near = ((p - torch.as_tensor(e.centre, device="cuda")).norm(dim=1) <= float(np.max(e.axes)) + 0.3)
+        idx = near.nonzero().squeeze(1)
+        if len(idx) == 0:
+            continue
+        d, ins = _ellipsoid_distance(torch, p[idx], e)
+        out_d[idx] = torch.minimum(out_d[idx], torch.where(ins, torch.full_like(d, float("inf")), d))
+        in_d[idx] = torch.where(ins, torch.maximum(in_d[idx], d), in_d[idx])
+        any_in[idx] |= ins
+    return torch.where(any_in, in_d, out_d).cpu().numpy()
+
+
+def _stats_mm(x):
+    x = np.asarray(x, np.float64) * 1000.0
+    return {"mean": float(x.mean()), "median": float(np.median(x)), "p95": float(np.percentile(x, 95)),
+            "max": float(x.max())}
+
+
+def study_surface(fvv, torch, args):
+    """Sec. II-C: where the three surface rules put the vertices.  Rules:
+    bisection with the configured 10 steps, the paper's pixel walk and
+    minimum ratio (Eqs. (2)-(3)), and the edge midpoint (0 steps, the
+    isovalue 0.5 of conventional marching cubes).  Errors against (i) the
+    crossing of the all-camera predicate along each edge, found by 24
+    bisection steps (within 1 cm / 2^24 of it), and (ii) the analytic
+    surfaces of the ellipsoids the silhouettes were rendered from (which
+    also holds the visual hull's own excess over the objects)."""
+    from dataclasses import replace
+    from synth import make_frame, make_rig
+    base = make_rig(CONFIG)
+    frames = [make_frame(CONFIG, i, device="cuda", rig=base)[1] for i in range(args.study_frames)]
+    rules = {"bisect_10": replace(base, bisect_steps=10), "lambda_eq2_eq3": replace(base, surface_rule=1),
+             "midpoint": replace(base, bisect_steps=0), "_crossing": replace(base, bisect_steps=24)}
+    runs = {k: _timed_reconstruction(fvv, torch, rig, frames, keep_results=True) for k, rig in rules.items()}
+    ref = runs["_crossing"][1]
+    out = {"study": "surface", "workload": WORKLOAD, "frames": len(frames), "rules": {}}
+    for k in ("bisect_10", "lambda_eq2_eq3", "midpoint"):
+        timing, res = runs[k]
+        cross, surf = [], []
+        for fr, rr, r0 in zip(frames, res, ref):
+            v, v0 = rr["verts"].double(), r0["verts"].double()
+            assert v.shape == v0.shape, "the rules share the mesh topology"
+            cross.append((v - v0).norm(dim=1).cpu().numpy())
+            surf.append(_surface_error(torch, rr["verts"].cpu().numpy(), fr.ellipsoids))
+        out["rules"][k] = {"crossing_error_mm": _stats_mm(np.concatenate(cross)),
+                           "object_surface_error_mm": _stats_mm(np.concatenate(surf)),
+                           "surface_step_ms_per_frame": timing["stages_ms_per_frame"]["bisect"],
+                           "surface_step_tests_per_frame": timing["per_frame"]["tests_bisect"],
+                           "verts_per_frame": timing["per_frame"]["n_verts"]}
+    return out
+
+
+def study_fig10(fvv, torch, args):
+    """Fig. 10: per-stage time against the coarse voxel size (20-60 mm, fine
+    20 mm; coarse = fine = 20 mm is the coarse-to-fine scheme switched off)
+    and against the fine voxel size (15-35 mm, coarse 50 mm), on the
+    volleyball-shaped scene."""
+    from dataclasses import replace
+    from synth import make_frame, make_rig
+    base = make_rig(CONFIG)
+    frames = [make_frame(CONFIG, i, device="cuda", rig=base)[1] for i in range(args.study_frames)]
+    out = {"study": "fig10", "workload": WORKLOAD, "frames": len(frames), "coarse_sweep": {}, "fine_sweep": {}}
+    for c in (0.02, 0.03, 0.04, 0.05, 0.06):
+        t, _ = _timed_reconstruction(fvv, torch, replace(base, coarse_m=c, fine_m=0.02), frames)
+        out["coarse_sweep"][f"{round(c * 1000)}mm"] = t
+    for f in (0.015, 0.02, 0.025, 0.03, 0.035):
+        t, _ = _timed_reconstruction(fvv, torch, replace(base, coarse_m=0.05, fine_m=f), frames)
+        out["fine_sweep"][f"{round(f * 1000)}mm"] = t
+    return out
+
+
+# the paper's own per-stage times (Table II) and totals (Table I), GTX 1080 Ti,
+# real footage: context for the Table I shapes, not a target
+PAPER_TABLE = {"volleyball_t1": {"B-1": 0.54, "B-2": 21.49, "B-3": 1.23, "C": 3.90, "D-1": 5.93, "D-2": 3.30,
+                                 "total": 36.39},
+               "judo_t1": {"B-1": 0.06, "B-2": 2.11, "B-3": 0.23, "C": 0.65, "D-1": 2.99, "D-2": 1.26,
+                           "total": 7.30}}
+
+
+def study_table1(fvv, torch, args):
+    """The capture shapes of Table I on synthetic scenes: volleyball (10
+    cameras 4K, 18 x 18 x 9 m, 50/20 mm) and judo (16 cameras 1080p,
+    5 x 6 x 2.1 m, 80/40 mm); per-stage time in the Table II buckets beside
+    the paper's numbers (GTX 1080 Ti, real footage: context only)."""
+    from synth import make_frame, make_rig
+    out = {"study": "table1", "frames": args.study_frames, "shapes": {}}
+    for cfg in ("volleyball_t1", "judo_t1"):
+        rig = make_rig(cfg)
+        frames = [make_frame(cfg, i, device="cuda", rig=rig)[1] for i in range(args.study_frames)]
+        t, _ = _timed_reconstruction(fvv, torch, rig, frames)
+        t["paper_gtx1080ti_ms"] = PAPER_TABLE[cfg]
+        out["shapes"][cfg] = t
+    return out
+
+
+def run_study(args):
+    import torch
+    assert torch.cuda.is_available(), "the studies need a CUDA GPU"
+    from paper_1903_11785_gb300.build import build
+    build()
+    from paper_1903_11785_gb300 import fvv
+    fn = {"surface": study_surface, "fig10": study_fig10, "table1": study_table1}[args.study]
+    print(json.dumps(fn(fvv, torch, args)), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.study:
+        return run_study(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

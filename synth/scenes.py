@@ -177,6 +177,25 @@ def make_rig(config: str) -> Rig:
               for k in range(n)]
         return _make_rig("judo", cs, [(0, 0, 0.8)] * n, 3600.0, 3840, 2160, g,
                          (-6.0, -6.0, 0.0), (6.0, 6.0, 3.0), 0.04, 0.005, 12)
+    if config == "volleyball_t1":
+        # the paper's volleyball capture shape (Table I): 10 cameras at 4K,
+        # an 18 x 18 x 9 m volume, 50 mm coarse and 20 mm fine voxels
+        n = 10
+        cs = []
+        for k in range(n):
+            a = 2 * math.pi * (k + 0.5) / n
+            hgt = 6.0 + 4.0 * float(torch.rand(1, generator=g, dtype=torch.float64))
+            cs.append((30.0 * math.cos(a), 20.0 * math.sin(a), hgt))
+        return _make_rig("volleyball_t1", cs, [(0, 0, 1.0)] * n, 3600.0, 3840, 2160, g,
+                         (-9.0, -9.0, 0.0), (9.0, 9.0, 9.0), 0.05, 0.02, 10)
+    if config == "judo_t1":
+        # the paper's judo capture shape (Table I): 16 cameras at 1080p, a
+        # 5 x 6 x 2.1 m volume, 80 mm coarse and 40 mm fine voxels
+        n, r, h = 16, 14.0, 6.0
+        cs = [(r * math.cos(2 * math.pi * (k + 0.25) / n), r * math.sin(2 * math.pi * (k + 0.25) / n), h)
+              for k in range(n)]
+        return _make_rig("judo_t1", cs, [(0, 0, 0.8)] * n, 1800.0, 1920, 1080, g,
+                         (-2.5, -3.0, 0.0), (2.5, 3.0, 2.1), 0.08, 0.04, 10)
     if config == "hd720":
         n, r, h = 8, 8.0, 4.0
         cs = [(r * math.cos(2 * math.pi * (k + 0.5) / n), r * math.sin(2 * math.pi * (k + 0.5) / n), h)
@@ -224,6 +243,19 @@ def scene_objects(config: str, index: int = 0):
     if config == "tiny":
         pos = (_u(g, -1.5, 1.5), _u(g, -1.5, 1.5))
         return player(pos, _u(g, 0, 2 * math.pi), 1.8, g)
+    if config == "volleyball_t1":
+        return scene_objects("volleyball", index)
+    if config == "judo_t1":
+        # the judo pair near the middle of the 5 x 6 m volume and the referee
+        # 2 m from it along y, on the side with more room
+        cx, cy = _u(g, -0.5, 0.5), _u(g, -0.5, 0.5)
+        yaw = _u(g, 0, 2 * math.pi)
+        d = np.array([math.cos(yaw), math.sin(yaw)]) * 0.225
+        objs = player((cx - d[0], cy - d[1]), yaw, _u(g, 1.7, 1.9), g, obj=0)
+        objs += player((cx + d[0], cy + d[1]), yaw + math.pi, _u(g, 1.7, 1.9), g, obj=1)
+        side = -1.0 if cy > 0 else 1.0
+        objs += player((cx + _u(g, -0.3, 0.3), cy + 2.0 * side), _u(g, 0, 2 * math.pi), 1.75, g, obj=2)
+        return objs
     if config == "volleyball":
         objs, placed = [], []
         for p in range(12):
