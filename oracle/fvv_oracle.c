@@ -24,6 +24,7 @@
  *   Sec. II-D-1  depth image per camera, Eq. (4)       orc_depth
  *   Sec. II-D-2/E visibility by T_v and colour from the
  *                nearest visible camera               orc_colour
+ *   Sec. II-E    a novel view of the coloured mesh    orc_render_view
  *
  * Readings of the paper used here (each is also listed with the design notes):
  *  - A voxel is tested at its centre c = o + (i + 1/2) s (Sec. II-B-1 says
@@ -852,7 +853,7 @@ int orc_mesh_one(const orc_rig *rig, const uint8_t *const *masks, const orc_roi 
     return 0;
 }
 
-/* -------------------------------------------- Sec. II-D-1: depth image, Eq. (4) */
+/* ------------------------ Sec. II-D-1: which pixels a projected triangle covers */
 
 /* For camera n, every triangle whose three vertices are in front of it
  * (w' > 0) and whose projected area is non-zero writes, into each pixel whose
@@ -868,7 +869,98 @@ int orc_mesh_one(const orc_rig *rig, const uint8_t *const *masks, const orc_roi 
  * all <= 0.  The projected area is zero iff (x_0 a_12 - y_0 b_12) + w_0 c_12
  * is.  Only pixel centres inside the closed box spanned by the projected
  * vertices are tested; that box is decided exactly, by the signs of
- * p_x w_j - x_j (and p_y w_j - y_j) formed with one fma each. */
+ * p_x w_j - x_j (and p_y w_j - y_j) formed with one fma each.
+ *
+ * tri_cover holds one projected triangle set up for that test: the
+ * homogeneous image points of camera matrix p, the edge functions of edges
+ * (0,1), (1,2), (2,0), and the candidate pixel box. */
+typedef struct {
+    R xh[3], yh[3], wh[3], ea[3], eb[3], ec[3];
+    int x0, y0, x1, y1;
+} tri_cover;
+
+/* Set up triangle (X, Y, Z) in the view of matrix p (image W x H).  Returns
+ * 0 if the triangle is skipped: a vertex not in front (w' <= 0), zero
+ * projected area, or a box entirely off the image. */
+static int cover_setup(const float *p, int W, int H, const R *X, const R *Y, const R *Z, tri_cover *t)
+{
+    for (int j = 0; j < 3; ++j) {
+        t->xh[j] = (((R)p[0] * X[j] + (R)p[1] * Y[j]) + (R)p[2] * Z[j]) + (R)p[3];
+        t->yh[j] = (((R)p[4] * X[j] + (R)p[5] * Y[j]) + (R)p[6] * Z[j]) + (R)p[7];
+        t->wh[j] = (((R)p[8] * X[j] + (R)p[9] * Y[j]) + (R)p[10] * Z[j]) + (R)p[11];
+        if (!(t->wh[j] > (R)0)) return 0;
+    }
+    for (int e = 0; e < 3; ++e) {
+        int i = e, j = (e + 1) % 3;
+        t->ea[e] = t->yh[i] * t->wh[j] - t->wh[i] * t->yh[j];
+        t->eb[e] = t->xh[i] * t->wh[j] - t->wh[i] * t->xh[j];
+        t->ec[e] = t->xh[i] * t->yh[j] - t->yh[i] * t->xh[j];
+    }
+    R det = (t->xh[0] * t->ea[1] - t->yh[0] * t->eb[1]) + t->wh[0] * t->ec[1];
+    if (!(det > (R)0 || det < (R)0)) return 0;
+    /* candidate pixels: the projected box widened by one pixel (any superset
+     * of the box gives the same coverage) */
+    double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
+    for (int j = 0; j < 3; ++j) {
+        double u = (double)t->xh[j] / (double)t->wh[j], v = (double)t->yh[j] / (double)t->wh[j];
+        if (u < umin) umin = u;
+        if (u > umax) umax = u;
+        if (v < vmin) vmin = v;
+        if (v > vmax) vmax = v;
+    }
+    if (umax < 0.0 || vmax < 0.0 || umin > (double)W || vmin > (double)H) return 0;
+    t->x0 = umin < 1.0 ? 0 : (int)floor(umin) - 1;
+    t->y0 = vmin < 1.0 ? 0 : (int)floor(vmin) - 1;
+    t->x1 = umax > (double)W - 2.0 ? W - 1 : (int)floor(umax) + 1;
+    t->y1 = vmax > (double)H - 2.0 ? H - 1 : (int)floor(vmax) + 1;
+    return 1;
+}
+
+/* Row yy of the candidate box: is the pixel-centre row inside the closed
+ * box of the projection (signs of pcy*w_j - y_j, exact by one fma)? */
+static int cover_row(const tri_cover *t, int yy)
+{
+    R pcy = (R)yy + (R)0.5;
+    R s0 = fma(pcy, t->wh[0], -t->yh[0]), s1 = fma(pcy, t->wh[1], -t->yh[1]), s2 = fma(pcy, t->wh[2], -t->yh[2]);
+    return (s0 >= (R)0 || s1 >= (R)0 || s2 >= (R)0) && (s0 <= (R)0 || s1 <= (R)0 || s2 <= (R)0);
+}
+
+/* Pixel (xx, yy) of a row that passed cover_row: centre in the closed box
+ * and on the inner side of (or on) all three edges, either winding. */
+static int cover_pixel(const tri_cover *t, int xx, int yy)
+{
+    R pcy = (R)yy + (R)0.5, pcx = (R)xx + (R)0.5;
+    R r0 = fma(pcx, t->wh[0], -t->xh[0]), r1 = fma(pcx, t->wh[1], -t->xh[1]), r2 = fma(pcx, t->wh[2], -t->xh[2]);
+    if (!((r0 >= (R)0 || r1 >= (R)0 || r2 >= (R)0) && (r0 <= (R)0 || r1 <= (R)0 || r2 <= (R)0))) return 0;
+    R e0 = (pcx * t->ea[0] - pcy * t->eb[0]) + t->ec[0];
+    R e1 = (pcx * t->ea[1] - pcy * t->eb[1]) + t->ec[1];
+    R e2 = (pcx * t->ea[2] - pcy * t->eb[2]) + t->ec[2];
+    return (e0 >= (R)0 && e1 >= (R)0 && e2 >= (R)0) || (e0 <= (R)0 && e1 <= (R)0 && e2 <= (R)0);
+}
+
+/* Triangle t's vertices and centroid ((v0 + v1) + v2) / 3 (Sec. II-D-1). */
+static int tri_points(long long n_verts, const double *verts, const uint32_t *tris, long long t, R *X, R *Y, R *Z,
+                      R *g)
+{
+    for (int j = 0; j < 3; ++j) {
+        uint32_t vi = tris[3 * t + j];
+        if ((long long)vi >= n_verts) return -1;
+        X[j] = (R)verts[3 * vi]; Y[j] = (R)verts[3 * vi + 1]; Z[j] = (R)verts[3 * vi + 2];
+    }
+    g[0] = ((X[0] + X[1]) + X[2]) / (R)3;
+    g[1] = ((Y[0] + Y[1]) + Y[2]) / (R)3;
+    g[2] = ((Z[0] + Z[1]) + Z[2]) / (R)3;
+    return 0;
+}
+
+/* ------------------------------------------ Sec. II-D-1: depth images, Eq. (4) */
+
+/* Per camera, each pixel holds the minimum over the triangles covering it of
+ * the distance from the triangle's centroid to the camera centre, +inf if
+ * none.  A pixel is covered when its centre lies inside or on the projected
+ * triangle, decided on the homogeneous image points without dividing
+ * (cover_setup, cover_row, cover_pixel); triangles with a vertex behind the
+ * camera or zero projected area are skipped. */
 int orc_depth(const orc_rig *rig, long long n_verts, const double *verts,
               long long n_tris, const uint32_t *tris, R *depth)
 {
@@ -881,65 +973,16 @@ int orc_depth(const orc_rig *rig, long long n_verts, const double *verts,
         const float *p = rig->P + 12 * n;
         R Cx = (R)rig->centre[3 * n], Cy = (R)rig->centre[3 * n + 1], Cz = (R)rig->centre[3 * n + 2];
         for (long long t = 0; t < n_tris; ++t) {
-            R X[3], Y[3], Z[3], xh[3], yh[3], wh[3];
-            int ok = 1;
-            for (int j = 0; j < 3; ++j) {
-                uint32_t vi = tris[3 * t + j];
-                if ((long long)vi >= n_verts) return -1;
-                X[j] = (R)verts[3 * vi]; Y[j] = (R)verts[3 * vi + 1]; Z[j] = (R)verts[3 * vi + 2];
-                xh[j] = (((R)p[0] * X[j] + (R)p[1] * Y[j]) + (R)p[2] * Z[j]) + (R)p[3];
-                yh[j] = (((R)p[4] * X[j] + (R)p[5] * Y[j]) + (R)p[6] * Z[j]) + (R)p[7];
-                wh[j] = (((R)p[8] * X[j] + (R)p[9] * Y[j]) + (R)p[10] * Z[j]) + (R)p[11];
-                if (!(wh[j] > (R)0)) { ok = 0; break; }
-            }
-            if (!ok) continue;
-            /* homogeneous edge functions of edges (0,1), (1,2), (2,0) */
-            R ea[3], eb[3], ec[3];
-            for (int e = 0; e < 3; ++e) {
-                int i = e, j = (e + 1) % 3;
-                ea[e] = yh[i] * wh[j] - wh[i] * yh[j];
-                eb[e] = xh[i] * wh[j] - wh[i] * xh[j];
-                ec[e] = xh[i] * yh[j] - yh[i] * xh[j];
-            }
-            R det = (xh[0] * ea[1] - yh[0] * eb[1]) + wh[0] * ec[1];
-            if (!(det > (R)0 || det < (R)0)) continue;
-            R gx = ((X[0] + X[1]) + X[2]) / (R)3;
-            R gy = ((Y[0] + Y[1]) + Y[2]) / (R)3;
-            R gz = ((Z[0] + Z[1]) + Z[2]) / (R)3;
-            R dx = gx - Cx, dy = gy - Cy, dz = gz - Cz;
+            R X[3], Y[3], Z[3], g[3];
+            if (tri_points(n_verts, verts, tris, t, X, Y, Z, g)) return -1;
+            tri_cover tc;
+            if (!cover_setup(p, W, H, X, Y, Z, &tc)) continue;
+            R dx = g[0] - Cx, dy = g[1] - Cy, dz = g[2] - Cz;
             R d = sqrt((dx * dx + dy * dy) + dz * dz);
-            /* candidate pixels: the projected box widened by one pixel (any
-             * superset of the box gives the same image) */
-            double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
-            for (int j = 0; j < 3; ++j) {
-                double u = (double)xh[j] / (double)wh[j], v = (double)yh[j] / (double)wh[j];
-                if (u < umin) umin = u;
-                if (u > umax) umax = u;
-                if (v < vmin) vmin = v;
-                if (v > vmax) vmax = v;
-            }
-            if (umax < 0.0 || vmax < 0.0 || umin > (double)W || vmin > (double)H) continue;
-            int x0 = umin < 1.0 ? 0 : (int)floor(umin) - 1;
-            int y0 = vmin < 1.0 ? 0 : (int)floor(vmin) - 1;
-            int x1 = umax > (double)W - 2.0 ? W - 1 : (int)floor(umax) + 1;
-            int y1 = vmax > (double)H - 2.0 ? H - 1 : (int)floor(vmax) + 1;
-            for (int yy = y0; yy <= y1; ++yy) {
-                R pcy = (R)yy + (R)0.5;
-                /* pcy within [min v_j, max v_j]: signs of pcy*w_j - y_j, exact by one fma */
-                R s0 = fma(pcy, wh[0], -yh[0]), s1 = fma(pcy, wh[1], -yh[1]), s2 = fma(pcy, wh[2], -yh[2]);
-                if (!((s0 >= (R)0 || s1 >= (R)0 || s2 >= (R)0) && (s0 <= (R)0 || s1 <= (R)0 || s2 <= (R)0)))
-                    continue;
-                for (int xx = x0; xx <= x1; ++xx) {
-                    R pcx = (R)xx + (R)0.5;
-                    R r0 = fma(pcx, wh[0], -xh[0]), r1 = fma(pcx, wh[1], -xh[1]), r2 = fma(pcx, wh[2], -xh[2]);
-                    if (!((r0 >= (R)0 || r1 >= (R)0 || r2 >= (R)0) && (r0 <= (R)0 || r1 <= (R)0 || r2 <= (R)0)))
-                        continue;
-                    R e0 = (pcx * ea[0] - pcy * eb[0]) + ec[0];
-                    R e1 = (pcx * ea[1] - pcy * eb[1]) + ec[1];
-                    R e2 = (pcx * ea[2] - pcy * eb[2]) + ec[2];
-                    int inside = (e0 >= (R)0 && e1 >= (R)0 && e2 >= (R)0) ||
-                                 (e0 <= (R)0 && e1 <= (R)0 && e2 <= (R)0);
-                    if (!inside) continue;
+            for (int yy = tc.y0; yy <= tc.y1; ++yy) {
+                if (!cover_row(&tc, yy)) continue;
+                for (int xx = tc.x0; xx <= tc.x1; ++xx) {
+                    if (!cover_pixel(&tc, xx, yy)) continue;
                     R *px = &D[(size_t)yy * W + xx];
                     if (d < *px) *px = d;
                 }
@@ -951,21 +994,14 @@ int orc_depth(const orc_rig *rig, long long n_verts, const double *verts,
 
 /* ------------------------ Sec. II-D-2 and II-E: visibility and vertex colour */
 
-/* Cameras are ranked by squared distance from their centre to the virtual
- * viewpoint ((dx*dx + dy*dy) + dz*dz), ties to the lower index.  A vertex
- * takes the first camera in rank order that has it in front (w' > 0), inside
- * the image, and not occluded: |v - C| - depth[pixel] <= T_v.  Its colour is
- * that camera's RGB at the pixel; with no such camera it is (0,0,0) and the
- * camera index is -1. */
-int orc_colour(const orc_rig *rig, const uint8_t *const *rgb, const float *viewpoint,
-               const R *depth, long long n_verts, const double *verts,
-               uint8_t *out_rgb, int32_t *out_cam)
+/* Capture cameras ranked by squared distance from their centre to the
+ * viewpoint ((dx*dx + dy*dy) + dz*dz), ties to the lower index; doff[n] is
+ * camera n's first pixel in the concatenated depth images. */
+static int rank_cameras(const orc_rig *rig, const float *viewpoint, int *rank, size_t *doff)
 {
     int N = rig->n_cams;
-    int *rank = (int *)malloc((size_t)N * sizeof(int));
     R *d2 = (R *)malloc((size_t)N * sizeof(R));
-    size_t *doff = (size_t *)malloc((size_t)N * sizeof(size_t));
-    if (!rank || !d2 || !doff) { free(rank); free(d2); free(doff); return -1; }
+    if (!d2) return -1;
     size_t off = 0;
     for (int n = 0; n < N; ++n) {
         R dx = (R)rig->centre[3 * n] - (R)viewpoint[0];
@@ -981,34 +1017,107 @@ int orc_colour(const orc_rig *rig, const uint8_t *const *rgb, const float *viewp
         while (j >= 0 && d2[rank[j]] > d2[c]) { rank[j + 1] = rank[j]; --j; }
         rank[j + 1] = c;
     }
+    free(d2);
+    return 0;
+}
+
+/* The colour of world point (X,Y,Z): the first camera in rank order that
+ * has it in front (w' > 0), inside the image, and not occluded:
+ * |X - C| - depth[pixel] <= T_v.  Returns that camera (its RGB at the pixel
+ * in out3) or -1 with (0,0,0). */
+static int colour_point(const orc_rig *rig, const uint8_t *const *rgb, const int *rank, const size_t *doff,
+                        const R *depth, R X, R Y, R Z, uint8_t *out3)
+{
+    out3[0] = out3[1] = out3[2] = 0;
     R tv = (R)rig->t_v;
-    for (long long i = 0; i < n_verts; ++i) {
-        R X = (R)verts[3 * i], Y = (R)verts[3 * i + 1], Z = (R)verts[3 * i + 2];
-        out_rgb[3 * i] = out_rgb[3 * i + 1] = out_rgb[3 * i + 2] = 0;
-        out_cam[i] = -1;
-        for (int r = 0; r < N; ++r) {
-            int n = rank[r];
-            const float *p = rig->P + 12 * n;
-            R xp = (((R)p[0] * X + (R)p[1] * Y) + (R)p[2] * Z) + (R)p[3];
-            R yp = (((R)p[4] * X + (R)p[5] * Y) + (R)p[6] * Z) + (R)p[7];
-            R wp = (((R)p[8] * X + (R)p[9] * Y) + (R)p[10] * Z) + (R)p[11];
-            if (!(wp > (R)0)) continue;
-            double fu = pixel_floor(xp, wp), fv = pixel_floor(yp, wp);
-            int W = rig->width[n], H = rig->height[n];
-            if (!(fu >= 0.0 && fu < (double)W && fv >= 0.0 && fv < (double)H)) continue;
-            size_t pix = (size_t)(int)fv * W + (size_t)(int)fu;
-            R dx = X - (R)rig->centre[3 * n], dy = Y - (R)rig->centre[3 * n + 1],
-              dz = Z - (R)rig->centre[3 * n + 2];
-            R dist = sqrt((dx * dx + dy * dy) + dz * dz);
-            if (!(dist - depth[doff[n] + pix] <= tv)) continue;
-            out_rgb[3 * i + 0] = rgb[n][3 * pix + 0];
-            out_rgb[3 * i + 1] = rgb[n][3 * pix + 1];
-            out_rgb[3 * i + 2] = rgb[n][3 * pix + 2];
-            out_cam[i] = n;
-            break;
+    for (int r = 0; r < rig->n_cams; ++r) {
+        int n = rank[r];
+        const float *p = rig->P + 12 * n;
+        R xp = (((R)p[0] * X + (R)p[1] * Y) + (R)p[2] * Z) + (R)p[3];
+        R yp = (((R)p[4] * X + (R)p[5] * Y) + (R)p[6] * Z) + (R)p[7];
+        R wp = (((R)p[8] * X + (R)p[9] * Y) + (R)p[10] * Z) + (R)p[11];
+        if (!(wp > (R)0)) continue;
+        double fu = pixel_floor(xp, wp), fv = pixel_floor(yp, wp);
+        int W = rig->width[n], H = rig->height[n];
+        if (!(fu >= 0.0 && fu < (double)W && fv >= 0.0 && fv < (double)H)) continue;
+        size_t pix = (size_t)(int)fv * W + (size_t)(int)fu;
+        R dx = X - (R)rig->centre[3 * n], dy = Y - (R)rig->centre[3 * n + 1], dz = Z - (R)rig->centre[3 * n + 2];
+        R dist = sqrt((dx * dx + dy * dy) + dz * dz);
+        if (!(dist - depth[doff[n] + pix] <= tv)) continue;
+        out3[0] = rgb[n][3 * pix + 0];
+        out3[1] = rgb[n][3 * pix + 1];
+        out3[2] = rgb[n][3 * pix + 2];
+        return n;
+    }
+    return -1;
+}
+
+/* Per vertex: colour_point with the cameras ranked for the viewpoint. */
+int orc_colour(const orc_rig *rig, const uint8_t *const *rgb, const float *viewpoint,
+               const R *depth, long long n_verts, const double *verts,
+               uint8_t *out_rgb, int32_t *out_cam)
+{
+    int N = rig->n_cams;
+    int *rank = (int *)malloc((size_t)N * sizeof(int));
+    size_t *doff = (size_t *)malloc((size_t)N * sizeof(size_t));
+    if (!rank || !doff || rank_cameras(rig, viewpoint, rank, doff)) { free(rank); free(doff); return -1; }
+    for (long long i = 0; i < n_verts; ++i)
+        out_cam[i] = colour_point(rig, rgb, rank, doff, depth, (R)verts[3 * i], (R)verts[3 * i + 1],
+                                  (R)verts[3 * i + 2], out_rgb + 3 * i);
+    free(rank); free(doff);
+    return 0;
+}
+
+/* -------------------------------- Sec. II-E: rendering a novel view (step E) */
+
+/* The coloured mesh seen from a virtual camera (matrix Pv, centre Cv, image
+ * Wv x Hv).  Visibility: each pixel of the view keeps, among the triangles
+ * covering it (the coverage test of the depth images), the one with the
+ * smallest squared distance from its centroid to Cv ((dx*dx + dy*dy) +
+ * dz*dz), ties to the lower triangle index; out_tri gets its index (-1 for
+ * none) and out_d2 that squared distance (+inf for none).  Colour: the
+ * pixel takes colour_point of that triangle's centroid with the capture
+ * cameras ranked for the viewpoint Cv -- the nearest capture camera that
+ * sees the surface point unoccluded, else the next ones (Sec. II-E) -- so
+ * the camera is chosen per pixel; out_cam gets it (-1 for none or an empty
+ * pixel, whose colour is (0,0,0)).  `depth` holds the capture cameras'
+ * depth images (orc_depth). */
+int orc_render_view(const orc_rig *rig, const uint8_t *const *rgb, const R *depth, long long n_verts,
+                    const double *verts, long long n_tris, const uint32_t *tris, const float *Pv, const float *Cv,
+                    int Wv, int Hv, int64_t *out_tri, R *out_d2, uint8_t *out_rgb, int32_t *out_cam)
+{
+    size_t np = (size_t)Wv * Hv;
+    for (size_t i = 0; i < np; ++i) { out_tri[i] = -1; out_d2[i] = (R)INFINITY; }
+    R cx = (R)Cv[0], cy = (R)Cv[1], cz = (R)Cv[2];
+    for (long long t = 0; t < n_tris; ++t) {
+        R X[3], Y[3], Z[3], g[3];
+        if (tri_points(n_verts, verts, tris, t, X, Y, Z, g)) return -1;
+        tri_cover tc;
+        if (!cover_setup(Pv, Wv, Hv, X, Y, Z, &tc)) continue;
+        R dx = g[0] - cx, dy = g[1] - cy, dz = g[2] - cz;
+        R d2 = (dx * dx + dy * dy) + dz * dz;
+        for (int yy = tc.y0; yy <= tc.y1; ++yy) {
+            if (!cover_row(&tc, yy)) continue;
+            for (int xx = tc.x0; xx <= tc.x1; ++xx) {
+                if (!cover_pixel(&tc, xx, yy)) continue;
+                size_t i = (size_t)yy * Wv + xx;
+                if (d2 < out_d2[i]) { out_d2[i] = d2; out_tri[i] = t; } /* t increases: ties keep the lower */
+            }
         }
     }
-    free(rank); free(d2); free(doff);
+    int N = rig->n_cams;
+    int *rank = (int *)malloc((size_t)N * sizeof(int));
+    size_t *doff = (size_t *)malloc((size_t)N * sizeof(size_t));
+    if (!rank || !doff || rank_cameras(rig, Cv, rank, doff)) { free(rank); free(doff); return -1; }
+    for (size_t i = 0; i < np; ++i) {
+        out_cam[i] = -1;
+        out_rgb[3 * i] = out_rgb[3 * i + 1] = out_rgb[3 * i + 2] = 0;
+        if (out_tri[i] < 0) continue;
+        R X[3], Y[3], Z[3], g[3];
+        tri_points(n_verts, verts, tris, out_tri[i], X, Y, Z, g);
+        out_cam[i] = colour_point(rig, rgb, rank, doff, depth, g[0], g[1], g[2], out_rgb + 3 * i);
+    }
+    free(rank); free(doff);
     return 0;
 }
 

@@ -337,3 +337,30 @@ class Oracle:
                             C.c_longlong(len(verts)), _p(verts, C.c_double), _p(out, C.c_uint8),
                             _p(cam, C.c_int32))
         return out, cam
+
+    # -- Sec. II-E, step E: a novel view
+    def render_view(self, rgb, depth, verts, tris, P, centre, width, height):
+        """The coloured mesh seen from a virtual camera (3x4 matrix P, centre,
+        image width x height): per pixel the nearest covering triangle (by
+        squared centroid distance, ties to the lower index) and the colour of
+        its centroid from the nearest capture camera that sees it unoccluded.
+        Returns (triangle index (H,W) int64, -1 = none; squared distance
+        (H,W), +inf = none; RGB (H,W,3) uint8; capture camera (H,W) int32)."""
+        arrs, ptrs = self._images(rgb)
+        verts = np.ascontiguousarray(np.asarray(verts, np.float64))
+        tris = np.ascontiguousarray(np.asarray(tris, np.uint32))
+        dep = np.ascontiguousarray(np.concatenate([np.asarray(d, self.real).ravel() for d in depth]))
+        Pv = np.ascontiguousarray(np.asarray(P, np.float32).reshape(12))
+        Cv = np.ascontiguousarray(np.asarray(centre, np.float32).reshape(3))
+        tri = np.empty((height, width), np.int64)
+        d2 = np.empty((height, width), self.real)
+        out = np.empty((height, width, 3), np.uint8)
+        cam = np.empty((height, width), np.int32)
+        ctype = C.c_float if self.prec == "f32" else C.c_double
+        rc = self.lib.orc_render_view(C.byref(self._rig), ptrs, _p(dep, ctype), C.c_longlong(len(verts)),
+                                      _p(verts, C.c_double), C.c_longlong(len(tris)), _p(tris, C.c_uint32),
+                                      _p(Pv, C.c_float), _p(Cv, C.c_float), C.c_int(width), C.c_int(height),
+                                      _p(tri, C.c_int64), _p(d2, ctype), _p(out, C.c_uint8), _p(cam, C.c_int32))
+        if rc:
+            raise ValueError("triangle index out of range")
+        return tri, d2, out, cam
