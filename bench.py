@@ -69,10 +69,11 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--study", choices=("surface", "fig10", "table1"), default=None,
+    ap.add_argument("--study", choices=("surface", "fig10", "table1", "view"), default=None,
                     help="instead of the benchmark line: surface-rule errors (Sec. II-C), the coarse/fine "
-                         "voxel-size sweeps of Fig. 10, or the Table I capture shapes")
+                         "voxel-size sweeps of Fig. 10, the Table I capture shapes, or novel-view rendering")
     ap.add_argument("--study-frames", type=int, default=4)
+    ap.add_argument("--study-image", default=None, help="--study view: write the first view here (PPM)")
     return ap.parse_args()
 
 
@@ -736,13 +737,60 @@ def study_table1(fvv, torch, args):
     return out
 
 
+def study_view(fvv, torch, args):
+    """Step E (Sec. II-E): novel 1920x1080 views of reconstructed
+    volleyball-shaped frames from a virtual camera between two capture
+    cameras; device time per view (events), covered pixels and how many
+    pixels each capture camera coloured."""
+    from synth import default_viewpoint, look_at_camera, make_frame, make_rig
+    rig = make_rig(CONFIG)
+    F = args.study_frames
+    frames = [make_frame(CONFIG, i, device="cuda", rig=rig)[1] for i in range(F)]
+    W, H = 1920, 1080
+    r = fvv.Rig(rig, max_slots=F, host_staging=0)
+    try:
+        for i, fr in enumerate(frames):
+            r.upload_silhouettes(i, fr.masks)
+        r.reconstruct(list(range(F)))
+        views = []
+        for i in range(F):
+            C = default_viewpoint(rig, i)
+            _, _, P = look_at_camera(np.asarray(C, np.float64), np.array([0.0, 0.0, 1.0]), 1800.0, W, H)
+            views.append((P.astype(np.float32), np.asarray(C, np.float32)))
+        for i in range(F):                                      # warm-up
+            r.render_view(i, frames[i].rgb, *views[i], W, H)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        a.record()
+        for _ in range(reps):
+            for i in range(F):
+                key, img, cam = r.render_view(i, frames[i].rgb, *views[i], W, H)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / (reps * F)
+        key, img, cam = r.render_view(0, frames[0].rgb, *views[0], W, H)
+        cam = cam.cpu().numpy()
+        covered = int((key != -1).sum())
+        if args.study_image:
+            with open(args.study_image, "wb") as fh:
+                fh.write(b"P6 %d %d 255\n" % (W, H))
+                fh.write(img.cpu().numpy().tobytes())
+        return {"study": "view", "workload": WORKLOAD, "view": [W, H], "frames": F, "ms_per_view": ms,
+                "views_per_s": 1000.0 / ms, "covered_pixels": covered,
+                "pixels_per_capture_camera": {int(c): int((cam == c).sum()) for c in np.unique(cam) if c >= 0},
+                "uncoloured_pixels": int(((cam < 0) & (key.cpu().numpy() != -1)).sum())}
+    finally:
+        r.close()
+
+
 def run_study(args):
     import torch
     assert torch.cuda.is_available(), "the studies need a CUDA GPU"
     from paper_1903_11785_gb300.build import build
     build()
     from paper_1903_11785_gb300 import fvv
-    fn = {"surface": study_surface, "fig10": study_fig10, "table1": study_table1}[args.study]
+    fn = {"surface": study_surface, "fig10": study_fig10, "table1": study_table1, "view": study_view}[args.study]
     print(json.dumps(fn(fvv, torch, args)), flush=True)
     return 0
 

@@ -285,6 +285,35 @@ enum {
     FVV_N_STAGES = 8
 };
 
+/* Step E (Sec. II-E): render a novel view of a reconstructed slot's coloured
+ * mesh into a headless image, from a virtual camera with row-major 3x4
+ * matrix P (world -> pixel, as for the rig's cameras) and centre `centre`,
+ * width x height pixels.  Visibility: each pixel keeps, among the mesh
+ * triangles whose projection covers its centre (the coverage test of the
+ * depth images), the one with the smallest squared distance from its
+ * centroid to `centre`, ties to the lower triangle index.  Colour: that
+ * triangle's centroid takes the colour rule of fvv_colour with the capture
+ * cameras ranked for the viewpoint `centre` -- the nearest capture camera
+ * that sees the point unoccluded (|X - C| - depth <= t_v), else the next
+ * ones -- so the capture camera is chosen per pixel.
+ *   rgb      n_cams capture images (H x W x 3 uint8 each), device pointers
+ *            if rgb_on_device, else host (needs host_staging; copied into the
+ *            slot's staging, which this call then overwrites);
+ *   P, centre  host arrays of 12 and 3 finite floats;
+ *   key      device, width*height uint64, written: per pixel (squared
+ *            distance as float bits) << 32 | triangle index within the slot's
+ *            mesh, all ones where no triangle covers the pixel;
+ *   out_rgb  device, width*height*3 uint8, written ((0,0,0) where empty or
+ *            no camera sees the point);
+ *   out_cam  device, width*height int32, or NULL: the capture camera per
+ *            pixel, -1 where none.
+ * The slot must hold a reconstruction (FVV_ERR_NOT_READY otherwise); its
+ * depth images and mesh are read, not changed.  All buffers are the caller's;
+ * work is enqueued on `stream`. */
+fvv_status fvv_render_view(fvv_rig *rig, int slot, const uint8_t *const *rgb, int rgb_on_device, const float *P,
+                           const float *centre, int width, int height, uint64_t *key, uint8_t *out_rgb,
+                           int32_t *out_cam, void *stream);
+
 /* Switch per-stage timing on (1) or off (0).  When on, each call records CUDA
  * events around its stages on its stream (no synchronisation). */
 fvv_status fvv_set_timing(fvv_rig *rig, int enable);

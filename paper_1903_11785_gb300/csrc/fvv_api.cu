@@ -595,6 +595,53 @@ fvv_status fvv_colour(fvv_rig* rig, const int* slots, int n_slots, const uint8_t
     return FVV_OK;
 }
 
+fvv_status fvv_render_view(fvv_rig* rig, int slot, const uint8_t* const* rgb, int rgb_on_device, const float* P,
+                           const float* centre, int width, int height, uint64_t* key, uint8_t* out_rgb,
+                           int32_t* out_cam, void* stream) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    SlotList sl;
+    fvv_status s = make_slot_list(rig, &slot, 1, 2, sl);
+    if (s != FVV_OK) return s;
+    if (!rgb || !P || !centre || !key || !out_rgb)
+        return fail(rig, FVV_ERR_INVALID_ARG, "rgb, P, centre, key and out_rgb must not be NULL");
+    if (width < 1 || height < 1 || width > 65535 || height > 65535)
+        return fail(rig, FVV_ERR_INVALID_ARG, "view size must be 1..65535 pixels per side");
+    if (!rgb_on_device && !rig->host_staging) return fail(rig, FVV_ERR_INVALID_ARG, "host RGB needs host_staging");
+    for (int i = 0; i < 12; ++i)
+        if (!std::isfinite(P[i])) return fail(rig, FVV_ERR_INVALID_ARG, "P must be finite");
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(centre[i])) return fail(rig, FVV_ERR_INVALID_ARG, "centre must be finite");
+    const int N = rig->cams.n;
+    for (int n = 0; n < N; ++n)
+        if (!rgb[n]) return fail(rig, FVV_ERR_INVALID_ARG, "an rgb pointer is NULL");
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ViewArgs va;
+    std::memset(&va, 0, sizeof(va));
+    for (int i = 0; i < 12; ++i) va.v.P[i] = P[i];
+    for (int i = 0; i < 3; ++i) va.v.C[i] = centre[i];
+    va.v.W = width;
+    va.v.H = height;
+    va.v.Wf = (float)width;
+    va.v.Hf = (float)height;
+    va.slot = slot;
+    cudaError_t e = cudaSuccess;
+    for (int n = 0; n < N && e == cudaSuccess; ++n) {
+        if (rgb_on_device) {
+            va.rgb[n] = rgb[n];
+        } else {
+            const Cam& c = rig->cams.c[n];
+            uint8_t* dst = slot_ptr<uint8_t>(rig->L, slot, rig->L.rgb_stage) + 3 * c.pix_off;
+            e = cudaMemcpyAsync(dst, rgb[n], (size_t)3 * c.W * c.H, cudaMemcpyHostToDevice, st);
+            va.rgb[n] = dst;
+        }
+    }
+    if (e == cudaSuccess)
+        e = launch_render_view(rig->cams, rig->grid, rig->L, va, reinterpret_cast<unsigned long long*>(key), out_rgb,
+                               out_cam, rig->sms, st);
+    if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_render_view");
+    return FVV_OK;
+}
+
 fvv_status fvv_set_timing(fvv_rig* rig, int enable) {
     if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
     rig->timing = enable != 0;

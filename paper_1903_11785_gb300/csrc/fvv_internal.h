@@ -185,6 +185,17 @@ struct ColourBatch {
 
 cudaError_t launch_colour(const CamSet& cams, const Grid& g, const Layout& L, const ColourBatch& cb, int sms,
                           int total_slots, cudaStream_t st);
+
+// A novel view (step E) of one reconstructed slot: the virtual camera as a
+// Cam (P, C, W, H, Wf, Hf; the other fields unused) and the capture RGB.
+struct ViewArgs {
+    Cam v;
+    int slot;
+    const uint8_t* rgb[FVV_MAX_CAMS];
+};
+
+cudaError_t launch_render_view(const CamSet& cams, const Grid& g, const Layout& L, const ViewArgs& va,
+                              unsigned long long* key, uint8_t* out_rgb, int32_t* out_cam, int sms, cudaStream_t st);
 cudaError_t launch_debug_pixels(const CamSet& cams, int cam, long long n, const float* pts, int32_t* px,
                                 int32_t* py, cudaStream_t st);
 cudaError_t launch_debug_labels(const Grid& g, const Layout& L, int slot, int32_t* dst, cudaStream_t st);

@@ -30,11 +30,11 @@ __global__ void __launch_bounds__(256) k_clear_depth(const __grid_constant__ Lay
 // sign is the image-plane one for w > 0), the area is zero iff
 // (x_0 a_12 - y_0 b_12) + w_0 c_12 is, and the box test uses the exact signs
 // of p w_j - x_j from one FMA each.
-// The buffer keeps the minimum of the squared distance: sqrt is monotone, so
-// the square root of that minimum is the minimum distance itself, taken
-// where the depth is read.
-__device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const float* Y, const float* Z, uint32_t d2,
-                                           uint32_t* __restrict__ depth) {
+// `sink(pixel)` is called for each covered pixel (row-major index in c's
+// image).
+template <class Sink>
+__device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const float* Y, const float* Z,
+                                           Sink&& sink) {
     float xh[3], yh[3], wh[3];
     bool ok = true;
 #pragma unroll
@@ -71,7 +71,6 @@ __device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const f
     const int y0 = max(0, (int)ceilf(fsub(vmin, kSlack)));
     const int x1 = umax > c.Wf ? c.W - 1 : min(c.W - 1, (int)floorf(fsub(fadd(umax, 1.0f / 64.0f), 0.5f)));
     const int y1 = vmax > c.Hf ? c.H - 1 : min(c.H - 1, (int)floorf(fsub(fadd(vmax, 1.0f / 64.0f), 0.5f)));
-    uint32_t* D = depth + c.pix_off;
     for (int yy = y0; yy <= y1; ++yy) {
         const float pcy = fadd((float)yy, 0.5f);
         const float s0 = __fmaf_rn(pcy, wh[0], -yh[0]), s1 = __fmaf_rn(pcy, wh[1], -yh[1]),
@@ -86,10 +85,7 @@ __device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const f
             const float e1 = fadd(fsub(fmul(pcx, ea[1]), fmul(pcy, eb[1])), ec[1]);
             const float e2 = fadd(fsub(fmul(pcx, ea[2]), fmul(pcy, eb[2])), ec[2]);
             const bool in = (e0 >= 0.0f && e1 >= 0.0f && e2 >= 0.0f) || (e0 <= 0.0f && e1 <= 0.0f && e2 <= 0.0f);
-            if (in) {
-                uint32_t* p = D + (size_t)yy * (unsigned)c.W + xx;
-                if (__ldcg(p) > d2) atomicMin(p, d2);   // skip the atomic when already nearer
-            }
+            if (in) sink((size_t)yy * (unsigned)c.W + xx);
         }
     }
 }
@@ -122,7 +118,14 @@ __global__ void __launch_bounds__(256) k_zbuffer(const __grid_constant__ CamSet 
         const float dy = fsub(__ldg(tcen + 3 * (size_t)t + 1), c.C[1]);
         const float dz = fsub(__ldg(tcen + 3 * (size_t)t + 2), c.C[2]);
         const uint32_t d2 = __float_as_uint(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
-        raster_tri(c, X, Y, Z, d2, depth);
+        // the buffer keeps the minimum of the squared distance: sqrt is
+        // monotone, so the square root of that minimum is the minimum
+        // distance itself, taken where the depth is read
+        uint32_t* D = depth + c.pix_off;
+        raster_tri(c, X, Y, Z, [&](size_t pix) {
+            uint32_t* p = D + pix;
+            if (__ldcg(p) > d2) atomicMin(p, d2);   // skip the atomic when already nearer
+        });
     }
 }
 
@@ -131,17 +134,11 @@ __device__ __forceinline__ float depth_of(uint32_t bits) {
     return bits == kEmptyDepth ? __int_as_float(0x7f800000) : __fsqrt_rn(__uint_as_float(bits));
 }
 
-// Sec. II-D-2 and II-E: cameras ranked by squared distance of their centre to
-// the viewpoint (ties to the lower index); a vertex takes the first camera in
-// rank order that has it in front, inside the image and with
-// |v - C| - depth <= t_v, and that camera's RGB at the vertex's pixel.
-__global__ void __launch_bounds__(256) k_colour(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
-                                                const __grid_constant__ Layout L,
-                                                const __grid_constant__ ColourBatch cb) {
-    __shared__ int rank_cam[FVV_MAX_CAMS];
-    const int slot = cb.slot[blockIdx.y];
+// Sec. II-D-2 and II-E: the capture cameras ranked by squared distance of
+// their centre to the viewpoint vp, ties to the lower index (thread m <
+// cams.n places camera m; the caller synchronises).
+__device__ __forceinline__ void rank_cameras(const CamSet& cams, const float* vp, int* rank_cam) {
     if (threadIdx.x < (unsigned)cams.n) {
-        const float* vp = cb.view[blockIdx.y];
         float d2[FVV_MAX_CAMS];
         const int me = threadIdx.x;
         int r = 0;
@@ -153,6 +150,42 @@ __global__ void __launch_bounds__(256) k_colour(const __grid_constant__ CamSet c
         for (int m = 0; m < cams.n; ++m) r += (d2[m] < d2[me]) || (d2[m] == d2[me] && m < me);
         rank_cam[r] = me;
     }
+}
+
+// The colour of world point (X,Y,Z): the first camera in rank order that has
+// it in front, inside the image and with |X - C| - depth <= t_v, and that
+// camera's RGB at the point's pixel.  Returns the camera, or -1 with (0,0,0).
+__device__ __forceinline__ int colour_point(const CamSet& cams, const int* rank_cam,
+                                            const uint32_t* __restrict__ depth, const uint8_t* const* rgb, float t_v,
+                                            float X, float Y, float Z, uint8_t* col) {
+    col[0] = col[1] = col[2] = 0;
+    for (int k = 0; k < cams.n; ++k) {
+        const int n = rank_cam[k];
+        const Cam& c = cams.c[n];
+        int px, py;
+        cam_pixel(c, X, Y, Z, px, py);
+        if (px < 0) continue;
+        const size_t pix = (size_t)py * (unsigned)c.W + (size_t)px;
+        const float dx = fsub(X, c.C[0]), dy = fsub(Y, c.C[1]), dz = fsub(Z, c.C[2]);
+        const float dist = __fsqrt_rn(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
+        const float dep = depth_of(__ldg(depth + c.pix_off + pix));
+        if (!(fsub(dist, dep) <= t_v)) continue;
+        const uint8_t* src = rgb[n] + 3 * pix;
+        col[0] = __ldg(src);
+        col[1] = __ldg(src + 1);
+        col[2] = __ldg(src + 2);
+        return n;
+    }
+    return -1;
+}
+
+// Per vertex: colour_point with the cameras ranked for the slot's viewpoint.
+__global__ void __launch_bounds__(256) k_colour(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
+                                                const __grid_constant__ Layout L,
+                                                const __grid_constant__ ColourBatch cb) {
+    __shared__ int rank_cam[FVV_MAX_CAMS];
+    const int slot = cb.slot[blockIdx.y];
+    rank_cameras(cams, cb.view[blockIdx.y], rank_cam);
     __syncthreads();
     const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
     const uint32_t nv = info->n_words ? info->n_verts : 0u;
@@ -162,32 +195,85 @@ __global__ void __launch_bounds__(256) k_colour(const __grid_constant__ CamSet c
     uint8_t* out = slot_ptr<uint8_t>(L, slot, L.vrgb);
     int* ocam = slot_ptr<int>(L, slot, L.vcam);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
-        const float X = verts[3 * (size_t)i], Y = verts[3 * (size_t)i + 1], Z = verts[3 * (size_t)i + 2];
-        int chosen = -1;
-        uint8_t col[3] = {0, 0, 0};
-        for (int k = 0; k < cams.n; ++k) {
-            const int n = rank_cam[k];
-            const Cam& c = cams.c[n];
-            int px, py;
-            cam_pixel(c, X, Y, Z, px, py);
-            if (px < 0) continue;
-            const size_t pix = (size_t)py * (unsigned)c.W + (size_t)px;
-            const float dx = fsub(X, c.C[0]), dy = fsub(Y, c.C[1]), dz = fsub(Z, c.C[2]);
-            const float dist = __fsqrt_rn(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
-            const uint32_t db = __ldg(depth + c.pix_off + pix);
-            const float dep = depth_of(db);
-            if (!(fsub(dist, dep) <= g.t_v)) continue;
-            const uint8_t* src = rgb[n] + 3 * pix;
-            col[0] = __ldg(src);
-            col[1] = __ldg(src + 1);
-            col[2] = __ldg(src + 2);
-            chosen = n;
-            break;
-        }
+        uint8_t col[3];
+        const int chosen = colour_point(cams, rank_cam, depth, rgb, g.t_v, verts[3 * (size_t)i],
+                                        verts[3 * (size_t)i + 1], verts[3 * (size_t)i + 2], col);
         out[3 * (size_t)i] = col[0];
         out[3 * (size_t)i + 1] = col[1];
         out[3 * (size_t)i + 2] = col[2];
         ocam[i] = chosen;
+    }
+}
+
+// ---- Sec. II-E, step E: a novel view of the coloured mesh
+
+__global__ void __launch_bounds__(256) k_view_clear(unsigned long long* __restrict__ key, size_t npix) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (size_t)gridDim.x * blockDim.x)
+        key[i] = ~0ull;
+}
+
+// Visibility in the virtual view: every covered pixel keeps the minimum of
+// (squared distance from the triangle's centroid to the view centre, as float
+// bits) << 32 | triangle index -- the nearest triangle, ties to the lower
+// index.  One thread per triangle.
+__global__ void __launch_bounds__(256) k_view_raster(const __grid_constant__ Layout L,
+                                                     const __grid_constant__ ViewArgs va,
+                                                     unsigned long long* __restrict__ key) {
+    const Cam& v = va.v;
+    const SlotInfo* info = slot_ptr<SlotInfo>(L, va.slot, L.info);
+    const uint32_t nt = info->n_words ? info->n_tris : 0u;
+    const float* verts = slot_ptr<float>(L, va.slot, L.verts);
+    const uint32_t* tris = slot_ptr<uint32_t>(L, va.slot, L.tris);
+    const float* tcen = slot_ptr<float>(L, va.slot, L.tcen);
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        float X[3], Y[3], Z[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const uint32_t vi = __ldg(tris + 3 * (size_t)t + j);
+            X[j] = __ldg(verts + 3 * (size_t)vi);
+            Y[j] = __ldg(verts + 3 * (size_t)vi + 1);
+            Z[j] = __ldg(verts + 3 * (size_t)vi + 2);
+        }
+        const float dx = fsub(__ldg(tcen + 3 * (size_t)t), v.C[0]);
+        const float dy = fsub(__ldg(tcen + 3 * (size_t)t + 1), v.C[1]);
+        const float dz = fsub(__ldg(tcen + 3 * (size_t)t + 2), v.C[2]);
+        const unsigned long long k =
+            (unsigned long long)__float_as_uint(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz))) << 32 | t;
+        raster_tri(v, X, Y, Z, [&](size_t pix) {
+            unsigned long long* p = key + pix;
+            if (__ldcg(p) > k) atomicMin(p, k);
+        });
+    }
+}
+
+// Colour of every pixel of the view: colour_point of its triangle's
+// centroid, with the capture cameras ranked for the view centre, so the
+// camera is chosen per pixel (Sec. II-E: the nearest camera where it sees
+// the surface, its neighbours where it is occluded).
+__global__ void __launch_bounds__(256) k_view_shade(const __grid_constant__ CamSet cams,
+                                                    const __grid_constant__ Grid g, const __grid_constant__ Layout L,
+                                                    const __grid_constant__ ViewArgs va,
+                                                    const unsigned long long* __restrict__ key,
+                                                    uint8_t* __restrict__ out_rgb, int32_t* __restrict__ out_cam) {
+    __shared__ int rank_cam[FVV_MAX_CAMS];
+    rank_cameras(cams, va.v.C, rank_cam);
+    __syncthreads();
+    const uint32_t* depth = slot_ptr<uint32_t>(L, va.slot, L.depth);
+    const float* tcen = slot_ptr<float>(L, va.slot, L.tcen);
+    const size_t npix = (size_t)va.v.W * (unsigned)va.v.H;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = key[i];
+        uint8_t col[3] = {0, 0, 0};
+        int chosen = -1;
+        if (k != ~0ull) {
+            const size_t t = (size_t)(uint32_t)k;
+            chosen = colour_point(cams, rank_cam, depth, va.rgb, g.t_v, __ldg(tcen + 3 * t), __ldg(tcen + 3 * t + 1),
+                                  __ldg(tcen + 3 * t + 2), col);
+        }
+        out_rgb[3 * i] = col[0];
+        out_rgb[3 * i + 1] = col[1];
+        out_rgb[3 * i + 2] = col[2];
+        if (out_cam) out_cam[i] = chosen;
     }
 }
 
@@ -215,6 +301,17 @@ cudaError_t launch_colour(const CamSet& cams, const Grid& g, const Layout& L, co
                           int total_slots, cudaStream_t st) {
     const int gv = grid_x(sms, total_slots, g.max_verts, 256);
     k_colour<<<dim3(gv, cb.n), 256, 0, st>>>(cams, g, L, cb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_view(const CamSet& cams, const Grid& g, const Layout& L, const ViewArgs& va,
+                              unsigned long long* key, uint8_t* out_rgb, int32_t* out_cam, int sms, cudaStream_t st) {
+    const size_t npix = (size_t)va.v.W * (unsigned)va.v.H;
+    const unsigned gp = (unsigned)std::max<size_t>(1, std::min<size_t>((npix + 255) / 256, (size_t)sms * 8));
+    k_view_clear<<<gp, 256, 0, st>>>(key, npix);
+    const unsigned gt = (unsigned)std::max<long long>(1, std::min<long long>((g.max_tris + 255) / 256, (long long)sms * 8));
+    k_view_raster<<<gt, 256, 0, st>>>(L, va, key);
+    k_view_shade<<<gp, 256, 0, st>>>(cams, g, L, va, key, out_rgb, out_cam);
     return cudaGetLastError();
 }
 

@@ -94,6 +94,8 @@ _sigs = {
     "fvv_set_tuning": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "fvv_set_graphs": ([_vp, C.c_int], C.c_int),
     "fvv_get_timing": ([_vp, C.POINTER(C.c_float), C.POINTER(C.c_int)], C.c_int),
+    "fvv_render_view": ([_vp, C.c_int, C.POINTER(_vp), C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int,
+                         C.c_int, _vp, _vp, _vp, _vp], C.c_int),
     "fvv_probe_l2": ([C.c_int, _vp, C.c_size_t, C.c_int, _vp, C.c_int, C.c_int, _vp], C.c_int),
     "fvv_last_error": ([_vp], C.c_char_p),
     "fvv_status_string": ([C.c_int], C.c_char_p),
@@ -227,6 +229,30 @@ def fvv_colour(rig_ptr, slots, rgb, viewpoints, stream=None):
                            vp.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream)), rig_ptr)
 
 
+def fvv_render_view(rig_ptr, slot, rgb, P, centre, width, height, stream=None, with_cam=True):
+    """Step E: a novel view of a reconstructed slot from a virtual camera.
+    rgb: per-camera (H,W,3) uint8 tensors (or an (N,H,W,3) tensor), all on
+    the device or all in host memory.  Returns device tensors (key (H,W)
+    int64 = squared-distance bits << 32 | triangle, -1 where empty; rgb
+    (H,W,3) uint8; capture camera (H,W) int32 or None)."""
+    imgs = list(rgb) if not torch.is_tensor(rgb) else list(rgb.unbind(0))
+    on_dev = None
+    for t in imgs:
+        assert t.dtype == torch.uint8 and t.is_contiguous()
+        on_dev = int(t.is_cuda) if on_dev is None else on_dev
+        assert int(t.is_cuda) == on_dev
+    Pm = np.ascontiguousarray(np.asarray(P, np.float32).reshape(12))
+    Cm = np.ascontiguousarray(np.asarray(centre, np.float32).reshape(3))
+    key = torch.empty((height, width), dtype=torch.int64, device="cuda")
+    out = torch.empty((height, width, 3), dtype=torch.uint8, device="cuda")
+    cam = torch.empty((height, width), dtype=torch.int32, device="cuda") if with_cam else None
+    _check(_lib.fvv_render_view(rig_ptr, slot, _ptr_array([t.data_ptr() for t in imgs]), on_dev,
+                                Pm.ctypes.data_as(C.POINTER(C.c_float)), Cm.ctypes.data_as(C.POINTER(C.c_float)),
+                                width, height, _vp(key.data_ptr()), _vp(out.data_ptr()),
+                                _vp(cam.data_ptr()) if cam is not None else None, _stream(stream)), rig_ptr)
+    return key, out, cam
+
+
 def fvv_get_counts(rig_ptr, slot, stream=None, allow_capacity=False) -> dict:
     c = Counts()
     st = _lib.fvv_get_counts(rig_ptr, slot, C.byref(c), _stream(stream))
@@ -322,6 +348,9 @@ class Rig:
 
     def colour(self, slots, rgb, viewpoints, stream=None):
         fvv_colour(self.ptr, list(slots), rgb, viewpoints, stream)
+
+    def render_view(self, slot, rgb, P, centre, width, height, stream=None, with_cam=True):
+        return fvv_render_view(self.ptr, slot, rgb, P, centre, width, height, stream, with_cam)
 
     def counts(self, slot, stream=None, allow_capacity=False):
         return fvv_get_counts(self.ptr, slot, stream, allow_capacity)
