@@ -60,6 +60,57 @@ fvv_status cuda_fail(fvv_rig* rig, cudaError_t e, const char* what) {
 
 long long um_of(float m) { return llround((double)m * 1e6); }
 
+// Per camera, the margins seg_du, seg_dv used by the bisection to decide,
+// once per grid edge, that a camera sees every point of the edge in its
+// silhouette.  Every point a bisection tests lies within 2^-19 |X| per
+// coordinate of the edge (at most 30 midpoints, each rounded by half an ulp)
+// and inside the box B = the grid grown by one coarse and two fine voxels
+// (ROI overshoot and padding samples).  For a row r of P, the computed
+// binary32 value ((p0 X + p1 Y) + p2 Z) + p3 differs from the exact value at
+// the nearest edge point by at most 2^-18 S_r, with S_r = sum |p_rj| max_B
+// |X_j| + |p_r3| (four roundings of at most 2^-24 relative to S_r, plus the
+// point's deviation).  With w' >= w_min - 2^-18 S_w > 0 on B and |u| <= W + 1
+// inside the image, the computed u = x'/w' of a tested point lies within
+// 2^-18 (S_x + (W + 1) S_w) / (w_min - 2^-18 S_w) of the exact projection of
+// an edge point, which lies between the exact projections of the ends (a
+// projective map keeps segments straight).  The ends' approximate positions
+// carry the same error plus that of rcp.approx and one multiply (below
+// (W + 2) 2^-21), so the margin is twice the first term plus that, plus 2^-12.
+void segment_margins(CamSet& cs, const Grid& g) {
+    double lo[3], hi[3];
+    const int dims[3] = {g.nx, g.ny, g.nz};
+    for (int a = 0; a < 3; ++a) {
+        const double pad = (double)g.sc + 2.0 * (double)g.sf;
+        lo[a] = (double)g.o[a] - pad;
+        hi[a] = (double)g.o[a] + (double)dims[a] * (double)g.sc + pad;
+    }
+    const double e = std::ldexp(1.0, -18);
+    for (int n = 0; n < cs.n; ++n) {
+        Cam& c = cs.c[n];
+        double S[3], wmin = 1e300;
+        for (int r = 0; r < 3; ++r) {
+            S[r] = std::fabs((double)c.P[4 * r + 3]);
+            for (int j = 0; j < 3; ++j)
+                S[r] += std::fabs((double)c.P[4 * r + j]) * std::max(std::fabs(lo[j]), std::fabs(hi[j]));
+        }
+        for (int k = 0; k < 8; ++k) {
+            const double X = (k & 1) ? hi[0] : lo[0], Y = (k & 2) ? hi[1] : lo[1], Z = (k & 4) ? hi[2] : lo[2];
+            wmin = std::min(wmin, (double)c.P[8] * X + (double)c.P[9] * Y + (double)c.P[10] * Z + (double)c.P[11]);
+        }
+        const double den = wmin - e * S[2];
+        if (!(den > 0.0)) {
+            c.seg_du = c.seg_dv = -1.0f;
+            continue;
+        }
+        const double du = 2.0 * e * (S[0] + (c.W + 1.0) * S[2]) / den + (c.W + 2.0) * std::ldexp(1.0, -21) +
+                          std::ldexp(1.0, -12);
+        const double dv = 2.0 * e * (S[1] + (c.H + 1.0) * S[2]) / den + (c.H + 2.0) * std::ldexp(1.0, -21) +
+                          std::ldexp(1.0, -12);
+        c.seg_du = (float)(du * (1.0 + 1e-6));
+        c.seg_dv = (float)(dv * (1.0 + 1e-6));
+    }
+}
+
 struct Plan {
     CamSet cams;
     Grid grid;
@@ -129,6 +180,7 @@ fvv_status make_plan(const fvv_rig_desc* d, const fvv_recon_params* p, Plan& pl,
     g.sc = p->coarse_m;
     g.sf = p->fine_m;
     if (p->bisect_steps < 0 || p->bisect_steps > 30) { err = "bisect_steps must be 0..30"; return FVV_ERR_INVALID_ARG; }
+    segment_margins(cs, g);
     g.steps = p->bisect_steps;
     if (p->surface_rule != FVV_SURFACE_BISECT && p->surface_rule != FVV_SURFACE_LAMBDA) {
         err = "bad surface_rule";

@@ -29,6 +29,11 @@ struct Cam {
     float Wf, Hf;        // W and H as floats
     uint32_t bit_off;    // first silhouette word of this camera in a slot
     uint64_t pix_off;    // first pixel of this camera in per-slot pixel arrays
+    // Bound (pixels) on how far the computed image position of any point the
+    // bisection of a grid edge can test lies from the box of the edge ends'
+    // approximate image positions; negative: no bound (the camera can see
+    // part of the volume at w' <= 0).  See segment_margins in fvv_api.cu.
+    float seg_du, seg_dv;
 };
 
 struct CamSet {

@@ -305,13 +305,80 @@ __global__ void __launch_bounds__(kChunk) k_mc_vertices(const __grid_constant__ 
     }
 }
 
+// Does camera c see every point the bisection of the edge (a, b) can test in
+// its silhouette?  True when the pixels of the box spanned by the ends'
+// approximate image positions, widened by the camera's margins (see
+// segment_margins on the host), are all inside the image and set.  Boxes
+// wider than 32 or taller than 8 pixels are not scanned (false).
+__device__ __forceinline__ bool segment_all_fg(const Cam& c, const uint32_t* __restrict__ sil, const float* a,
+                                               const float* b) {
+    if (!(c.seg_du >= 0.0f)) return false;
+    float xa, ya, wa, xb, yb, wb;
+    project(c.P, a[0], a[1], a[2], xa, ya, wa);
+    project(c.P, b[0], b[1], b[2], xb, yb, wb);
+    if (!(wa > 0.0f && wb > 0.0f)) return false;
+    const float ra = rcp_approx(wa), rb = rcp_approx(wb);
+    const float ua = fmul(xa, ra), va = fmul(ya, ra), ub = fmul(xb, rb), vb = fmul(yb, rb);
+    const float u0 = fsub(fminf(ua, ub), c.seg_du), u1 = fadd(fmaxf(ua, ub), c.seg_du);
+    const float v0 = fsub(fminf(va, vb), c.seg_dv), v1 = fadd(fmaxf(va, vb), c.seg_dv);
+    if (!(u0 >= 0.0f && v0 >= 0.0f && u1 < c.Wf && v1 < c.Hf)) return false;
+    const int x0 = (int)u0, x1 = (int)u1, y0 = (int)v0, y1 = (int)v1;   // truncation = floor here
+    if (x1 - x0 > 31 || y1 - y0 > 7) return false;
+    const int w0 = x0 >> 5, w1 = x1 >> 5;
+    const uint32_t m0 = ~0u << (x0 & 31), m1 = ~0u >> (31 - (x1 & 31));
+    const uint32_t* row = sil + c.bit_off + (unsigned)y0 * (unsigned)c.Wq;
+    bool all = true;
+    for (int y = y0; y <= y1; ++y, row += c.Wq) {
+        if (w0 == w1) {
+            all &= (__ldg(row + w0) & (m0 & m1)) == (m0 & m1);
+        } else {
+            all &= (__ldg(row + w0) & m0) == m0;
+            all &= (__ldg(row + w1) & m1) == m1;
+        }
+    }
+    return all;
+}
+
+// A camera's fields for the bisection's per-lane tests, in shared memory
+// (lanes test different cameras).
+struct __align__(16) SegCam {
+    float P[12];
+    float Wf, Hf;
+    int W, H, Wq;
+    uint32_t bit_off;
+    float pad_[2];
+};
+
 // Sec. II-C, exact intersection: between the ON end a and the OFF end b of a
 // bipolar edge, `steps` times m = (a+b)/2, a = m if m is occupied else b = m;
-// the vertex is the final midpoint.
+// the vertex is the final midpoint.  One vertex per thread.
+//
+// Every point tested lies on the edge (up to rounding), so a camera that sees
+// the whole edge inside its silhouette (segment_all_fg) votes foreground for
+// all of them: it is decided once per edge, and only the other cameras are
+// tested at each midpoint, from a per-lane list.  A midpoint's first
+// background camera in index order is then the first listed camera that votes
+// background, so the occupancy and the test count (that camera's index + 1,
+// or N when the midpoint is occupied) are those of the plain early-exit loop
+// over all cameras.
 template <int NC>
 __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
                                                 const __grid_constant__ Layout L, const __grid_constant__ SlotList sl) {
     __shared__ unsigned long long sh_t[32];
+    __shared__ SegCam sc[FVV_MAX_CAMS];
+    const int ncam = NC > 0 ? NC : cams.n;
+    for (int n = threadIdx.x; n < ncam; n += blockDim.x) {
+        const Cam& c = cams.c[n];
+        for (int k = 0; k < 12; ++k) sc[n].P[k] = c.P[k];
+        sc[n].Wf = c.Wf;
+        sc[n].Hf = c.Hf;
+        sc[n].W = c.W;
+        sc[n].H = c.H;
+        sc[n].Wq = c.Wq;
+        sc[n].bit_off = c.bit_off;
+    }
+    __syncthreads();
+    const bool abstain = cams.oob == FVV_OOB_ABSTAIN;
     const int slot = sl.s[blockIdx.y];
     const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
     const uint32_t nv = info->n_words ? info->n_verts : 0u;
@@ -319,14 +386,9 @@ __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet c
     const uint32_t* __restrict__ sil = slot_ptr<uint32_t>(L, slot, L.sil);
     const uint64_t* vrec = slot_ptr<uint64_t>(L, slot, L.vrec);
     float* verts = slot_ptr<float>(L, slot, L.verts);
-    uint32_t tests = 0;
-    // Warps walk the vertices together (the loop bounds are warp-uniform) so
-    // that the camera loop can stop when a ballot shows no lane still needs it.
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nv; base += stride) {
-        const uint32_t i = base + (threadIdx.x & 31u);
-        const bool act = i < nv;
-        const uint64_t rec = act ? vrec[i] : 0ull;
+    unsigned long long tests = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
+        const uint64_t rec = vrec[i];
         const int k = (int)(rec & 0x3FFFu), axis = (int)(rec >> 14 & 3u), s0 = (int)(rec >> 16 & 1u);
         const int q[3] = {(int)(rec >> 17 & 0x7FFFu), (int)(rec >> 32 & 0x7FFFu), (int)(rec >> 47 & 0x7FFFu)};
         const DRoi& r = rois[k];
@@ -338,21 +400,59 @@ __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet c
             a[d] = s0 ? c0 : c1;
             b[d] = s0 ? c1 : c0;
         }
+        // cameras that must be tested at each midpoint (bit n: camera n)
+        uint64_t undecided = 0;
+        bool seen_fg = false;          // ABSTAIN: some camera votes foreground everywhere
+        if (g.steps > 0) {
+            if constexpr (NC > 0) {
+#pragma unroll
+                for (int n = 0; n < NC; ++n) {
+                    const bool fg = segment_all_fg(cams.c[n], sil, a, b);
+                    undecided |= fg ? 0ull : 1ull << n;
+                    seen_fg |= fg;
+                }
+            } else {
+                for (int n = 0; n < cams.n; ++n) {
+                    const bool fg = segment_all_fg(cams.c[n], sil, a, b);
+                    undecided |= fg ? 0ull : 1ull << n;
+                    seen_fg |= fg;
+                }
+            }
+        }
         for (int it = 0; it < g.steps; ++it) {
             float m[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) m[d] = fmul(fadd(a[d], b[d]), 0.5f);
-            const bool on = warp_test<NC>(cams, sil, m[0], m[1], m[2], act, tests);
+            int stop = -1;
+            bool voted = !abstain || seen_fg;
+            for (uint64_t u = undecided; u; u &= u - 1) {
+                const int n = __ffsll((long long)u) - 1;
+                const SegCam& c = sc[n];
+                float xp, yp, wp;
+                project(c.P, m[0], m[1], m[2], xp, yp, wp);
+                const float rw = rcp_approx(wp);
+                const int px = pixel_floor(xp, wp, rw, c.Wf);
+                const int py = pixel_floor(yp, wp, rw, c.Hf);
+                const bool in = wp > 0.0f && (unsigned)px < (unsigned)c.W && (unsigned)py < (unsigned)c.H;
+                const uint32_t word =
+                    in ? __ldg(sil + c.bit_off + (unsigned)py * (unsigned)c.Wq + ((unsigned)px >> 5)) : 0u;
+                const bool bit = (word >> (px & 31)) & 1u;
+                if (abstain ? (in && !bit) : !bit) {
+                    stop = n;
+                    break;
+                }
+                voted |= bit;
+            }
+            tests += stop < 0 ? (unsigned)ncam : (unsigned)(stop + 1);
+            const bool on = stop < 0 && voted;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 a[d] = on ? m[d] : a[d];
                 b[d] = on ? b[d] : m[d];
             }
         }
-        if (act) {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) verts[3 * (size_t)i + d] = fmul(fadd(a[d], b[d]), 0.5f);
-        }
+        for (int d = 0; d < 3; ++d) verts[3 * (size_t)i + d] = fmul(fadd(a[d], b[d]), 0.5f);
     }
     const unsigned long long t = block_sum<unsigned long long>(tests, sh_t);
     if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_bisect, t);

@@ -111,6 +111,20 @@ def test_paper_surface_rule_abstain_ragged():
     compare(rig, fr, g)
 
 
+def test_abstain_policy_with_bisection():
+    """ABSTAIN with bisection on 630 px images: cameras that do not see a
+    midpoint do not vote, and cameras decided once per edge are skipped."""
+    n, r, h = 6, 6.0, 3.0
+    cs = [(r * math.cos(2 * math.pi * k / n), r * math.sin(2 * math.pi * k / n), h) for k in range(n)]
+    rig = _make_rig("ragged", cs, [(0, 0, 0.9)] * n, 480.0, 630, 349, _gen("ragged/rig"),
+                    (-2.0, -2.0, 0.0), (2.0, 2.0, 2.5), 0.05, 0.01, 9)
+    rig.oob_policy = ABSTAIN
+    fr = render(rig, scene_objects("tiny", 6), index=6, config_tag="ragged")
+    g = run_gpu(rig, [fr])[0]
+    ref = compare(rig, fr, g)
+    assert ref.tests_bisect > 0
+
+
 def test_ragged_image_width():
     """Images whose width is not a multiple of 32 (scalar packing path, partial
     last word of every silhouette row)."""
