@@ -52,7 +52,8 @@ __device__ __forceinline__ int pixel_floor(float x, float w, float r, float n) {
 // (floor(x'/w'), floor(y'/w')) of the exact quotients of the binary32
 // homogeneous coordinates.  `in` says whether the point is in front of the
 // camera and inside its image; the bit is 0 when it is not.
-__device__ __forceinline__ uint32_t cam_bit(const Cam& c, const uint32_t* __restrict__ sil, float X, float Y,
+template <class CamT>
+__device__ __forceinline__ uint32_t cam_bit(const CamT& c, const uint32_t* __restrict__ sil, float X, float Y,
                                             float Z, bool& in) {
     float xp, yp, wp;
     project(c.P, X, Y, Z, xp, yp, wp);
@@ -141,6 +142,33 @@ __device__ __forceinline__ bool warp_test(const CamSet& cams, const uint32_t* __
         case 16: F(16); break;  \
         default: F(0); break;   \
     }
+
+// A camera's fields for tests where lanes use different cameras, kept in
+// shared memory (80 bytes: consecutive cameras fall in different banks).
+struct __align__(16) SmemCam {
+    float P[12];
+    float Wf, Hf;
+    int W, H, Wq;
+    uint32_t bit_off;
+    float du, dv;            // Cam::seg_du, seg_dv
+};
+
+// Copy the first n cameras into sc (all threads of the block; the caller
+// synchronises).
+__device__ __forceinline__ void load_smem_cams(const CamSet& cams, int n, SmemCam* sc) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const Cam& c = cams.c[i];
+        for (int k = 0; k < 12; ++k) sc[i].P[k] = c.P[k];
+        sc[i].Wf = c.Wf;
+        sc[i].Hf = c.Hf;
+        sc[i].W = c.W;
+        sc[i].H = c.H;
+        sc[i].Wq = c.Wq;
+        sc[i].bit_off = c.bit_off;
+        sc[i].du = c.seg_du;
+        sc[i].dv = c.seg_dv;
+    }
+}
 
 // The ROI holding fine word w: the last ROI whose first word is <= w.
 __device__ __forceinline__ int roi_of_word(const DRoi* rois, int n, uint32_t w) {

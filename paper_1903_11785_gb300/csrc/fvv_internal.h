@@ -56,6 +56,9 @@ struct Grid {
     uint32_t max_verts, max_tris;
 };
 
+// Fine-carve tiles: kTileX x kTileY x kTileZ interior samples, one per lane.
+constexpr int kTileX = 4, kTileY = 2, kTileZ = 4;
+
 // Per-slot device bookkeeping (zeroed at the start of each reconstruction).
 struct SlotInfo {
     unsigned int flags;
@@ -63,7 +66,7 @@ struct SlotInfo {
     int n_rois;
     uint32_t n_words;           // fine words in use
     uint32_t n_chunks;
-    uint32_t n_samples;         // interior fine samples of all ROIs
+    uint32_t n_tiles;           // fine-carve tiles of all ROIs
     uint32_t pad_;
     uint32_t n_verts, n_tris;
     uint32_t n_on;
@@ -78,7 +81,7 @@ struct DRoi {
     int nxw;                    // words per padded fine row
     uint32_t word_off;          // first fine word of this ROI in the slot
     uint32_t n_words;
-    uint32_t samp_off;          // first interior fine sample of this ROI in the slot
+    uint32_t tile_off;          // first fine-carve tile of this ROI in the slot
     uint32_t vert_off, tri_off; // filled after the scans (for fvv_roi)
 };
 

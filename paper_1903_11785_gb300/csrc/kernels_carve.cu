@@ -102,66 +102,95 @@ __global__ void __launch_bounds__(256) k_clear_fine(const __grid_constant__ Layo
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) fine[w] = 0u;
 }
 
-// The ROI holding interior fine sample s: the last ROI whose first sample <= s.
-__device__ __forceinline__ int roi_of_sample(const DRoi* rois, int n, uint32_t s) {
+// The ROI holding fine-carve tile t: the last ROI whose first tile is <= t.
+__device__ __forceinline__ int roi_of_tile(const DRoi* rois, int n, uint32_t t) {
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (rois[mid].samp_off <= s) lo = mid;
+        if (rois[mid].tile_off <= t) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
-// Levels of the fine carve: a sample at level j has passed cameras
-// [0, lvb(j)) and tests cameras [lvb(j), lvb(j + 1)) next: [0,2), [2,4),
-// [4,8), [8,N).
-constexpr int kLevels = 4;
-__host__ __device__ constexpr int lvb(int n, int j) {
-    return j == 0 ? 0 : (j < kLevels && (1 << j) < n ? (1 << j) : n);
+// Bits 0, 2, 4, ... of x packed into bits 0..15.
+__device__ __forceinline__ uint32_t even_bits(uint32_t x) {
+    x &= 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    return (x | (x >> 8)) & 0x0000FFFFu;
 }
 
-// Cameras [C0, C1) of the test (Sec. II-B-1) for the live lanes of a warp,
-// in index order, each lane stopping at its first background vote and the
-// warp at the first camera where no lane is left.
-template <bool ABSTAIN, int C0, int C1>
-__device__ __forceinline__ void test_span(const CamSet& cams, const uint32_t* __restrict__ sil, float X, float Y,
-                                          float Z, bool& alive, bool& voted, uint32_t& tests) {
-#pragma unroll
-    for (int n = C0; n < C1; ++n) {
-        if (!__any_sync(kFull, alive)) break;
-        if (alive) {
-            ++tests;
-            test_cam<ABSTAIN>(cams.c[n], sil, X, Y, Z, alive, voted);
-        }
-    }
-}
-
+// What every sample of a fine-carve tile sees in camera c (two lanes per
+// camera, `half` = 0 or 1, each projecting four of the tile's eight extreme
+// samples (cx[i], cy[j], cz[k])).  The box of their image positions, widened
+// by the camera's error margin (Cam::seg_du, seg_dv), holds the pixel of
+// every sample of the tile (two lanes per camera; the caller has all lanes
+// call it).  fg_all: the box is inside the image and every
+// pixel of it is set, so every sample votes foreground.  bg_all: no pixel of
+// the box inside the image is set and (under STRICT, where a point outside
+// the image votes background) the rest lies outside it, or (under ABSTAIN)
+// the box is inside the image: every sample votes background.
 template <bool ABSTAIN>
-__device__ __forceinline__ void test_span_rt(const CamSet& cams, const uint32_t* __restrict__ sil, int c0, int c1,
-                                             float X, float Y, float Z, bool& alive, bool& voted, uint32_t& tests) {
-    for (int n = c0; n < c1; ++n) {
-        if (!__any_sync(kFull, alive)) break;
-        if (alive) {
-            ++tests;
-            test_cam<ABSTAIN>(cams.c[n], sil, X, Y, Z, alive, voted);
+__device__ __forceinline__ void classify_tile_camera(const SmemCam& c, const uint32_t* __restrict__ sil,
+                                                     const float* cx, const float* cy, const float* cz, int half,
+                                                     bool& fg_all, bool& bg_all) {
+    // the two lanes of a camera take the same path through this function, so
+    // they exchange values among themselves only
+    const unsigned pm = 3u << ((threadIdx.x & 31u) & ~1u);
+    float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
+    bool wpos = true;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int kk = half * 4 + q;
+        float xh, yh, wh;
+        project(c.P, cx[kk & 1], cy[(kk >> 1) & 1], cz[kk >> 2], xh, yh, wh);
+        wpos &= wh > 0.0f;
+        const float r = rcp_approx(wh);
+        const float u = fmul(xh, r), v = fmul(yh, r);
+        umin = fminf(umin, u); umax = fmaxf(umax, u);
+        vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
+    }
+    umin = fminf(umin, __shfl_xor_sync(pm, umin, 1));
+    umax = fmaxf(umax, __shfl_xor_sync(pm, umax, 1));
+    vmin = fminf(vmin, __shfl_xor_sync(pm, vmin, 1));
+    vmax = fmaxf(vmax, __shfl_xor_sync(pm, vmax, 1));
+    const int wpos_other = __shfl_xor_sync(pm, (int)wpos, 1);   // both lanes, unconditionally
+    wpos = wpos && wpos_other != 0;
+    fg_all = bg_all = false;
+    if (!wpos || !(c.du >= 0.0f)) return;
+    const float u0 = fsub(umin, c.du), u1 = fadd(umax, c.du), v0 = fsub(vmin, c.dv), v1 = fadd(vmax, c.dv);
+    if (!(u0 > -1.0e6f && u1 < 1.0e6f && v0 > -1.0e6f && v1 < 1.0e6f)) return;   // also NaN
+    const int bx0 = (int)floorf(u0), bx1 = (int)floorf(u1), by0 = (int)floorf(v0), by1 = (int)floorf(v1);
+    const bool inside = bx0 >= 0 && by0 >= 0 && bx1 < c.W && by1 < c.H;
+    // the part of the box inside the image
+    const int x0 = max(bx0, 0), x1 = min(bx1, c.W - 1), y0 = max(by0, 0), y1 = min(by1, c.H - 1);
+    if (x0 > x1 || y0 > y1) {            // entirely outside the image
+        bg_all = !ABSTAIN;
+        return;
+    }
+    if (x1 - x0 > 31 || y1 - y0 > 15) return;   // too large to scan: undecided
+    const int w0 = x0 >> 5, w1 = x1 >> 5;
+    const uint32_t m0 = ~0u << (x0 & 31), m1 = ~0u >> (31 - (x1 & 31));
+    bool all = true, any = false;
+    for (int y = y0 + half; y <= y1; y += 2) {     // the two lanes take alternate rows
+        const uint32_t* row = sil + c.bit_off + (unsigned)y * (unsigned)c.Wq;
+        if (w0 == w1) {
+            const uint32_t m = m0 & m1, v = __ldg(row + w0) & m;
+            all &= v == m;
+            any |= v != 0u;
+        } else {
+            const uint32_t va = __ldg(row + w0) & m0, vb = __ldg(row + w1) & m1;
+            all &= va == m0 && vb == m1;
+            any |= (va | vb) != 0u;
         }
     }
-}
-
-template <int NC, bool ABSTAIN>
-__device__ __forceinline__ void test_level(const CamSet& cams, const uint32_t* __restrict__ sil, int lv, float X,
-                                           float Y, float Z, bool& alive, bool& voted, uint32_t& tests) {
-    if constexpr (NC > 0) {
-        switch (lv) {
-            case 0: test_span<ABSTAIN, lvb(NC, 0), lvb(NC, 1)>(cams, sil, X, Y, Z, alive, voted, tests); break;
-            case 1: test_span<ABSTAIN, lvb(NC, 1), lvb(NC, 2)>(cams, sil, X, Y, Z, alive, voted, tests); break;
-            case 2: test_span<ABSTAIN, lvb(NC, 2), lvb(NC, 3)>(cams, sil, X, Y, Z, alive, voted, tests); break;
-            default: test_span<ABSTAIN, lvb(NC, 3), NC>(cams, sil, X, Y, Z, alive, voted, tests); break;
-        }
-    } else {
-        test_span_rt<ABSTAIN>(cams, sil, lvb(cams.n, lv), lvb(cams.n, lv + 1), X, Y, Z, alive, voted, tests);
-    }
+    const int all_other = __shfl_xor_sync(pm, (int)all, 1), any_other = __shfl_xor_sync(pm, (int)any, 1);
+    all = all && all_other != 0;
+    any = any || any_other != 0;
+    fg_all = inside && all;
+    bg_all = !any && (inside || !ABSTAIN);
 }
 
 // Sec. II-B-3: the fine hull of every ROI, each treated as its own volume.
@@ -169,125 +198,139 @@ __device__ __forceinline__ void test_level(const CamSet& cams, const uint32_t* _
 // and fdim+1), rows of ceil((fdim_x+2)/32) words, cleared beforehand; only
 // occupied samples are written, by OR into their word.
 //
-// Most samples are rejected by the first camera or two while the points
-// inside the hull take every camera, so a warp that kept its 32 samples to
-// the end would idle most lanes.  Each warp therefore moves samples through
-// levels (cameras [0,2), [2,4), [4,8), [8,N)): a step takes 32 samples at
-// one level (fresh interior samples of all ROIs, in order, at level 0),
-// tests that level's cameras and queues the survivors in the warp's part of
-// shared memory for the next level; the deepest level holding 32 goes
-// first, so each queue stays under 64 entries.  The queue counts are the
-// same in every lane (they follow from ballots), so the warp needs no
-// shared counters and the block no barrier.  Each sample still tests the
-// cameras in index order and stops at its first background vote, so
-// occupancy and test counts are those of the plain per-sample loop.
+// A warp takes a tile of 4 x 2 x 4 interior samples (x, y, z; one per lane)
+// and first decides, per camera, whether all of the tile's samples vote
+// foreground or all vote background there (classify_tile_camera).  A
+// sample's first background camera in index order is then either an
+// undecided camera before the tile's first all-background camera, where it
+// is tested, or that camera; so each sample projects and looks its pixel up
+// only at those undecided cameras, and its test count (first background
+// camera + 1, or N when occupied) and occupancy are those of the plain
+// per-sample loop.
+template <int NC, bool ABSTAIN>
+__device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, const SmemCam* sc, int ncam,
+                                           uint32_t ntiles, int nrois, const DRoi* rois,
+                                           const uint32_t* __restrict__ sil, uint32_t* fine,
+                                           unsigned long long& tests) {
+    const int lane = threadIdx.x & 31, half = lane & 1;
+    const int xi = lane & 3, yi = (lane >> 2) & 1, zi = lane >> 3;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    // ROI of the current tile (the same in every lane)
+    uint32_t lo = 0, hi = 0, woff = 0;
+    int fx = 1, fy = 1, fz = 1, nxw = 1, ntx = 1, nty = 1;
+    float fo0 = 0.f, fo1 = 0.f, fo2 = 0.f;
+    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += nwarps) {
+        if (t >= hi || t < lo) {
+            const DRoi& r = rois[roi_of_tile(rois, nrois, t)];
+            lo = r.tile_off;
+            fx = r.fdim[0];
+            fy = r.fdim[1];
+            fz = r.fdim[2];
+            ntx = (fx + kTileX - 1) / kTileX;
+            nty = (fy + kTileY - 1) / kTileY;
+            hi = lo + (uint32_t)ntx * (uint32_t)nty * (uint32_t)((fz + kTileZ - 1) / kTileZ);
+            woff = r.word_off;
+            nxw = r.nxw;
+            fo0 = r.fo[0];
+            fo1 = r.fo[1];
+            fo2 = r.fo[2];
+        }
+        const uint32_t lt = t - lo;
+        const uint32_t r1 = lt / (uint32_t)ntx;
+        const int tx = (int)(lt - r1 * (uint32_t)ntx), ty = (int)(r1 % (uint32_t)nty), tz = (int)(r1 / (uint32_t)nty);
+        const int x0 = tx * kTileX, y0 = ty * kTileY, z0 = tz * kTileZ;
+        // the tile's extreme samples
+        const int xs[2] = {x0, min(x0 + kTileX - 1, fx - 1)};
+        const int ys[2] = {y0, min(y0 + kTileY - 1, fy - 1)};
+        const int zs[2] = {z0, min(z0 + kTileZ - 1, fz - 1)};
+        float cx[2], cy[2], cz[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            cx[e] = fadd(fo0, fmul(fadd((float)xs[e], 0.5f), g.sf));
+            cy[e] = fadd(fo1, fmul(fadd((float)ys[e], 0.5f), g.sf));
+            cz[e] = fadd(fo2, fmul(fadd((float)zs[e], 0.5f), g.sf));
+        }
+        // bit n: every sample votes foreground (fgm) / background (bgm) in camera n
+        uint64_t fgm = 0, bgm = 0;
+        for (int cg = 0; cg < ncam; cg += 16) {
+            const int cam = cg + (lane >> 1);
+            bool fg, bg;
+            classify_tile_camera<ABSTAIN>(sc[min(cam, ncam - 1)], sil, cx, cy, cz, half, fg, bg);
+            fg = fg && cam < ncam;
+            bg = bg && cam < ncam;
+            fgm |= (uint64_t)even_bits(__ballot_sync(kFull, fg)) << cg;
+            bgm |= (uint64_t)even_bits(__ballot_sync(kFull, bg)) << cg;
+        }
+        // this lane's sample
+        const int x = x0 + xi, y = y0 + yi, z = z0 + zi;
+        const bool act = x < fx && y < fy && z < fz;
+        const float X = fadd(fo0, fmul(fadd((float)x, 0.5f), g.sf));
+        const float Y = fadd(fo1, fmul(fadd((float)y, 0.5f), g.sf));
+        const float Z = fadd(fo2, fmul(fadd((float)z, 0.5f), g.sf));
+        // In camera order: the first all-background camera nb stops every
+        // sample still alive there; before it, all-foreground cameras pass
+        // every sample and only the undecided ones are tested, per lane.
+        const int nb = bgm ? __ffsll((long long)bgm) - 1 : ncam;
+        const uint64_t before = nb >= 64 ? ~0ull : (1ull << nb) - 1ull;
+        uint64_t todo = ~(fgm | bgm) & before;
+        bool alive = act, voted = !ABSTAIN || (fgm & before) != 0ull;
+        int stop = -1;
+        while (todo && __any_sync(kFull, alive)) {
+            const int n = __ffsll((long long)todo) - 1;
+            todo &= todo - 1ull;
+            if (alive) {
+                bool in;
+                const uint32_t bit = cam_bit(sc[n], sil, X, Y, Z, in);
+                if (ABSTAIN ? (in && !bit) : !bit) {
+                    alive = false;
+                    stop = n;
+                }
+                voted |= bit != 0u;
+            }
+        }
+        if (act) tests += stop >= 0 ? (unsigned)(stop + 1) : (nb < ncam ? (unsigned)(nb + 1) : (unsigned)ncam);
+        alive = alive && nb >= ncam;
+        const bool on = alive && voted;
+        // OR the occupied samples into their words: the four lanes of one
+        // (y, z) row span at most two words
+        if (__any_sync(kFull, on)) {
+            const uint32_t word = woff + ((uint32_t)(z + 1) * (uint32_t)(fy + 2) + (uint32_t)(y + 1)) * (uint32_t)nxw +
+                                  (uint32_t)((x + 1) >> 5);
+            const uint32_t first = __shfl_sync(kFull, word, lane & ~3);
+            const uint32_t bit = on ? 1u << ((x + 1) & 31) : 0u;
+            uint32_t blo = word == first ? bit : 0u, bhi = word == first ? 0u : bit;
+            blo |= __shfl_xor_sync(kFull, blo, 1);
+            bhi |= __shfl_xor_sync(kFull, bhi, 1);
+            blo |= __shfl_xor_sync(kFull, blo, 2);
+            bhi |= __shfl_xor_sync(kFull, bhi, 2);
+            if (xi == 0) {
+                if (blo) atomicOr(fine + first, blo);
+                if (bhi) atomicOr(fine + first + 1, bhi);
+            }
+        }
+    }
+}
+
 template <int NC>
 __global__ void __launch_bounds__(256) k_fine_carve(const __grid_constant__ CamSet cams,
                                                     const __grid_constant__ Grid g,
                                                     const __grid_constant__ Layout L,
                                                     const __grid_constant__ SlotList sl) {
-    extern __shared__ float4 fq_all[];       // per warp: levels 1..3, 64 entries each
     __shared__ unsigned long long sh_t[32];
+    __shared__ SmemCam sc[FVV_MAX_CAMS];
+    const int ncam = NC > 0 ? NC : cams.n;
+    load_smem_cams(cams, ncam, sc);
+    __syncthreads();
     const int slot = sl.s[blockIdx.y];
     const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
-    const uint32_t nsamp = info->n_words ? info->n_samples : 0u;
+    const uint32_t ntiles = info->n_words ? info->n_tiles : 0u;
     const int nrois = info->n_rois;
     const DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
     const uint32_t* __restrict__ sil = slot_ptr<uint32_t>(L, slot, L.sil);
     uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    float4* fq = fq_all + (threadIdx.x >> 5) * (kLevels - 1) * 64;
-    const int ncam = NC > 0 ? NC : cams.n;
-    const bool abstain = cams.oob == FVV_OOB_ABSTAIN;
-    const uint32_t fresh_step = gridDim.x * blockDim.x;
-    uint32_t fresh = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
-    int qn[kLevels] = {0, 0, 0, 0};          // entries queued per level (level 0 unused)
-    uint32_t tests = 0;
-    // per-lane ROI cursor for fresh samples
-    uint32_t lo = 0, hi = 0, woff = 0;
-    int fx = 1, fy = 1, nxw = 1;
-    float fo0 = 0.f, fo1 = 0.f, fo2 = 0.f;
-    for (;;) {
-        int lv = -1;
-#pragma unroll
-        for (int j = 1; j < kLevels; ++j)
-            if (qn[j] >= 32) lv = j;
-        if (lv < 0 && fresh < nsamp) lv = 0;
-        if (lv < 0) {
-#pragma unroll
-            for (int j = kLevels - 1; j >= 1; --j)
-                if (qn[j] > 0) lv = j;
-        }
-        if (lv < 0) break;
-        float X = 0.f, Y = 0.f, Z = 0.f;
-        uint32_t wb = 0;                     // word << 6 | voted << 5 | bit
-        bool act;
-        if (lv == 0) {
-            const uint32_t s = fresh + lane;
-            fresh += fresh_step;
-            act = s < nsamp;
-            if (act && (s >= hi || s < lo)) {
-                const DRoi& r = rois[roi_of_sample(rois, nrois, s)];
-                lo = r.samp_off;
-                fx = r.fdim[0];
-                fy = r.fdim[1];
-                hi = lo + (uint32_t)fx * (uint32_t)fy * (uint32_t)r.fdim[2];
-                woff = r.word_off;
-                nxw = r.nxw;
-                fo0 = r.fo[0];
-                fo1 = r.fo[1];
-                fo2 = r.fo[2];
-            }
-            const uint32_t loc = act ? s - lo : 0u;
-            const uint32_t row = loc / (uint32_t)fx;
-            const int x = (int)(loc - row * (uint32_t)fx);
-            const int y = (int)(row % (uint32_t)fy), z = (int)(row / (uint32_t)fy);
-            X = fadd(fo0, fmul(fadd((float)x, 0.5f), g.sf));
-            Y = fadd(fo1, fmul(fadd((float)y, 0.5f), g.sf));
-            Z = fadd(fo2, fmul(fadd((float)z, 0.5f), g.sf));
-            const uint32_t word = woff + ((uint32_t)(z + 1) * (uint32_t)(fy + 2) + (uint32_t)(y + 1)) * (uint32_t)nxw +
-                                  (uint32_t)((x + 1) >> 5);
-            wb = (word << 6) | (uint32_t)((x + 1) & 31);
-        } else {
-            const int take = min(qn[lv], 32);
-            qn[lv] -= take;
-            act = lane < take;
-            if (act) {
-                const float4 e = fq[(lv - 1) * 64 + qn[lv] + lane];
-                X = e.x;
-                Y = e.y;
-                Z = e.z;
-                wb = __float_as_uint(e.w);
-            }
-        }
-        bool alive = act, voted = !abstain || ((wb >> 5) & 1u);
-        if (abstain) test_level<NC, true>(cams, sil, lv, X, Y, Z, alive, voted, tests);
-        else test_level<NC, false>(cams, sil, lv, X, Y, Z, alive, voted, tests);
-        if (lvb(ncam, lv + 1) == ncam) {
-            // every camera done: OR the occupied samples into their words,
-            // one atomic per distinct word of the warp
-            const bool on = alive && voted;
-            const uint32_t word = wb >> 6, bit = 1u << (wb & 31u);
-            uint32_t pend = __ballot_sync(kFull, on);
-            while (pend) {
-                const int leader = __ffs(pend) - 1;
-                const uint32_t T = __shfl_sync(kFull, word, leader);
-                const bool mine = on && word == T;
-                const uint32_t ored = __reduce_or_sync(kFull, mine ? bit : 0u);
-                if (lane == leader) atomicOr(fine + T, ored);
-                pend &= ~__ballot_sync(kFull, mine);
-            }
-        } else {
-            // the popped entries were read above, before any lane writes
-            const uint32_t m = __ballot_sync(kFull, alive);
-            if (alive)
-                fq[lv * 64 + qn[lv + 1] + __popc(m & lt)] =
-                    make_float4(X, Y, Z, __uint_as_float((wb & ~32u) | (voted ? 32u : 0u)));
-            qn[lv + 1] += __popc(m);
-        }
-        __syncwarp();
-    }
+    unsigned long long tests = 0;
+    if (cams.oob == FVV_OOB_ABSTAIN) fine_tiles<NC, true>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tests);
+    else fine_tiles<NC, false>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tests);
     const unsigned long long t = block_sum<unsigned long long>(tests, sh_t);
     if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_fine, t);
 }
@@ -342,7 +385,7 @@ cudaError_t launch_fine_carve(const CamSet& cams, const Grid& g, const Layout& L
     k_clear_fine<<<dim3(gc, sl.n), 256, 0, st>>>(L, sl);
     const int th = tu.threads[FVV_TUNE_FINE];
     const int gx = tuned_grid(tu, FVV_TUNE_FINE, sms, sl.n, (long long)g.max_fine_words * 32);
-#define FVV_LAUNCH(NC) k_fine_carve<NC><<<dim3(gx, sl.n), th, (size_t)th / 32 * 3 * 64 * sizeof(float4), st>>>(cams, g, L, sl)
+#define FVV_LAUNCH(NC) k_fine_carve<NC><<<dim3(gx, sl.n), th, 0, st>>>(cams, g, L, sl)
     FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
     return cudaGetLastError();

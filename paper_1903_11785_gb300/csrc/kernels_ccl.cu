@@ -295,19 +295,21 @@ __global__ void __launch_bounds__(1024) k_filter(const __grid_constant__ Grid g,
         }
         return;
     }
-    // pass 2: first fine word and first interior sample of each ROI
+    // pass 2: first fine word and first fine-carve tile of each ROI
     unsigned long long wbase = 0, sbase = 0;
     for (int t0 = 0; t0 < K; t0 += blockDim.x) {
         const int i = t0 + threadIdx.x;
         const unsigned long long nw = i < K ? rois[i].n_words : 0ull;
         const unsigned long long ns =
-            i < K ? (unsigned long long)rois[i].fdim[0] * rois[i].fdim[1] * rois[i].fdim[2] : 0ull;
+            i < K ? (unsigned long long)((rois[i].fdim[0] + kTileX - 1) / kTileX) *
+                        ((rois[i].fdim[1] + kTileY - 1) / kTileY) * ((rois[i].fdim[2] + kTileZ - 1) / kTileZ)
+                  : 0ull;
         unsigned long long tw, ts;
         const unsigned long long ew = block_exclusive_scan64(nw, sh64, tw);
         const unsigned long long es = block_exclusive_scan64(ns, sh64, ts);
         if (i < K) {
             rois[i].word_off = (uint32_t)min(wbase + ew, 0xFFFFFFFFull);
-            rois[i].samp_off = (uint32_t)min(sbase + es, 0xFFFFFFFFull);
+            rois[i].tile_off = (uint32_t)min(sbase + es, 0xFFFFFFFFull);
         }
         wbase += tw;
         sbase += ts;
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(1024) k_filter(const __grid_constant__ Grid g,
         } else {
             info->n_rois = K;
             info->n_words = (uint32_t)wbase;
-            info->n_samples = (uint32_t)sbase;
+            info->n_tiles = (uint32_t)sbase;
             info->n_chunks = (uint32_t)((wbase + kChunk - 1) / kChunk);
         }
     }

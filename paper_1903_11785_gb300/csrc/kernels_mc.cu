@@ -339,16 +339,6 @@ __device__ __forceinline__ bool segment_all_fg(const Cam& c, const uint32_t* __r
     return all;
 }
 
-// A camera's fields for the bisection's per-lane tests, in shared memory
-// (lanes test different cameras).
-struct __align__(16) SegCam {
-    float P[12];
-    float Wf, Hf;
-    int W, H, Wq;
-    uint32_t bit_off;
-    float pad_[2];
-};
-
 // Sec. II-C, exact intersection: between the ON end a and the OFF end b of a
 // bipolar edge, `steps` times m = (a+b)/2, a = m if m is occupied else b = m;
 // the vertex is the final midpoint.  One vertex per thread.
@@ -365,18 +355,9 @@ template <int NC>
 __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
                                                 const __grid_constant__ Layout L, const __grid_constant__ SlotList sl) {
     __shared__ unsigned long long sh_t[32];
-    __shared__ SegCam sc[FVV_MAX_CAMS];
+    __shared__ SmemCam sc[FVV_MAX_CAMS];
     const int ncam = NC > 0 ? NC : cams.n;
-    for (int n = threadIdx.x; n < ncam; n += blockDim.x) {
-        const Cam& c = cams.c[n];
-        for (int k = 0; k < 12; ++k) sc[n].P[k] = c.P[k];
-        sc[n].Wf = c.Wf;
-        sc[n].Hf = c.Hf;
-        sc[n].W = c.W;
-        sc[n].H = c.H;
-        sc[n].Wq = c.Wq;
-        sc[n].bit_off = c.bit_off;
-    }
+    load_smem_cams(cams, ncam, sc);
     __syncthreads();
     const bool abstain = cams.oob == FVV_OOB_ABSTAIN;
     const int slot = sl.s[blockIdx.y];
@@ -427,7 +408,7 @@ __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet c
             bool voted = !abstain || seen_fg;
             for (uint64_t u = undecided; u; u &= u - 1) {
                 const int n = __ffsll((long long)u) - 1;
-                const SegCam& c = sc[n];
+                const SmemCam& c = sc[n];
                 float xp, yp, wp;
                 project(c.P, m[0], m[1], m[2], xp, yp, wp);
                 const float rw = rcp_approx(wp);
