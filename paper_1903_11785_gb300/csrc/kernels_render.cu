@@ -43,17 +43,6 @@ __device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const f
         ok &= wh[j] > 0.0f;
     }
     if (!ok) return;
-    // homogeneous edge functions of edges (0,1), (1,2), (2,0): no division
-    float ea[3], eb[3], ec[3];
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-        const int i = e, j = (e + 1) % 3;
-        ea[e] = fsub(fmul(yh[i], wh[j]), fmul(wh[i], yh[j]));
-        eb[e] = fsub(fmul(xh[i], wh[j]), fmul(wh[i], xh[j]));
-        ec[e] = fsub(fmul(xh[i], yh[j]), fmul(yh[i], xh[j]));
-    }
-    const float det = fadd(fsub(fmul(xh[0], ea[1]), fmul(yh[0], eb[1])), fmul(wh[0], ec[1]));
-    if (!(det > 0.0f || det < 0.0f)) return;
     // candidate pixels: centres within 1/64 px of the box of the approximate
     // projections (their error is below 1e-3 px for images up to 65535 px;
     // the exact box test below decides)
@@ -71,6 +60,18 @@ __device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const f
     const int y0 = max(0, (int)ceilf(fsub(vmin, kSlack)));
     const int x1 = umax > c.Wf ? c.W - 1 : min(c.W - 1, (int)floorf(fsub(fadd(umax, 1.0f / 64.0f), 0.5f)));
     const int y1 = vmax > c.Hf ? c.H - 1 : min(c.H - 1, (int)floorf(fsub(fadd(vmax, 1.0f / 64.0f), 0.5f)));
+    if (x0 > x1 || y0 > y1) return;      // no pixel centre near the box
+    // homogeneous edge functions of edges (0,1), (1,2), (2,0): no division
+    float ea[3], eb[3], ec[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int i = e, j = (e + 1) % 3;
+        ea[e] = fsub(fmul(yh[i], wh[j]), fmul(wh[i], yh[j]));
+        eb[e] = fsub(fmul(xh[i], wh[j]), fmul(wh[i], xh[j]));
+        ec[e] = fsub(fmul(xh[i], yh[j]), fmul(yh[i], xh[j]));
+    }
+    const float det = fadd(fsub(fmul(xh[0], ea[1]), fmul(yh[0], eb[1])), fmul(wh[0], ec[1]));
+    if (!(det > 0.0f || det < 0.0f)) return;
     for (int yy = y0; yy <= y1; ++yy) {
         const float pcy = fadd((float)yy, 0.5f);
         const float s0 = __fmaf_rn(pcy, wh[0], -yh[0]), s1 = __fmaf_rn(pcy, wh[1], -yh[1]),
