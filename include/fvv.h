@@ -96,6 +96,9 @@ enum { FVV_OOB_STRICT = 0, FVV_OOB_ABSTAIN = 1 };
  *   pixel visited counts as one test (fvv_counts.tests_bisect). */
 enum { FVV_SURFACE_BISECT = 0, FVV_SURFACE_LAMBDA = 1 };
 
+/* fvv_colour / fvv_render_view: RGB read in place from mapped host memory. */
+#define FVV_RGB_MAPPED_HOST 2
+
 /* Bits of fvv_counts.flags: which capacity a reconstruction exceeded. */
 enum {
     FVV_FLAG_ROOTS = 1u << 0,      /* raw 26-connected components > max_components */
@@ -296,9 +299,9 @@ enum {
  * cameras ranked for the viewpoint `centre` -- the nearest capture camera
  * that sees the point unoccluded (|X - C| - depth <= t_v), else the next
  * ones -- so the capture camera is chosen per pixel.
- *   rgb      n_cams capture images (H x W x 3 uint8 each), device pointers
- *            if rgb_on_device, else host (needs host_staging; copied into the
- *            slot's staging, which this call then overwrites);
+ *   rgb      n_cams capture images (H x W x 3 uint8 each), located as
+ *            rgb_on_device says (see fvv_colour; with 0 they are copied into
+ *            the slot's staging, which this call then overwrites);
  *   P, centre  host arrays of 12 and 3 finite floats;
  *   key      device, width*height uint64, written: per pixel (squared
  *            distance as float bits) << 32 | triangle index within the slot's

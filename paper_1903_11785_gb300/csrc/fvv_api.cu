@@ -236,6 +236,7 @@ fvv_status make_plan(const fvv_rig_desc* d, const fvv_recon_params* p, Plan& pl,
     take(L.verts, (size_t)mv * 12);
     take(L.tris, (size_t)mt * 12);
     take(L.tcen, (size_t)mt * 12);
+    take(L.trec, (size_t)mt * 8);
     take(L.vrgb, (size_t)mv * 3);
     take(L.vcam, (size_t)mv * 4);
     take(L.depth, align_up(pix * 4));
@@ -602,6 +603,26 @@ fvv_status fvv_autotune(fvv_rig* rig, const int* slots, int n_slots, void* strea
     return FVV_OK;
 }
 
+// The device address of a camera image of `bytes` bytes at host address p in
+// page-locked, device-mapped host memory (FVV_RGB_MAPPED_HOST), or NULL if
+// its first or last byte is not in such memory.
+static const uint8_t* mapped_host(const uint8_t* p, size_t bytes) {
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaPointerGetAttributes(&b, p + bytes - 1) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+        return nullptr;
+    const uint8_t* d = static_cast<const uint8_t*>(a.devicePointer);
+    if (static_cast<const uint8_t*>(b.devicePointer) != d + bytes - 1) return nullptr;
+    return d;
+}
+
 fvv_status fvv_colour(fvv_rig* rig, const int* slots, int n_slots, const uint8_t* const* rgb, int rgb_on_device,
                       const float* viewpoints, void* stream) {
     if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
@@ -609,6 +630,8 @@ fvv_status fvv_colour(fvv_rig* rig, const int* slots, int n_slots, const uint8_t
     fvv_status s = make_slot_list(rig, slots, n_slots, 2, sl);
     if (s != FVV_OK) return s;
     if (!rgb || !viewpoints) return fail(rig, FVV_ERR_INVALID_ARG, "rgb and viewpoints must not be NULL");
+    if (rgb_on_device < 0 || rgb_on_device > FVV_RGB_MAPPED_HOST)
+        return fail(rig, FVV_ERR_INVALID_ARG, "rgb_on_device must be 0, 1 or FVV_RGB_MAPPED_HOST");
     if (!rgb_on_device && !rig->host_staging) return fail(rig, FVV_ERR_INVALID_ARG, "host RGB needs host_staging");
     for (int i = 0; i < 3 * n_slots; ++i)
         if (!std::isfinite(viewpoints[i])) return fail(rig, FVV_ERR_INVALID_ARG, "viewpoints must be finite");
@@ -616,6 +639,13 @@ fvv_status fvv_colour(fvv_rig* rig, const int* slots, int n_slots, const uint8_t
     const int N = rig->cams.n;
     for (size_t i = 0; i < (size_t)n_slots * N; ++i)
         if (!rgb[i]) return fail(rig, FVV_ERR_INVALID_ARG, "an rgb pointer is NULL");
+    if (rgb_on_device == FVV_RGB_MAPPED_HOST)
+        for (int i = 0; i < n_slots; ++i)
+            for (int n = 0; n < N; ++n) {
+                const Cam& c = rig->cams.c[n];
+                if (!mapped_host(rgb[(size_t)i * N + n], (size_t)3 * c.W * c.H))
+                    return fail(rig, FVV_ERR_INVALID_ARG, "an rgb image is not in mapped page-locked host memory");
+            }
     cudaError_t e = cudaSuccess;
     const int t = stage_begin(rig, FVV_STAGE_COLOUR, st);
     // slots go to the kernel in groups of kColourBatch, with their RGB sources
@@ -629,8 +659,11 @@ fvv_status fvv_colour(fvv_rig* rig, const int* slots, int n_slots, const uint8_t
             for (int k = 0; k < 3; ++k) cb.view[j][k] = viewpoints[3 * i + k];
             for (int n = 0; n < N; ++n) {
                 const uint8_t* src = rgb[(size_t)i * N + n];
-                if (rgb_on_device) {
+                if (rgb_on_device == 1) {
                     cb.rgb[j][n] = src;
+                } else if (rgb_on_device == FVV_RGB_MAPPED_HOST) {
+                    const Cam& c = rig->cams.c[n];
+                    cb.rgb[j][n] = mapped_host(src, (size_t)3 * c.W * c.H);   // checked above
                 } else {
                     const Cam& c = rig->cams.c[n];
                     uint8_t* dst = slot_ptr<uint8_t>(rig->L, sl.s[i], rig->L.rgb_stage) + 3 * c.pix_off;
@@ -658,6 +691,8 @@ fvv_status fvv_render_view(fvv_rig* rig, int slot, const uint8_t* const* rgb, in
         return fail(rig, FVV_ERR_INVALID_ARG, "rgb, P, centre, key and out_rgb must not be NULL");
     if (width < 1 || height < 1 || width > 65535 || height > 65535)
         return fail(rig, FVV_ERR_INVALID_ARG, "view size must be 1..65535 pixels per side");
+    if (rgb_on_device < 0 || rgb_on_device > FVV_RGB_MAPPED_HOST)
+        return fail(rig, FVV_ERR_INVALID_ARG, "rgb_on_device must be 0, 1 or FVV_RGB_MAPPED_HOST");
     if (!rgb_on_device && !rig->host_staging) return fail(rig, FVV_ERR_INVALID_ARG, "host RGB needs host_staging");
     for (int i = 0; i < 12; ++i)
         if (!std::isfinite(P[i])) return fail(rig, FVV_ERR_INVALID_ARG, "P must be finite");
@@ -678,8 +713,12 @@ fvv_status fvv_render_view(fvv_rig* rig, int slot, const uint8_t* const* rgb, in
     va.slot = slot;
     cudaError_t e = cudaSuccess;
     for (int n = 0; n < N && e == cudaSuccess; ++n) {
-        if (rgb_on_device) {
+        if (rgb_on_device == 1) {
             va.rgb[n] = rgb[n];
+        } else if (rgb_on_device == FVV_RGB_MAPPED_HOST) {
+            const Cam& c = rig->cams.c[n];
+            va.rgb[n] = mapped_host(rgb[n], (size_t)3 * c.W * c.H);
+            if (!va.rgb[n]) return fail(rig, FVV_ERR_INVALID_ARG, "an rgb image is not in mapped page-locked host memory");
         } else {
             const Cam& c = rig->cams.c[n];
             uint8_t* dst = slot_ptr<uint8_t>(rig->L, slot, rig->L.rgb_stage) + 3 * c.pix_off;

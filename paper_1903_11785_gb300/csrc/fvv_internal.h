@@ -106,6 +106,7 @@ struct Layout {
     size_t verts;               // float x3, max_verts
     size_t tris;                // uint32 x3, max_tris
     size_t tcen;                // float x3 triangle centroids, max_tris
+    size_t trec;                // uint64 triangle records (word, cell, case, triangle, ROI), max_tris
     size_t vrgb;                // uint8 x3, max_verts
     size_t vcam;                // int32, max_verts
     size_t depth;               // uint32 per pixel of all cameras

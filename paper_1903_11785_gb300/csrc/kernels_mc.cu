@@ -260,9 +260,24 @@ __device__ __forceinline__ uint64_t pack_vrec(int k, int axis, int s0on, int xp,
            (uint64_t)zp << 47;
 }
 
+// Triangle record: fine word (26 bits) | cell bit (5) | triangle of the cell
+// (4) | cell case (8) | ROI (14).
+__device__ __forceinline__ uint64_t pack_trec(uint32_t w, int b, int j, int cs, int k) {
+    return (uint64_t)w | (uint64_t)b << 26 | (uint64_t)j << 31 | (uint64_t)cs << 35 | (uint64_t)k << 43;
+}
+
+// After the scans: per fine word its vertex and triangle offsets, a record
+// per vertex (the bipolar edges in canonical order) and a record per
+// triangle (the word's surface cells in order, each cell's triangles in
+// table order), so that the bisection and the triangle kernel take one
+// vertex or triangle per thread.
 __global__ void __launch_bounds__(kChunk) k_mc_vertices(const __grid_constant__ Layout L,
-                                                        const __grid_constant__ SlotList sl) {
+                                                        const __grid_constant__ SlotList sl,
+                                                        const __grid_constant__ McTable mc) {
     __shared__ uint32_t sh[33];
+    __shared__ uint8_t s_ntri[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_ntri[i] = mc.ntri[i];
+    __syncthreads();
     const int slot = sl.s[blockIdx.y];
     const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
     const uint32_t nwords = info->n_words, nchunks = (nwords + kChunk - 1) / kChunk;
@@ -276,6 +291,7 @@ __global__ void __launch_bounds__(kChunk) k_mc_vertices(const __grid_constant__ 
     uint32_t* vpre = slot_ptr<uint32_t>(L, slot, L.vpre);
     uint32_t* tpre = slot_ptr<uint32_t>(L, slot, L.tpre);
     uint64_t* vrec = slot_ptr<uint64_t>(L, slot, L.vrec);
+    uint64_t* trec = slot_ptr<uint64_t>(L, slot, L.trec);
     RoiCursor p;
     for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const uint32_t w = c * kChunk + threadIdx.x;
@@ -301,6 +317,17 @@ __global__ void __launch_bounds__(kChunk) k_mc_vertices(const __grid_constant__ 
             if ((xm >> b) & 1u) vrec[id++] = pack_vrec(p.k, 0, s0, xp, p.yp, p.zp);
             if ((ym >> b) & 1u) vrec[id++] = pack_vrec(p.k, 1, s0, xp, p.yp, p.zp);
             if ((zm >> b) & 1u) vrec[id++] = pack_vrec(p.k, 2, s0, xp, p.yp, p.zp);
+        }
+        if (tcnt[w]) {
+            Nbhd n;
+            load_nbhd(fine, p, w, n);
+            uint32_t mx = mixed_cells(n), t = et;
+            while (mx) {
+                const int b = __ffs(mx) - 1;
+                mx &= mx - 1;
+                const int cs = cell_case(n, b);
+                for (int j = 0; j < (int)s_ntri[cs]; ++j) trec[t++] = pack_trec(w, b, j, cs, p.k);
+            }
         }
     }
 }
@@ -538,74 +565,60 @@ __global__ void __launch_bounds__(256) k_lambda(const __grid_constant__ CamSet c
     if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_bisect, t);
 }
 
+// Sec. II-C: the triangles, one per thread from the triangle records: the
+// table gives the triangle's three cube edges, and each edge's vertex id is
+// its word's vertex offset plus the rank of the edge among the word's
+// bipolar edges (x, y, z masks in canonical order).  Also the centroid
+// ((v0 + v1) + v2) / 3 of each triangle, for the depth images (Sec. II-D-1).
 __global__ void __launch_bounds__(256) k_mc_triangles(const __grid_constant__ Layout L,
                                                       const __grid_constant__ SlotList sl,
                                                       const __grid_constant__ McTable mc) {
-    __shared__ uint8_t s_ntri[256];
     __shared__ uint8_t s_edges[256 * kMaxTriPerCell * 3];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_ntri[i] = mc.ntri[i];
     for (int i = threadIdx.x; i < 256 * kMaxTriPerCell * 3; i += blockDim.x) s_edges[i] = mc.edges[i];
     __syncthreads();
     const int slot = sl.s[blockIdx.y];
     const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
-    const uint32_t nwords = info->n_words;
-    const int nrois = info->n_rois;
+    const uint32_t nt = info->n_words ? info->n_tris : 0u;
     const DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
-    const uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
     const uint32_t* emask = slot_ptr<uint32_t>(L, slot, L.emask);
     const uint32_t* vpre = slot_ptr<uint32_t>(L, slot, L.vpre);
-    const uint32_t* tpre = slot_ptr<uint32_t>(L, slot, L.tpre);
+    const uint64_t* trec = slot_ptr<uint64_t>(L, slot, L.trec);
     uint32_t* tris = slot_ptr<uint32_t>(L, slot, L.tris);
     const float* verts = slot_ptr<float>(L, slot, L.verts);
     float* tcen = slot_ptr<float>(L, slot, L.tcen);
-    RoiCursor p;
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) {
-        p.seek(rois, nrois, w);
-        const RoiCursor& r = p;
-        Nbhd n;
-        load_nbhd(fine, r, w, n);
-        uint32_t mx = mixed_cells(n);
-        uint32_t t = tpre[w];
-        const uint32_t rs = (uint32_t)r.nxw, ps = rs * (uint32_t)(r.fdim[1] + 2);
-        while (mx) {
-            const int b = __ffs(mx) - 1;
-            mx &= mx - 1;
-            const int cs = cell_case(n, b);
-            const int nt = s_ntri[cs];
-            for (int j = 0; j < nt; ++j) {
-                uint32_t id[3];
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        const uint64_t rec = trec[t];
+        const uint32_t w = (uint32_t)(rec & 0x3FFFFFFu);
+        const int b = (int)(rec >> 26 & 31u), j = (int)(rec >> 31 & 15u), cs = (int)(rec >> 35 & 255u);
+        const int k = (int)(rec >> 43 & 0x3FFFu);
+        const uint32_t rs = (uint32_t)rois[k].nxw, ps = rs * (uint32_t)(rois[k].fdim[1] + 2);
+        uint32_t id[3];
 #pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    const int e = s_edges[(cs * kMaxTriPerCell + j) * 3 + v];
-                    const int axis = e >> 2;
-                    // offsets of the edge's lower corner (same convention as the table)
-                    const int o0 = e & 1, o1 = (e >> 1) & 1;
-                    const int dx = axis == 0 ? 0 : o0;
-                    const int dy = axis == 1 ? 0 : (axis == 0 ? o0 : o1);
-                    const int dz = axis == 2 ? 0 : o1;
-                    const int X = p.wx * 32 + b + dx;
-                    const uint32_t wi = w + (uint32_t)(X >> 5) - (uint32_t)p.wx + (dy ? rs : 0u) + (dz ? ps : 0u);
-                    const int bb = X & 31;
-                    const uint32_t lm = (1u << bb) - 1u;
-                    const uint32_t xm = emask[3 * (size_t)wi], ym = emask[3 * (size_t)wi + 1],
-                                   zm = emask[3 * (size_t)wi + 2];
-                    uint32_t rank = __popc(xm & lm) + __popc(ym & lm) + __popc(zm & lm);
-                    if (axis >= 1) rank += (xm >> bb) & 1u;
-                    if (axis >= 2) rank += (ym >> bb) & 1u;
-                    id[v] = vpre[wi] + rank;
-                }
-                tris[3 * (size_t)t + 0] = id[0];
-                tris[3 * (size_t)t + 1] = id[1];
-                tris[3 * (size_t)t + 2] = id[2];
-                // centroid ((v0 + v1) + v2) / 3 for the depth images (Sec. II-D-1)
+        for (int v = 0; v < 3; ++v) {
+            const int e = s_edges[(cs * kMaxTriPerCell + j) * 3 + v];
+            const int axis = e >> 2;
+            // offsets of the edge's lower corner (same convention as the table)
+            const int o0 = e & 1, o1 = (e >> 1) & 1;
+            const int dx = axis == 0 ? 0 : o0;
+            const int dy = axis == 1 ? 0 : (axis == 0 ? o0 : o1);
+            const int dz = axis == 2 ? 0 : o1;
+            const uint32_t wi = w + (uint32_t)((b + dx) >> 5) + (dy ? rs : 0u) + (dz ? ps : 0u);
+            const int bb = (b + dx) & 31;
+            const uint32_t lm = (1u << bb) - 1u;
+            const uint32_t xm = emask[3 * (size_t)wi], ym = emask[3 * (size_t)wi + 1], zm = emask[3 * (size_t)wi + 2];
+            uint32_t rank = __popc(xm & lm) + __popc(ym & lm) + __popc(zm & lm);
+            if (axis >= 1) rank += (xm >> bb) & 1u;
+            if (axis >= 2) rank += (ym >> bb) & 1u;
+            id[v] = vpre[wi] + rank;
+        }
+        tris[3 * (size_t)t + 0] = id[0];
+        tris[3 * (size_t)t + 1] = id[1];
+        tris[3 * (size_t)t + 2] = id[2];
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const float s = fadd(fadd(verts[3 * (size_t)id[0] + d], verts[3 * (size_t)id[1] + d]),
-                                         verts[3 * (size_t)id[2] + d]);
-                    tcen[3 * (size_t)t + d] = __fdiv_rn(s, 3.0f);
-                }
-                ++t;
-            }
+        for (int d = 0; d < 3; ++d) {
+            const float s = fadd(fadd(verts[3 * (size_t)id[0] + d], verts[3 * (size_t)id[1] + d]),
+                                 verts[3 * (size_t)id[2] + d]);
+            tcen[3 * (size_t)t + d] = __fdiv_rn(s, 3.0f);
         }
     }
 }
@@ -617,7 +630,7 @@ cudaError_t launch_mc_prefix(const Grid& g, const Layout& L, const SlotList& sl,
     const int gc = grid_x(sms, sl.n, g.max_chunks, 1);
     k_mc_count<<<dim3(gc, sl.n), kChunk, 0, st>>>(L, sl, mc);
     k_mc_scan<<<sl.n, 1024, 0, st>>>(g, L, sl);
-    k_mc_vertices<<<dim3(gc, sl.n), kChunk, 0, st>>>(L, sl);
+    k_mc_vertices<<<dim3(gc, sl.n), kChunk, 0, st>>>(L, sl, mc);
     return cudaGetLastError();
 }
 
@@ -639,7 +652,7 @@ cudaError_t launch_bisect(const CamSet& cams, const Grid& g, const Layout& L, co
 
 cudaError_t launch_mc_triangles(const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc, int sms,
                                 const Tuning& tu, cudaStream_t st) {
-    const int gw = tuned_grid(tu, FVV_TUNE_TRIANGLES, sms, sl.n, g.max_fine_words);
+    const int gw = tuned_grid(tu, FVV_TUNE_TRIANGLES, sms, sl.n, g.max_tris);
     k_mc_triangles<<<dim3(gw, sl.n), tu.threads[FVV_TUNE_TRIANGLES], 0, st>>>(L, sl, mc);
     return cudaGetLastError();
 }

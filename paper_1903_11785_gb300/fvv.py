@@ -29,6 +29,7 @@ FVV_OK, FVV_ERR_INVALID_ARG, FVV_ERR_OUT_OF_MEMORY, FVV_ERR_CAPACITY, FVV_ERR_NO
     FVV_ERR_CUDA = range(7)
 FVV_OOB_STRICT, FVV_OOB_ABSTAIN = 0, 1
 FVV_SURFACE_BISECT, FVV_SURFACE_LAMBDA = 0, 1
+FVV_RGB_MAPPED_HOST = 2
 FVV_MAX_CAMS, FVV_MAX_BATCH = 64, 256
 FVV_DEBUG_SIL_BITS, FVV_DEBUG_COARSE_BITS, FVV_DEBUG_LABELS, FVV_DEBUG_FINE_BITS, FVV_DEBUG_DEPTH = range(5)
 FLAG_NAMES = {1: "ROOTS", 2: "ROIS", 4: "FINE", 8: "VERTS", 16: "TRIS", 32: "LOOP"}
@@ -212,10 +213,19 @@ def fvv_reconstruct(rig_ptr, slots, stream=None):
     _check(_lib.fvv_reconstruct(rig_ptr, arr, len(slots), _stream(stream)), rig_ptr)
 
 
-def fvv_colour(rig_ptr, slots, rgb, viewpoints, stream=None):
+def _rgb_mode(on_dev, imgs, in_place):
+    if on_dev or not in_place:
+        return on_dev
+    assert all(t.is_pinned() for t in imgs), "in-place RGB needs pinned host tensors"
+    return FVV_RGB_MAPPED_HOST
+
+
+def fvv_colour(rig_ptr, slots, rgb, viewpoints, stream=None, in_place=False):
     """rgb: per slot, a list of per-camera (H,W,3) uint8 tensors (or an
-    (N,H,W,3) tensor); viewpoints: (n_slots,3)."""
-    ptrs, on_dev = [], None
+    (N,H,W,3) tensor); viewpoints: (n_slots,3).  in_place: pinned host
+    tensors are read in place by the kernel (FVV_RGB_MAPPED_HOST) instead of
+    being copied to the device."""
+    ptrs, on_dev, all_imgs = [], None, []
     for per_slot in rgb:
         imgs = list(per_slot) if not torch.is_tensor(per_slot) else list(per_slot.unbind(0))
         for t in imgs:
@@ -223,13 +233,15 @@ def fvv_colour(rig_ptr, slots, rgb, viewpoints, stream=None):
             on_dev = int(t.is_cuda) if on_dev is None else on_dev
             assert int(t.is_cuda) == on_dev
             ptrs.append(t.data_ptr())
+            all_imgs.append(t)
+    on_dev = _rgb_mode(on_dev, all_imgs, in_place)
     vp = np.ascontiguousarray(np.asarray(viewpoints, np.float32).reshape(len(slots), 3))
     arr = (C.c_int * len(slots))(*slots)
     _check(_lib.fvv_colour(rig_ptr, arr, len(slots), _ptr_array(ptrs), on_dev,
                            vp.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream)), rig_ptr)
 
 
-def fvv_render_view(rig_ptr, slot, rgb, P, centre, width, height, stream=None, with_cam=True):
+def fvv_render_view(rig_ptr, slot, rgb, P, centre, width, height, stream=None, with_cam=True, in_place=False):
     """Step E: a novel view of a reconstructed slot from a virtual camera.
     rgb: per-camera (H,W,3) uint8 tensors (or an (N,H,W,3) tensor), all on
     the device or all in host memory.  Returns device tensors (key (H,W)
@@ -241,6 +253,7 @@ def fvv_render_view(rig_ptr, slot, rgb, P, centre, width, height, stream=None, w
         assert t.dtype == torch.uint8 and t.is_contiguous()
         on_dev = int(t.is_cuda) if on_dev is None else on_dev
         assert int(t.is_cuda) == on_dev
+    on_dev = _rgb_mode(on_dev, imgs, in_place)
     Pm = np.ascontiguousarray(np.asarray(P, np.float32).reshape(12))
     Cm = np.ascontiguousarray(np.asarray(centre, np.float32).reshape(3))
     key = torch.empty((height, width), dtype=torch.int64, device="cuda")
@@ -346,11 +359,11 @@ class Rig:
     def reconstruct(self, slots, stream=None):
         fvv_reconstruct(self.ptr, list(slots), stream)
 
-    def colour(self, slots, rgb, viewpoints, stream=None):
-        fvv_colour(self.ptr, list(slots), rgb, viewpoints, stream)
+    def colour(self, slots, rgb, viewpoints, stream=None, in_place=False):
+        fvv_colour(self.ptr, list(slots), rgb, viewpoints, stream, in_place)
 
-    def render_view(self, slot, rgb, P, centre, width, height, stream=None, with_cam=True):
-        return fvv_render_view(self.ptr, slot, rgb, P, centre, width, height, stream, with_cam)
+    def render_view(self, slot, rgb, P, centre, width, height, stream=None, with_cam=True, in_place=False):
+        return fvv_render_view(self.ptr, slot, rgb, P, centre, width, height, stream, with_cam, in_place)
 
     def counts(self, slot, stream=None, allow_capacity=False):
         return fvv_get_counts(self.ptr, slot, stream, allow_capacity)

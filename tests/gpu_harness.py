@@ -12,7 +12,7 @@ def unpack_rows(words: np.ndarray, shape_rows, width):
     return b.reshape(*shape_rows, -1)[..., :width]
 
 
-def run_gpu(rig, frames, host=False, caps=None, slots=None, batch=True):
+def run_gpu(rig, frames, host=False, caps=None, slots=None, batch=True, rgb_in_place=False):
     """Upload, reconstruct (all slots in one call when batch) and colour.
     Returns one dict of numpy outputs per frame."""
     from paper_1903_11785_gb300 import fvv
@@ -29,9 +29,9 @@ def run_gpu(rig, frames, host=False, caps=None, slots=None, batch=True):
         else:
             for s in slots:
                 r.reconstruct([s])
-        rgbs = [fr.rgb.pin_memory() if host else fr.rgb.cuda() for fr in frames]
+        rgbs = [fr.rgb.pin_memory() if (host or rgb_in_place) else fr.rgb.cuda() for fr in frames]
         vps = np.stack([fr.viewpoint for fr in frames])
-        r.colour(slots, rgbs, vps)
+        r.colour(slots, rgbs, vps, in_place=rgb_in_place)
         torch.cuda.synchronize()
         outs = []
         for s in slots:

@@ -38,6 +38,32 @@ def test_tiny_host_buffers_match():
     compare(rig, fr, g)
 
 
+def test_colour_reads_pinned_host_rgb_in_place():
+    """FVV_RGB_MAPPED_HOST: the colour kernel reads pinned host images in
+    place (no staging copy) and gives the oracle's colours; pageable host
+    memory is refused without launching anything."""
+    rig = make_rig("tiny")
+    frames = [make_frame("tiny", i, rig=rig)[1] for i in range(2)]
+    outs = run_gpu(rig, frames, rgb_in_place=True)
+    for fr, g in zip(frames, outs):
+        compare(rig, fr, g)
+    from paper_1903_11785_gb300 import fvv
+    r = fvv.Rig(rig, max_slots=1, host_staging=0)
+    try:
+        r.upload_silhouettes(0, frames[0].masks.cuda())
+        r.reconstruct([0])
+        pageable = [np.ascontiguousarray(frames[0].rgb[n].numpy()) for n in range(rig.n_cams)]
+        ptrs = fvv._ptr_array([a.ctypes.data for a in pageable])
+        vp = np.ascontiguousarray(frames[0].viewpoint, np.float32)
+        arr = (fvv.C.c_int * 1)(0)
+        st = fvv._lib.fvv_colour(r.ptr, arr, 1, ptrs, fvv.FVV_RGB_MAPPED_HOST,
+                                 vp.ctypes.data_as(fvv.C.POINTER(fvv.C.c_float)), fvv._stream())
+        assert st == fvv.FVV_ERR_INVALID_ARG
+        torch.cuda.synchronize()
+    finally:
+        r.close()
+
+
 def test_batched_slots_each_bit_exact():
     """Three frames in one reconstruct/colour call, slots listed out of order."""
     rig = make_rig("tiny")

@@ -24,14 +24,14 @@ def _view(rig, index, W, H, f, target):
     return P.astype(np.float32), np.asarray(C, np.float32)
 
 
-def _compare(rig, fr, P, C, W, H, host=False):
+def _compare(rig, fr, P, C, W, H, host=False, in_place=False):
     from paper_1903_11785_gb300 import fvv
     r = fvv.Rig(rig, max_slots=1, host_staging=int(host))
     try:
         r.upload_silhouettes(0, fr.masks.cuda())
         r.reconstruct([0])
-        rgb = fr.rgb.pin_memory() if host else fr.rgb.cuda()
-        key, out, cam = r.render_view(0, rgb, P, C, W, H)
+        rgb = fr.rgb.pin_memory() if (host or in_place) else fr.rgb.cuda()
+        key, out, cam = r.render_view(0, rgb, P, C, W, H, in_place=in_place)
         torch.cuda.synchronize()
         key, out, cam = key.cpu().numpy(), out.cpu().numpy(), cam.cpu().numpy()
     finally:
@@ -63,6 +63,13 @@ def test_tiny_view_host_rgb_and_ragged_size():
     P, C = _view(rig, 1, 333, 217, 300.0, (0.0, 0.0, 0.9))
     covered, _ = _compare(rig, fr, P, C, 333, 217, host=True)
     assert covered > 500
+
+
+def test_view_reads_pinned_host_rgb_in_place():
+    rig, fr = make_frame("tiny", 2)
+    P, C = _view(rig, 2, 320, 180, 250.0, (0.0, 0.0, 0.9))
+    covered, _ = _compare(rig, fr, P, C, 320, 180, in_place=True)
+    assert covered > 300
 
 
 def test_volleyball_view_bit_exact():
