@@ -120,7 +120,9 @@ typedef struct {
     const int *height;     /* n_cams: image height in pixels, 1..65535        */
     int max_slots;         /* frames that can be held at once, >= 1           */
     int host_staging;      /* 1: reserve per-slot buffers so masks and RGB can
-                              be passed in host memory; 0: device pointers only */
+                              be passed in host memory (copied); 2: masks
+                              only (RGB then comes from the device or is read
+                              in place, FVV_RGB_MAPPED_HOST); 0: none */
 } fvv_rig_desc;
 
 /* Reconstruction parameters.  The capacities are per slot; 0 picks a default

@@ -240,10 +240,9 @@ fvv_status make_plan(const fvv_rig_desc* d, const fvv_recon_params* p, Plan& pl,
     take(L.vrgb, (size_t)mv * 3);
     take(L.vcam, (size_t)mv * 4);
     take(L.depth, align_up(pix * 4));
-    if (d->host_staging) {
-        take(L.mask_stage, pix);
-        take(L.rgb_stage, pix * 3);
-    }
+    if (d->host_staging < 0 || d->host_staging > 2) { err = "host_staging must be 0, 1 or 2"; return FVV_ERR_INVALID_ARG; }
+    if (d->host_staging) take(L.mask_stage, pix);
+    if (d->host_staging == 1) take(L.rgb_stage, pix * 3);
     L.stride = o;
     pl.common = align_up(256) + align_up(256 * kMaxTriPerCell * 3) + align_up(FVV_MAX_BATCH * 3 * sizeof(float));
     pl.total = pl.common + (size_t)d->max_slots * L.stride;
@@ -632,7 +631,8 @@ fvv_status fvv_colour(fvv_rig* rig, const int* slots, int n_slots, const uint8_t
     if (!rgb || !viewpoints) return fail(rig, FVV_ERR_INVALID_ARG, "rgb and viewpoints must not be NULL");
     if (rgb_on_device < 0 || rgb_on_device > FVV_RGB_MAPPED_HOST)
         return fail(rig, FVV_ERR_INVALID_ARG, "rgb_on_device must be 0, 1 or FVV_RGB_MAPPED_HOST");
-    if (!rgb_on_device && !rig->host_staging) return fail(rig, FVV_ERR_INVALID_ARG, "host RGB needs host_staging");
+    if (!rgb_on_device && rig->host_staging != 1)
+        return fail(rig, FVV_ERR_INVALID_ARG, "copied host RGB needs host_staging = 1");
     for (int i = 0; i < 3 * n_slots; ++i)
         if (!std::isfinite(viewpoints[i])) return fail(rig, FVV_ERR_INVALID_ARG, "viewpoints must be finite");
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -693,7 +693,8 @@ fvv_status fvv_render_view(fvv_rig* rig, int slot, const uint8_t* const* rgb, in
         return fail(rig, FVV_ERR_INVALID_ARG, "view size must be 1..65535 pixels per side");
     if (rgb_on_device < 0 || rgb_on_device > FVV_RGB_MAPPED_HOST)
         return fail(rig, FVV_ERR_INVALID_ARG, "rgb_on_device must be 0, 1 or FVV_RGB_MAPPED_HOST");
-    if (!rgb_on_device && !rig->host_staging) return fail(rig, FVV_ERR_INVALID_ARG, "host RGB needs host_staging");
+    if (!rgb_on_device && rig->host_staging != 1)
+        return fail(rig, FVV_ERR_INVALID_ARG, "copied host RGB needs host_staging = 1");
     for (int i = 0; i < 12; ++i)
         if (!std::isfinite(P[i])) return fail(rig, FVV_ERR_INVALID_ARG, "P must be finite");
     for (int i = 0; i < 3; ++i)

@@ -8,7 +8,8 @@ admitted when its rig has a free slot, otherwise it waits in that rig's
 queue.  On every pass the loop gathers the requests admitted since the last
 pass into one batch per rig and issues, on one of the rig's streams, the
 host-to-device copies and packing of their silhouettes, one fvv_reconstruct
-over the batch and one fvv_colour; batches of different rigs, and
+over the batch and one fvv_colour (which reads pinned RGB images in place,
+so a slot needs no RGB staging); batches of different rigs, and
 successive batches of one rig (on alternating streams, disjoint slots), run
 concurrently on the GPU.  A slot is freed when its batch's completion event
 has fired.  Latency is measured from a request's scheduled arrival to the
@@ -49,10 +50,20 @@ class RigPool:
     viewpoints: np.ndarray  # (F,3) float32
 
 
-def slot_bytes(scene_rig, **caps) -> int:
-    """Device bytes one more slot costs for this rig (with host staging)."""
-    a = fvv.fvv_query_arena(fvv.make_desc(scene_rig, 1, 1), fvv.make_params(scene_rig, **caps))
-    b = fvv.fvv_query_arena(fvv.make_desc(scene_rig, 2, 1), fvv.make_params(scene_rig, **caps))
+def _staging(pool) -> int:
+    """Host staging a rig's slots need: masks only when the pool's RGB is
+    pinned (read in place by the colour kernel), else masks and RGB."""
+    return 2 if _rgb_pinned(pool) else 1
+
+
+def _rgb_pinned(pool) -> bool:
+    return all(t.is_pinned() for t in pool.rgb)
+
+
+def slot_bytes(scene_rig, staging: int = 1, **caps) -> int:
+    """Device bytes one more slot costs for this rig (with that host staging)."""
+    a = fvv.fvv_query_arena(fvv.make_desc(scene_rig, 1, staging), fvv.make_params(scene_rig, **caps))
+    b = fvv.fvv_query_arena(fvv.make_desc(scene_rig, 2, staging), fvv.make_params(scene_rig, **caps))
     return b - a
 
 
@@ -74,7 +85,8 @@ def poisson_schedule(n_rigs, rate_hz, n_requests, seed, pool_sizes):
 class _RigState:
     def __init__(self, pool: RigPool, n_slots: int, n_streams: int, caps: dict):
         self.pool = pool
-        self.rig = fvv.Rig(pool.scene_rig, max_slots=n_slots, host_staging=1, **caps)
+        self.rgb_in_place = _rgb_pinned(pool)
+        self.rig = fvv.Rig(pool.scene_rig, max_slots=n_slots, host_staging=_staging(pool), **caps)
         self.free = list(range(n_slots))
         self.queue = []            # waiting requests
         self.pending = []          # admitted, not yet issued
@@ -91,7 +103,7 @@ class Server:
         self.rigs = []
         self.slots = []
         for p in pools:
-            n = int(min(max_slots_per_rig, share // slot_bytes(p.scene_rig, **caps)))
+            n = int(min(max_slots_per_rig, share // slot_bytes(p.scene_rig, _staging(p), **caps)))
             if n < 1:
                 raise MemoryError("memory budget too small for one slot of a rig")
             self.slots.append(n)
@@ -110,8 +122,9 @@ class Server:
             for q in reqs:
                 r.rig.upload_silhouettes(q.slot, r.pool.masks[q.frame], stream=st)
             r.rig.reconstruct(slots, stream=st)
-            r.rig.colour(slots, [r.pool.rgb[q.frame] for q in reqs],
-                         np.stack([r.pool.viewpoints[q.frame] for q in reqs]), stream=st)
+            rgb = [r.pool.rgb[q.frame] for q in reqs]
+            r.rig.colour(slots, rgb, np.stack([r.pool.viewpoints[q.frame] for q in reqs]), stream=st,
+                         in_place=r.rgb_in_place)
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(st)
         for q in reqs:

@@ -80,6 +80,10 @@ def test_query_arena_and_validation(fvv):
     bad = fvv.make_params(rig, max_fine_words=(1 << 26) + 1)   # fine words are packed in 26 bits
     with pytest.raises(fvv.FvvError):
         fvv.fvv_query_arena(d, bad)
+    n_masks_only = fvv.fvv_query_arena(fvv.make_desc(rig, max_slots=2, host_staging=2), p)
+    assert n1 - n_masks_only >= 2 * pix * 3            # no RGB staging
+    with pytest.raises(fvv.FvvError):
+        fvv.fvv_query_arena(fvv.make_desc(rig, max_slots=2, host_staging=3), p)
     d0 = fvv.make_desc(rig, max_slots=0)
     with pytest.raises(fvv.FvvError):
         fvv.fvv_query_arena(d0, p)
