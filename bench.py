@@ -467,8 +467,9 @@ def run_ours(args):
                      rgb=torch.empty((c["n_verts"], 3), dtype=torch.uint8).pin_memory(),
                      cam=torch.empty((c["n_verts"],), dtype=torch.int32).pin_memory()) for c in cnt]
         vp_ = fvv._vp
-        # the masks are copied in; the RGB images stay in pinned host memory and
-        # the colour kernel reads the pixels it needs in place (FVV_RGB_MAPPED_HOST)
+        # masks and RGB stay in pinned host memory: the packing kernel reads
+        # every mask byte over the host link, the colour kernel only the RGB
+        # pixels it needs (FVV_MAPPED_HOST)
         h2d = int(masks_h.numel())
         d2h = int(sum(sum(t.numel() * t.element_size() for t in o.values()) for o in outs))
 
@@ -485,7 +486,7 @@ def run_ours(args):
             def compute(grp, st):
                 with torch.cuda.stream(st):
                     for i in grp:
-                        r.upload_silhouettes(i, masks_h[i], stream=st)
+                        r.upload_silhouettes(i, masks_h[i], stream=st, in_place=True)
                     r.reconstruct(grp, stream=st)
                     r.colour(grp, rgb_h[grp[0]:grp[-1] + 1], vps[grp[0]:grp[-1] + 1], stream=st, in_place=True)
 
@@ -522,8 +523,9 @@ def run_ours(args):
                "steps": ks, "results_match_device": bool(ok),
                "pipelining": f"{len(groups)} groups of {E2E_GROUP} frames on 2 alternating streams, each group read "
                              "back while the next one runs",
-               "rgb": f"{rgb_h.numel() / 1e9:.2f} GB of pinned host RGB per step read in place by the colour "
-                      "kernel (only the pixels it needs cross the host link)"}
+               "inputs": f"{masks_h.numel() / 1e9:.2f} GB of pinned host masks per step read in full by the "
+                         f"packing kernel; {rgb_h.numel() / 1e9:.2f} GB of pinned host RGB read in place by the "
+                         "colour kernel (only the pixels it needs cross the host link)"}
 
     S = min(args.cpu_frames, F)
     cpu_sample = (masks[:S].cpu().numpy(), rgb[:S].cpu().numpy(), vps[:S])

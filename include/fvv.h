@@ -96,8 +96,14 @@ enum { FVV_OOB_STRICT = 0, FVV_OOB_ABSTAIN = 1 };
  *   pixel visited counts as one test (fvv_counts.tests_bisect). */
 enum { FVV_SURFACE_BISECT = 0, FVV_SURFACE_LAMBDA = 1 };
 
-/* fvv_colour / fvv_render_view: RGB read in place from mapped host memory. */
-#define FVV_RGB_MAPPED_HOST 2
+/* Input images in page-locked host memory that the device can address (for
+ * example a pinned torch tensor), read in place by the kernels over the host
+ * link, with no staging copy: a value of masks_on_device / rgb_on_device.
+ * Both ends of every image must lie in such memory
+ * (cudaPointerGetAttributes), else FVV_ERR_INVALID_ARG with nothing
+ * launched; the memory must stay valid until the work has run. */
+#define FVV_MAPPED_HOST 2
+#define FVV_RGB_MAPPED_HOST FVV_MAPPED_HOST
 
 /* Bits of fvv_counts.flags: which capacity a reconstruction exceeded. */
 enum {
@@ -200,7 +206,8 @@ fvv_status fvv_destroy_rig(fvv_rig *rig);
  * masks_on_device = 1 the pointers are device memory that must stay valid
  * until the work on `stream` has run; with 0 they are host memory (pinned
  * memory makes the copy asynchronous; pageable memory is copied before this
- * call returns) and the rig needs host_staging. */
+ * call returns) and the rig needs host_staging; with FVV_MAPPED_HOST the
+ * packing kernel reads them in place from mapped page-locked host memory. */
 fvv_status fvv_upload_silhouettes(fvv_rig *rig, int slot, const uint8_t *const *masks,
                                   int masks_on_device, void *stream);
 

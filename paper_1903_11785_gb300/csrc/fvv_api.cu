@@ -384,6 +384,26 @@ fvv_status fvv_destroy_rig(fvv_rig* rig) {
     return FVV_OK;
 }
 
+// The device address of a camera image of `bytes` bytes at host address p in
+// page-locked, device-mapped host memory (FVV_MAPPED_HOST), or NULL if
+// its first or last byte is not in such memory.
+static const uint8_t* mapped_host(const uint8_t* p, size_t bytes) {
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaPointerGetAttributes(&b, p + bytes - 1) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+        return nullptr;
+    const uint8_t* d = static_cast<const uint8_t*>(a.devicePointer);
+    if (static_cast<const uint8_t*>(b.devicePointer) != d + bytes - 1) return nullptr;
+    return d;
+}
+
 fvv_status fvv_upload_silhouettes(fvv_rig* rig, int slot, const uint8_t* const* masks, int masks_on_device,
                                   void* stream) {
     if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
@@ -395,7 +415,15 @@ fvv_status fvv_upload_silhouettes(fvv_rig* rig, int slot, const uint8_t* const* 
         if (!masks[n]) return fail(rig, FVV_ERR_INVALID_ARG, "a mask pointer is NULL");
         src[n] = masks[n];
     }
-    if (!masks_on_device) {
+    if (masks_on_device < 0 || masks_on_device > FVV_MAPPED_HOST)
+        return fail(rig, FVV_ERR_INVALID_ARG, "masks_on_device must be 0, 1 or FVV_MAPPED_HOST");
+    if (masks_on_device == FVV_MAPPED_HOST) {
+        for (int n = 0; n < rig->cams.n; ++n) {
+            const Cam& c = rig->cams.c[n];
+            src[n] = mapped_host(masks[n], (size_t)c.W * c.H);
+            if (!src[n]) return fail(rig, FVV_ERR_INVALID_ARG, "a mask is not in mapped page-locked host memory");
+        }
+    } else if (!masks_on_device) {
         if (!rig->host_staging) return fail(rig, FVV_ERR_INVALID_ARG, "host masks need a rig with host_staging");
         uint8_t* stage = slot_ptr<uint8_t>(rig->L, slot, rig->L.mask_stage);
         for (int n = 0; n < rig->cams.n; ++n) {
@@ -602,26 +630,6 @@ fvv_status fvv_autotune(fvv_rig* rig, const int* slots, int n_slots, void* strea
     return FVV_OK;
 }
 
-// The device address of a camera image of `bytes` bytes at host address p in
-// page-locked, device-mapped host memory (FVV_RGB_MAPPED_HOST), or NULL if
-// its first or last byte is not in such memory.
-static const uint8_t* mapped_host(const uint8_t* p, size_t bytes) {
-    cudaPointerAttributes a{}, b{};
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    if (cudaPointerGetAttributes(&b, p + bytes - 1) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
-        return nullptr;
-    const uint8_t* d = static_cast<const uint8_t*>(a.devicePointer);
-    if (static_cast<const uint8_t*>(b.devicePointer) != d + bytes - 1) return nullptr;
-    return d;
-}
-
 fvv_status fvv_colour(fvv_rig* rig, const int* slots, int n_slots, const uint8_t* const* rgb, int rgb_on_device,
                       const float* viewpoints, void* stream) {
     if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
@@ -629,8 +637,8 @@ fvv_status fvv_colour(fvv_rig* rig, const int* slots, int n_slots, const uint8_t
     fvv_status s = make_slot_list(rig, slots, n_slots, 2, sl);
     if (s != FVV_OK) return s;
     if (!rgb || !viewpoints) return fail(rig, FVV_ERR_INVALID_ARG, "rgb and viewpoints must not be NULL");
-    if (rgb_on_device < 0 || rgb_on_device > FVV_RGB_MAPPED_HOST)
-        return fail(rig, FVV_ERR_INVALID_ARG, "rgb_on_device must be 0, 1 or FVV_RGB_MAPPED_HOST");
+    if (rgb_on_device < 0 || rgb_on_device > FVV_MAPPED_HOST)
+        return fail(rig, FVV_ERR_INVALID_ARG, "rgb_on_device must be 0, 1 or FVV_MAPPED_HOST");
     if (!rgb_on_device && rig->host_staging != 1)
         return fail(rig, FVV_ERR_INVALID_ARG, "copied host RGB needs host_staging = 1");
     for (int i = 0; i < 3 * n_slots; ++i)
@@ -639,7 +647,7 @@ fvv_status fvv_colour(fvv_rig* rig, const int* slots, int n_slots, const uint8_t
     const int N = rig->cams.n;
     for (size_t i = 0; i < (size_t)n_slots * N; ++i)
         if (!rgb[i]) return fail(rig, FVV_ERR_INVALID_ARG, "an rgb pointer is NULL");
-    if (rgb_on_device == FVV_RGB_MAPPED_HOST)
+    if (rgb_on_device == FVV_MAPPED_HOST)
         for (int i = 0; i < n_slots; ++i)
             for (int n = 0; n < N; ++n) {
                 const Cam& c = rig->cams.c[n];
@@ -661,7 +669,7 @@ fvv_status fvv_colour(fvv_rig* rig, const int* slots, int n_slots, const uint8_t
                 const uint8_t* src = rgb[(size_t)i * N + n];
                 if (rgb_on_device == 1) {
                     cb.rgb[j][n] = src;
-                } else if (rgb_on_device == FVV_RGB_MAPPED_HOST) {
+                } else if (rgb_on_device == FVV_MAPPED_HOST) {
                     const Cam& c = rig->cams.c[n];
                     cb.rgb[j][n] = mapped_host(src, (size_t)3 * c.W * c.H);   // checked above
                 } else {
@@ -691,8 +699,8 @@ fvv_status fvv_render_view(fvv_rig* rig, int slot, const uint8_t* const* rgb, in
         return fail(rig, FVV_ERR_INVALID_ARG, "rgb, P, centre, key and out_rgb must not be NULL");
     if (width < 1 || height < 1 || width > 65535 || height > 65535)
         return fail(rig, FVV_ERR_INVALID_ARG, "view size must be 1..65535 pixels per side");
-    if (rgb_on_device < 0 || rgb_on_device > FVV_RGB_MAPPED_HOST)
-        return fail(rig, FVV_ERR_INVALID_ARG, "rgb_on_device must be 0, 1 or FVV_RGB_MAPPED_HOST");
+    if (rgb_on_device < 0 || rgb_on_device > FVV_MAPPED_HOST)
+        return fail(rig, FVV_ERR_INVALID_ARG, "rgb_on_device must be 0, 1 or FVV_MAPPED_HOST");
     if (!rgb_on_device && rig->host_staging != 1)
         return fail(rig, FVV_ERR_INVALID_ARG, "copied host RGB needs host_staging = 1");
     for (int i = 0; i < 12; ++i)
@@ -716,7 +724,7 @@ fvv_status fvv_render_view(fvv_rig* rig, int slot, const uint8_t* const* rgb, in
     for (int n = 0; n < N && e == cudaSuccess; ++n) {
         if (rgb_on_device == 1) {
             va.rgb[n] = rgb[n];
-        } else if (rgb_on_device == FVV_RGB_MAPPED_HOST) {
+        } else if (rgb_on_device == FVV_MAPPED_HOST) {
             const Cam& c = rig->cams.c[n];
             va.rgb[n] = mapped_host(rgb[n], (size_t)3 * c.W * c.H);
             if (!va.rgb[n]) return fail(rig, FVV_ERR_INVALID_ARG, "an rgb image is not in mapped page-locked host memory");

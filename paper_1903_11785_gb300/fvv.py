@@ -29,7 +29,8 @@ FVV_OK, FVV_ERR_INVALID_ARG, FVV_ERR_OUT_OF_MEMORY, FVV_ERR_CAPACITY, FVV_ERR_NO
     FVV_ERR_CUDA = range(7)
 FVV_OOB_STRICT, FVV_OOB_ABSTAIN = 0, 1
 FVV_SURFACE_BISECT, FVV_SURFACE_LAMBDA = 0, 1
-FVV_RGB_MAPPED_HOST = 2
+FVV_MAPPED_HOST = 2
+FVV_RGB_MAPPED_HOST = FVV_MAPPED_HOST
 FVV_MAX_CAMS, FVV_MAX_BATCH = 64, 256
 FVV_DEBUG_SIL_BITS, FVV_DEBUG_COARSE_BITS, FVV_DEBUG_LABELS, FVV_DEBUG_FINE_BITS, FVV_DEBUG_DEPTH = range(5)
 FLAG_NAMES = {1: "ROOTS", 2: "ROIS", 4: "FINE", 8: "VERTS", 16: "TRIS", 32: "LOOP"}
@@ -197,13 +198,14 @@ def fvv_destroy_rig(rig_ptr):
     _check(_lib.fvv_destroy_rig(rig_ptr))
 
 
-def fvv_upload_silhouettes(rig_ptr, slot, masks, stream=None):
+def fvv_upload_silhouettes(rig_ptr, slot, masks, stream=None, in_place=False):
     """masks: list of per-camera uint8 tensors (H,W) (or one (N,H,W) tensor),
-    all on the GPU or all in host memory."""
+    all on the GPU or all in host memory; in_place: pinned host tensors are
+    read in place by the packing kernel (FVV_MAPPED_HOST)."""
     ms = list(masks) if not torch.is_tensor(masks) else list(masks.unbind(0))
-    on_dev = int(ms[0].is_cuda)
+    on_dev = _rgb_mode(int(ms[0].is_cuda), ms, in_place)
     for m in ms:
-        assert m.dtype == torch.uint8 and m.is_contiguous() and int(m.is_cuda) == on_dev
+        assert m.dtype == torch.uint8 and m.is_contiguous() and m.is_cuda == ms[0].is_cuda
     _check(_lib.fvv_upload_silhouettes(rig_ptr, slot, _ptr_array([m.data_ptr() for m in ms]), on_dev,
                                        _stream(stream)), rig_ptr)
 
@@ -216,8 +218,8 @@ def fvv_reconstruct(rig_ptr, slots, stream=None):
 def _rgb_mode(on_dev, imgs, in_place):
     if on_dev or not in_place:
         return on_dev
-    assert all(t.is_pinned() for t in imgs), "in-place RGB needs pinned host tensors"
-    return FVV_RGB_MAPPED_HOST
+    assert all(t.is_pinned() for t in imgs), "reading in place needs pinned host tensors"
+    return FVV_MAPPED_HOST
 
 
 def fvv_colour(rig_ptr, slots, rgb, viewpoints, stream=None, in_place=False):
@@ -353,8 +355,8 @@ class Rig:
         except Exception:
             pass
 
-    def upload_silhouettes(self, slot, masks, stream=None):
-        fvv_upload_silhouettes(self.ptr, slot, masks, stream)
+    def upload_silhouettes(self, slot, masks, stream=None, in_place=False):
+        fvv_upload_silhouettes(self.ptr, slot, masks, stream, in_place)
 
     def reconstruct(self, slots, stream=None):
         fvv_reconstruct(self.ptr, list(slots), stream)

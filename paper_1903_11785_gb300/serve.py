@@ -7,9 +7,9 @@ sized at start-up so that all rigs together stay within a memory budget
 admitted when its rig has a free slot, otherwise it waits in that rig's
 queue.  On every pass the loop gathers the requests admitted since the last
 pass into one batch per rig and issues, on one of the rig's streams, the
-host-to-device copies and packing of their silhouettes, one fvv_reconstruct
-over the batch and one fvv_colour (which reads pinned RGB images in place,
-so a slot needs no RGB staging); batches of different rigs, and
+packing of their silhouettes, one fvv_reconstruct
+over the batch and one fvv_colour (pinned masks and RGB images are read in
+place by the kernels, so a slot needs no staging); batches of different rigs, and
 successive batches of one rig (on alternating streams, disjoint slots), run
 concurrently on the GPU.  A slot is freed when its batch's completion event
 has fired.  Latency is measured from a request's scheduled arrival to the
@@ -51,13 +51,20 @@ class RigPool:
 
 
 def _staging(pool) -> int:
-    """Host staging a rig's slots need: masks only when the pool's RGB is
-    pinned (read in place by the colour kernel), else masks and RGB."""
-    return 2 if _rgb_pinned(pool) else 1
+    """Host staging a rig's slots need: none when the pool's masks and RGB are
+    pinned (read in place by the kernels), masks only when only the RGB is,
+    else masks and RGB."""
+    if _rgb_pinned(pool):
+        return 0 if _masks_pinned(pool) else 2
+    return 1
 
 
 def _rgb_pinned(pool) -> bool:
     return all(t.is_pinned() for t in pool.rgb)
+
+
+def _masks_pinned(pool) -> bool:
+    return all(t.is_pinned() for t in pool.masks)
 
 
 def slot_bytes(scene_rig, staging: int = 1, **caps) -> int:
@@ -86,6 +93,7 @@ class _RigState:
     def __init__(self, pool: RigPool, n_slots: int, n_streams: int, caps: dict):
         self.pool = pool
         self.rgb_in_place = _rgb_pinned(pool)
+        self.masks_in_place = self.rgb_in_place and _masks_pinned(pool)
         self.rig = fvv.Rig(pool.scene_rig, max_slots=n_slots, host_staging=_staging(pool), **caps)
         self.free = list(range(n_slots))
         self.queue = []            # waiting requests
@@ -120,7 +128,7 @@ class Server:
         slots = [q.slot for q in reqs]
         with torch.cuda.stream(st):
             for q in reqs:
-                r.rig.upload_silhouettes(q.slot, r.pool.masks[q.frame], stream=st)
+                r.rig.upload_silhouettes(q.slot, r.pool.masks[q.frame], stream=st, in_place=r.masks_in_place)
             r.rig.reconstruct(slots, stream=st)
             rgb = [r.pool.rgb[q.frame] for q in reqs]
             r.rig.colour(slots, rgb, np.stack([r.pool.viewpoints[q.frame] for q in reqs]), stream=st,

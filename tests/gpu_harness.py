@@ -12,7 +12,7 @@ def unpack_rows(words: np.ndarray, shape_rows, width):
     return b.reshape(*shape_rows, -1)[..., :width]
 
 
-def run_gpu(rig, frames, host=False, caps=None, slots=None, batch=True, rgb_in_place=False):
+def run_gpu(rig, frames, host=False, caps=None, slots=None, batch=True, rgb_in_place=False, masks_in_place=False):
     """Upload, reconstruct (all slots in one call when batch) and colour.
     Returns one dict of numpy outputs per frame."""
     from paper_1903_11785_gb300 import fvv
@@ -22,8 +22,8 @@ def run_gpu(rig, frames, host=False, caps=None, slots=None, batch=True, rgb_in_p
     r = fvv.Rig(rig, max_slots=max(slots) + 1, host_staging=int(host), **caps)
     try:
         for s, fr in zip(slots, frames):
-            m = fr.masks.pin_memory() if host else fr.masks.cuda()
-            r.upload_silhouettes(s, m)
+            m = fr.masks.pin_memory() if (host or masks_in_place) else fr.masks.cuda()
+            r.upload_silhouettes(s, m, in_place=masks_in_place)
         if batch:
             r.reconstruct(slots)
         else:

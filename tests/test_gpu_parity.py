@@ -64,6 +64,21 @@ def test_colour_reads_pinned_host_rgb_in_place():
         r.close()
 
 
+def test_masks_read_in_place_including_ragged_rows():
+    """FVV_MAPPED_HOST masks: the packing kernel reads pinned host images in
+    place, on 640-pixel rows (16-byte loads) and on 630-pixel rows (byte
+    loads, rows not 16-byte aligned)."""
+    rig = make_rig("tiny")
+    fr = make_frame("tiny", 3, rig=rig)[1]
+    compare(rig, fr, run_gpu(rig, [fr], masks_in_place=True, rgb_in_place=True)[0])
+    n, r, h = 6, 6.0, 3.0
+    cs = [(r * math.cos(2 * math.pi * k / n), r * math.sin(2 * math.pi * k / n), h) for k in range(n)]
+    rig = _make_rig("ragged", cs, [(0, 0, 0.9)] * n, 480.0, 630, 349, _gen("ragged/rig"),
+                    (-2.0, -2.0, 0.0), (2.0, 2.0, 2.5), 0.05, 0.01, 6)
+    fr = render(rig, scene_objects("tiny", 3), index=3, config_tag="ragged")
+    compare(rig, fr, run_gpu(rig, [fr], masks_in_place=True)[0])
+
+
 def test_batched_slots_each_bit_exact():
     """Three frames in one reconstruct/colour call, slots listed out of order."""
     rig = make_rig("tiny")
