@@ -56,8 +56,11 @@ struct Grid {
     uint32_t max_verts, max_tris;
 };
 
-// Fine-carve tiles: kTileX x kTileY x kTileZ interior samples, one per lane.
-constexpr int kTileX = 4, kTileY = 2, kTileZ = 4;
+// Fine-carve tiles: kTileX x kTileY x kTileZ interior samples, classified
+// per camera once and tested in kSubTiles sub-tiles of 4 x kSubY x kSubZ
+// samples, one per lane.
+constexpr int kTileX = 4, kTileY = 4, kTileZ = 8;
+constexpr int kSubY = 2, kSubZ = 4, kSubTiles = (kTileY / kSubY) * (kTileZ / kSubZ);
 
 // Per-slot device bookkeeping (zeroed at the start of each reconstruction).
 struct SlotInfo {

@@ -198,9 +198,10 @@ __device__ __forceinline__ void classify_tile_camera(const SmemCam& c, const uin
 // and fdim+1), rows of ceil((fdim_x+2)/32) words, cleared beforehand; only
 // occupied samples are written, by OR into their word.
 //
-// A warp takes a tile of 4 x 2 x 4 interior samples (x, y, z; one per lane)
-// and first decides, per camera, whether all of the tile's samples vote
-// foreground or all vote background there (classify_tile_camera).  A
+// A warp takes a tile of 4 x 4 x 8 interior samples (x, y, z) and first
+// decides, per camera, whether all of the tile's samples vote foreground or
+// all vote background there (classify_tile_camera); then it takes the tile's
+// samples 4 x 2 x 4 at a time, one per lane.  A
 // sample's first background camera in index order is then either an
 // undecided camera before the tile's first all-background camera, where it
 // is tested, or that camera; so each sample projects and looks its pixel up
@@ -261,51 +262,57 @@ __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, co
             fgm |= (uint64_t)even_bits(__ballot_sync(kFull, fg)) << cg;
             bgm |= (uint64_t)even_bits(__ballot_sync(kFull, bg)) << cg;
         }
-        // this lane's sample
-        const int x = x0 + xi, y = y0 + yi, z = z0 + zi;
-        const bool act = x < fx && y < fy && z < fz;
-        const float X = fadd(fo0, fmul(fadd((float)x, 0.5f), g.sf));
-        const float Y = fadd(fo1, fmul(fadd((float)y, 0.5f), g.sf));
-        const float Z = fadd(fo2, fmul(fadd((float)z, 0.5f), g.sf));
-        // In camera order: the first all-background camera nb stops every
-        // sample still alive there; before it, all-foreground cameras pass
-        // every sample and only the undecided ones are tested, per lane.
+        // the tile's samples, one sub-tile of 4 x 2 x 4 (one per lane) at a time
         const int nb = bgm ? __ffsll((long long)bgm) - 1 : ncam;
         const uint64_t before = nb >= 64 ? ~0ull : (1ull << nb) - 1ull;
-        uint64_t todo = ~(fgm | bgm) & before;
-        bool alive = act, voted = !ABSTAIN || (fgm & before) != 0ull;
-        int stop = -1;
-        while (todo && __any_sync(kFull, alive)) {
-            const int n = __ffsll((long long)todo) - 1;
-            todo &= todo - 1ull;
-            if (alive) {
-                bool in;
-                const uint32_t bit = cam_bit(sc[n], sil, X, Y, Z, in);
-                if (ABSTAIN ? (in && !bit) : !bit) {
-                    alive = false;
-                    stop = n;
+#pragma unroll 1
+        for (int sub = 0; sub < kSubTiles; ++sub) {
+            const int sy0 = y0 + (sub & 1) * kSubY, sz0 = z0 + (sub >> 1) * kSubZ;
+            if (sy0 >= fy || sz0 >= fz) continue;          // the same in every lane
+            // this lane's sample
+            const int x = x0 + xi, y = sy0 + yi, z = sz0 + zi;
+            const bool act = x < fx && y < fy && z < fz;
+            const float X = fadd(fo0, fmul(fadd((float)x, 0.5f), g.sf));
+            const float Y = fadd(fo1, fmul(fadd((float)y, 0.5f), g.sf));
+            const float Z = fadd(fo2, fmul(fadd((float)z, 0.5f), g.sf));
+            // In camera order: the first all-background camera nb stops every
+            // sample still alive there; before it, all-foreground cameras pass
+            // every sample and only the undecided ones are tested, per lane.
+            uint64_t todo = ~(fgm | bgm) & before;
+            bool alive = act, voted = !ABSTAIN || (fgm & before) != 0ull;
+            int stop = -1;
+            while (todo && __any_sync(kFull, alive)) {
+                const int n = __ffsll((long long)todo) - 1;
+                todo &= todo - 1ull;
+                if (alive) {
+                    bool in;
+                    const uint32_t bit = cam_bit(sc[n], sil, X, Y, Z, in);
+                    if (ABSTAIN ? (in && !bit) : !bit) {
+                        alive = false;
+                        stop = n;
+                    }
+                    voted |= bit != 0u;
                 }
-                voted |= bit != 0u;
             }
-        }
-        if (act) tests += stop >= 0 ? (unsigned)(stop + 1) : (nb < ncam ? (unsigned)(nb + 1) : (unsigned)ncam);
-        alive = alive && nb >= ncam;
-        const bool on = alive && voted;
-        // OR the occupied samples into their words: the four lanes of one
-        // (y, z) row span at most two words
-        if (__any_sync(kFull, on)) {
-            const uint32_t word = woff + ((uint32_t)(z + 1) * (uint32_t)(fy + 2) + (uint32_t)(y + 1)) * (uint32_t)nxw +
-                                  (uint32_t)((x + 1) >> 5);
-            const uint32_t first = __shfl_sync(kFull, word, lane & ~3);
-            const uint32_t bit = on ? 1u << ((x + 1) & 31) : 0u;
-            uint32_t blo = word == first ? bit : 0u, bhi = word == first ? 0u : bit;
-            blo |= __shfl_xor_sync(kFull, blo, 1);
-            bhi |= __shfl_xor_sync(kFull, bhi, 1);
-            blo |= __shfl_xor_sync(kFull, blo, 2);
-            bhi |= __shfl_xor_sync(kFull, bhi, 2);
-            if (xi == 0) {
-                if (blo) atomicOr(fine + first, blo);
-                if (bhi) atomicOr(fine + first + 1, bhi);
+            if (act) tests += stop >= 0 ? (unsigned)(stop + 1) : (nb < ncam ? (unsigned)(nb + 1) : (unsigned)ncam);
+            alive = alive && nb >= ncam;
+            const bool on = alive && voted;
+            // OR the occupied samples into their words: the four lanes of one
+            // (y, z) row span at most two words
+            if (__any_sync(kFull, on)) {
+                const uint32_t word = woff + ((uint32_t)(z + 1) * (uint32_t)(fy + 2) + (uint32_t)(y + 1)) * (uint32_t)nxw +
+                                      (uint32_t)((x + 1) >> 5);
+                const uint32_t first = __shfl_sync(kFull, word, lane & ~3);
+                const uint32_t bit = on ? 1u << ((x + 1) & 31) : 0u;
+                uint32_t blo = word == first ? bit : 0u, bhi = word == first ? 0u : bit;
+                blo |= __shfl_xor_sync(kFull, blo, 1);
+                bhi |= __shfl_xor_sync(kFull, bhi, 1);
+                blo |= __shfl_xor_sync(kFull, blo, 2);
+                bhi |= __shfl_xor_sync(kFull, bhi, 2);
+                if (xi == 0) {
+                    if (blo) atomicOr(fine + first, blo);
+                    if (bhi) atomicOr(fine + first + 1, bhi);
+                }
             }
         }
     }
