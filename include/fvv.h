@@ -172,6 +172,10 @@ typedef struct {
     long long n_verts, n_tris;
     long long tests_coarse, tests_fine, tests_bisect; /* camera tests, with the
                               per-point early exit at the first background vote */
+    long long lookups_fine, lookups_bisect; /* silhouette words the fine-hull and
+                              surface kernels actually read: they settle most
+                              tests for a whole tile or grid edge at once (the
+                              coarse hull reads one word per test) */
 } fvv_counts;
 
 /* Per-slot debug views for tests (fvv_get_debug). */

@@ -793,6 +793,8 @@ fvv_status fvv_get_counts(fvv_rig* rig, int slot, fvv_counts* out, void* stream)
     out->tests_coarse = (long long)info.tests_coarse;
     out->tests_fine = (long long)info.tests_fine;
     out->tests_bisect = (long long)info.tests_bisect;
+    out->lookups_fine = (long long)info.look_fine;
+    out->lookups_bisect = (long long)info.look_bisect;
     const unsigned cap = FVV_FLAG_ROOTS | FVV_FLAG_ROIS | FVV_FLAG_FINE | FVV_FLAG_VERTS | FVV_FLAG_TRIS | FVV_FLAG_LOOP;
     if (info.flags & cap) return fail(rig, FVV_ERR_CAPACITY, "a capacity was exceeded (see flags)");
     return FVV_OK;

@@ -74,6 +74,7 @@ struct SlotInfo {
     uint32_t n_verts, n_tris;
     uint32_t n_on;
     unsigned long long tests_coarse, tests_fine, tests_bisect;
+    unsigned long long look_fine, look_bisect;   // silhouette words read
 };
 
 // Device ROI record (one per kept component).

@@ -135,7 +135,7 @@ __device__ __forceinline__ uint32_t even_bits(uint32_t x) {
 template <bool ABSTAIN>
 __device__ __forceinline__ void classify_tile_camera(const SmemCam& c, const uint32_t* __restrict__ sil,
                                                      const float* cx, const float* cy, const float* cz, int half,
-                                                     bool& fg_all, bool& bg_all) {
+                                                     bool& fg_all, bool& bg_all, uint32_t& reads) {
     // the two lanes of a camera take the same path through this function, so
     // they exchange values among themselves only
     const unsigned pm = 3u << ((threadIdx.x & 31u) & ~1u);
@@ -185,6 +185,7 @@ __device__ __forceinline__ void classify_tile_camera(const SmemCam& c, const uin
             all &= va == m0 && vb == m1;
             any |= (va | vb) != 0u;
         }
+        reads += (unsigned)(w1 - w0 + 1);
     }
     const int all_other = __shfl_xor_sync(pm, (int)all, 1), any_other = __shfl_xor_sync(pm, (int)any, 1);
     all = all && all_other != 0;
@@ -212,7 +213,7 @@ template <int NC, bool ABSTAIN>
 __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, const SmemCam* sc, int ncam,
                                            uint32_t ntiles, int nrois, const DRoi* rois,
                                            const uint32_t* __restrict__ sil, uint32_t* fine,
-                                           unsigned long long& tests) {
+                                           uint32_t& tests, uint32_t& reads) {
     const int lane = threadIdx.x & 31, half = lane & 1;
     const int xi = lane & 3, yi = (lane >> 2) & 1, zi = lane >> 3;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -256,7 +257,9 @@ __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, co
         for (int cg = 0; cg < ncam; cg += 16) {
             const int cam = cg + (lane >> 1);
             bool fg, bg;
-            classify_tile_camera<ABSTAIN>(sc[min(cam, ncam - 1)], sil, cx, cy, cz, half, fg, bg);
+            uint32_t r = 0;
+            classify_tile_camera<ABSTAIN>(sc[min(cam, ncam - 1)], sil, cx, cy, cz, half, fg, bg, r);
+            if (cam < ncam) reads += r;
             fg = fg && cam < ncam;
             bg = bg && cam < ncam;
             fgm |= (uint64_t)even_bits(__ballot_sync(kFull, fg)) << cg;
@@ -287,6 +290,7 @@ __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, co
                 if (alive) {
                     bool in;
                     const uint32_t bit = cam_bit(sc[n], sil, X, Y, Z, in);
+                    reads += in ? 1u : 0u;
                     if (ABSTAIN ? (in && !bit) : !bit) {
                         alive = false;
                         stop = n;
@@ -335,11 +339,16 @@ __global__ void __launch_bounds__(256) k_fine_carve(const __grid_constant__ CamS
     const DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
     const uint32_t* __restrict__ sil = slot_ptr<uint32_t>(L, slot, L.sil);
     uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
-    unsigned long long tests = 0;
-    if (cams.oob == FVV_OOB_ABSTAIN) fine_tiles<NC, true>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tests);
-    else fine_tiles<NC, false>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tests);
-    const unsigned long long t = block_sum<unsigned long long>(tests, sh_t);
+    // per-lane counts stay below 2^30 (at most 2^24 tiles of 64 tests each)
+    uint32_t tests = 0, reads = 0;
+    if (cams.oob == FVV_OOB_ABSTAIN)
+        fine_tiles<NC, true>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tests, reads);
+    else
+        fine_tiles<NC, false>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tests, reads);
+    const unsigned long long t = block_sum<unsigned long long>((unsigned long long)tests, sh_t);
+    const unsigned long long rd = block_sum<unsigned long long>((unsigned long long)reads, sh_t);
     if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_fine, t);
+    if (threadIdx.x == 0 && rd) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->look_fine, rd);
 }
 
 // Test hook: the pixel each point falls in for one camera (-1, -1 if none).

@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kChunk) k_mc_vertices(const __grid_constant__ 
 // segment_margins on the host), are all inside the image and set.  Boxes
 // wider than 32 or taller than 8 pixels are not scanned (false).
 __device__ __forceinline__ bool segment_all_fg(const Cam& c, const uint32_t* __restrict__ sil, const float* a,
-                                               const float* b) {
+                                               const float* b, unsigned long long& reads) {
     if (!(c.seg_du >= 0.0f)) return false;
     float xa, ya, wa, xb, yb, wb;
     project(c.P, a[0], a[1], a[2], xa, ya, wa);
@@ -363,6 +363,7 @@ __device__ __forceinline__ bool segment_all_fg(const Cam& c, const uint32_t* __r
             all &= (__ldg(row + w1) & m1) == m1;
         }
     }
+    reads += (unsigned)((y1 - y0 + 1) * (w1 - w0 + 1));
     return all;
 }
 
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet c
     const uint32_t* __restrict__ sil = slot_ptr<uint32_t>(L, slot, L.sil);
     const uint64_t* vrec = slot_ptr<uint64_t>(L, slot, L.vrec);
     float* verts = slot_ptr<float>(L, slot, L.verts);
-    unsigned long long tests = 0;
+    unsigned long long tests = 0, reads = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
         const uint64_t rec = vrec[i];
         const int k = (int)(rec & 0x3FFFu), axis = (int)(rec >> 14 & 3u), s0 = (int)(rec >> 16 & 1u);
@@ -415,13 +416,13 @@ __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet c
             if constexpr (NC > 0) {
 #pragma unroll
                 for (int n = 0; n < NC; ++n) {
-                    const bool fg = segment_all_fg(cams.c[n], sil, a, b);
+                    const bool fg = segment_all_fg(cams.c[n], sil, a, b, reads);
                     undecided |= fg ? 0ull : 1ull << n;
                     seen_fg |= fg;
                 }
             } else {
                 for (int n = 0; n < cams.n; ++n) {
-                    const bool fg = segment_all_fg(cams.c[n], sil, a, b);
+                    const bool fg = segment_all_fg(cams.c[n], sil, a, b, reads);
                     undecided |= fg ? 0ull : 1ull << n;
                     seen_fg |= fg;
                 }
@@ -444,6 +445,7 @@ __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet c
                 const bool in = wp > 0.0f && (unsigned)px < (unsigned)c.W && (unsigned)py < (unsigned)c.H;
                 const uint32_t word =
                     in ? __ldg(sil + c.bit_off + (unsigned)py * (unsigned)c.Wq + ((unsigned)px >> 5)) : 0u;
+                reads += in ? 1u : 0u;
                 const bool bit = (word >> (px & 31)) & 1u;
                 if (abstain ? (in && !bit) : !bit) {
                     stop = n;
@@ -463,7 +465,9 @@ __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet c
         for (int d = 0; d < 3; ++d) verts[3 * (size_t)i + d] = fmul(fadd(a[d], b[d]), 0.5f);
     }
     const unsigned long long t = block_sum<unsigned long long>(tests, sh_t);
+    const unsigned long long rd = block_sum<unsigned long long>(reads, sh_t);
     if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_bisect, t);
+    if (threadIdx.x == 0 && rd) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->look_bisect, rd);
 }
 
 // Sec. II-C, Eq. (2), camera c, for the edge from the occupied end a to the
@@ -561,8 +565,12 @@ __global__ void __launch_bounds__(256) k_lambda(const __grid_constant__ CamSet c
 #pragma unroll
         for (int d = 0; d < 3; ++d) verts[3 * (size_t)i + d] = fadd(a[d], fmul(lam, fsub(b[d], a[d])));
     }
+    // every pixel visited is one silhouette word read
     const unsigned long long t = block_sum<unsigned long long>(tests, sh_t);
-    if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_bisect, t);
+    if (threadIdx.x == 0 && t) {
+        atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_bisect, t);
+        atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->look_bisect, t);
+    }
 }
 
 // Sec. II-C: the triangles, one per thread from the triangle records: the

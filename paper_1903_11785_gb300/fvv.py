@@ -69,7 +69,7 @@ class Counts(C.Structure):
     _fields_ = [("flags", C.c_uint), ("n_components", C.c_int), ("n_rois", C.c_int), ("pad_", C.c_int),
                 ("n_coarse_on", C.c_longlong), ("n_fine_words", C.c_longlong), ("n_verts", C.c_longlong),
                 ("n_tris", C.c_longlong), ("tests_coarse", C.c_longlong), ("tests_fine", C.c_longlong),
-                ("tests_bisect", C.c_longlong)]
+                ("tests_bisect", C.c_longlong), ("lookups_fine", C.c_longlong), ("lookups_bisect", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
