@@ -166,6 +166,22 @@ def test_abstain_policy_with_bisection():
     assert ref.tests_bisect > 0
 
 
+@pytest.mark.parametrize("n_cams", [5, 20])
+def test_generic_and_large_camera_counts(n_cams):
+    """5 cameras (no unrolled instantiation: the generic camera loops) and 20
+    cameras (two camera groups in the fine hull's per-tile decisions), with
+    bisection and with the paper's walk."""
+    r, h = 6.0, 3.0
+    cs = [(r * math.cos(2 * math.pi * k / n_cams), r * math.sin(2 * math.pi * k / n_cams), h + 0.3 * (k % 3))
+          for k in range(n_cams)]
+    rig = _make_rig(f"ring{n_cams}", cs, [(0, 0, 0.9)] * n_cams, 420.0, 480, 320, _gen(f"ring{n_cams}/rig"),
+                    (-2.0, -2.0, 0.0), (2.0, 2.0, 2.5), 0.05, 0.01, 7)
+    fr = render(rig, scene_objects("tiny", 7), index=7, config_tag=f"ring{n_cams}")
+    compare(rig, fr, run_gpu(rig, [fr])[0])
+    rig.surface_rule = 1
+    compare(rig, fr, run_gpu(rig, [fr])[0])
+
+
 def test_ragged_image_width():
     """Images whose width is not a multiple of 32 (scalar packing path, partial
     last word of every silhouette row)."""
