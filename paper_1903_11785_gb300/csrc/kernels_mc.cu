@@ -337,17 +337,18 @@ __global__ void __launch_bounds__(kChunk) k_mc_vertices(const __grid_constant__ 
 // approximate image positions, widened by the camera's margins (see
 // segment_margins on the host), are all inside the image and set.  Boxes
 // wider than 32 or taller than 8 pixels are not scanned (false).
-__device__ __forceinline__ bool segment_all_fg(const Cam& c, const uint32_t* __restrict__ sil, const float* a,
+template <class CamT>
+__device__ __forceinline__ bool segment_all_fg(const CamT& c, const uint32_t* __restrict__ sil, const float* a,
                                                const float* b, unsigned long long& reads) {
-    if (!(c.seg_du >= 0.0f)) return false;
+    if (!(c.du >= 0.0f)) return false;
     float xa, ya, wa, xb, yb, wb;
     project(c.P, a[0], a[1], a[2], xa, ya, wa);
     project(c.P, b[0], b[1], b[2], xb, yb, wb);
     if (!(wa > 0.0f && wb > 0.0f)) return false;
     const float ra = rcp_approx(wa), rb = rcp_approx(wb);
     const float ua = fmul(xa, ra), va = fmul(ya, ra), ub = fmul(xb, rb), vb = fmul(yb, rb);
-    const float u0 = fsub(fminf(ua, ub), c.seg_du), u1 = fadd(fmaxf(ua, ub), c.seg_du);
-    const float v0 = fsub(fminf(va, vb), c.seg_dv), v1 = fadd(fmaxf(va, vb), c.seg_dv);
+    const float u0 = fsub(fminf(ua, ub), c.du), u1 = fadd(fmaxf(ua, ub), c.du);
+    const float v0 = fsub(fminf(va, vb), c.dv), v1 = fadd(fmaxf(va, vb), c.dv);
     if (!(u0 >= 0.0f && v0 >= 0.0f && u1 < c.Wf && v1 < c.Hf)) return false;
     const int x0 = (int)u0, x1 = (int)u1, y0 = (int)v0, y1 = (int)v1;   // truncation = floor here
     if (x1 - x0 > 31 || y1 - y0 > 7) return false;
@@ -413,19 +414,14 @@ __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet c
         uint64_t undecided = 0;
         bool seen_fg = false;          // ABSTAIN: some camera votes foreground everywhere
         if (g.steps > 0) {
-            if constexpr (NC > 0) {
-#pragma unroll
-                for (int n = 0; n < NC; ++n) {
-                    const bool fg = segment_all_fg(cams.c[n], sil, a, b, reads);
-                    undecided |= fg ? 0ull : 1ull << n;
-                    seen_fg |= fg;
-                }
-            } else {
-                for (int n = 0; n < cams.n; ++n) {
-                    const bool fg = segment_all_fg(cams.c[n], sil, a, b, reads);
-                    undecided |= fg ? 0ull : 1ull << n;
-                    seen_fg |= fg;
-                }
+            // one compact loop over the cameras' fields in shared memory (the
+            // camera is the same in every lane): 16 inlined copies of this
+            // check cost more in instruction-cache misses than the loads
+#pragma unroll 1
+            for (int n = 0; n < ncam; ++n) {
+                const bool fg = segment_all_fg(sc[n], sil, a, b, reads);
+                undecided |= fg ? 0ull : 1ull << n;
+                seen_fg |= fg;
             }
         }
         for (int it = 0; it < g.steps; ++it) {
