@@ -77,6 +77,28 @@ def parse_args():
     return ap.parse_args()
 
 
+def first_frame(rank, frames_per_rank):
+    """Replicas only: rank r reconstructs its own consecutive frames, disjoint
+    from every other rank's (frames are independent; no data-path collective)."""
+    return rank * frames_per_rank
+
+
+def max_over_ranks(x, world, device):
+    """The slowest rank's time (the job's time); x itself on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, frames_per_rank, seconds):
+    """Whole-job throughput: the frames all ranks processed over the job's time."""
+    return world * frames_per_rank / seconds
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -347,7 +369,7 @@ def run_ours(args):
     from paper_1903_11785_gb300 import fvv
 
     F = args.frames
-    rig, masks, rgb, vps = make_batch(F, rank * F, "cuda")
+    rig, masks, rgb, vps = make_batch(F, first_frame(rank, F), "cuda")
     mask_bytes, rgb_bytes = masks.numel(), rgb.numel()
     N, H, W = masks.shape[1:]
     r = fvv.Rig(rig, max_slots=F, host_staging=0 if args.no_e2e else 1)
@@ -396,11 +418,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1) / args.steps
     stages = r.timing()
     r.set_timing(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * F / (ms / 1000.0)
+    ms = max_over_ranks(ms, world, "cuda")
+    value = job_rate(world, F, ms / 1000.0)
 
     # ---- plain path: one frame per call (slot 0, reconstruction replayed as a
     # CUDA graph on a side stream), per-frame latency by events
@@ -519,11 +538,8 @@ def run_ours(args):
         for _ in range(ks):
             e2e_step()
         dt = (time.perf_counter() - t0) / ks
-        if world > 1:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * F / dt, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        dt = max_over_ranks(dt, world, "cuda")
+        e2e = {"value": job_rate(world, F, dt), "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": ks, "results_match_device": bool(ok),
                "pipelining": f"{len(groups)} groups of {E2E_GROUP} frames on 2 alternating streams, each group read "
                              "back while the next one runs",
