@@ -51,7 +51,7 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 1e12
 # of a 4-frame launch of the current kernels (profiles/k_fine_carve_volleyball_batch4.md,
 # profiles/hull_and_depth_kernels_volleyball_batch4.md), scaled to a launch by
 # its frame count.  None for a kernel changed since that capture.
-DRAM_BYTES_PER_FRAME = {"fine": 7.212544e6 / 4, "bisect": None, "coarse": None}
+DRAM_BYTES_PER_FRAME = {"fine": 7.212544e6 / 4, "bisect": (17.208832e6 + 3584) / 4, "coarse": None}
 
 
 def parse_args():
