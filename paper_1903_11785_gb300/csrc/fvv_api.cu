@@ -240,6 +240,7 @@ fvv_status make_plan(const fvv_rig_desc* d, const fvv_recon_params* p, Plan& pl,
     take(L.vrgb, (size_t)mv * 3);
     take(L.vcam, (size_t)mv * 4);
     take(L.depth, align_up(pix * 4));
+    take(L.dbox, (size_t)FVV_MAX_CAMS * 4 * sizeof(int32_t));
     if (d->host_staging < 0 || d->host_staging > 2) { err = "host_staging must be 0, 1 or 2"; return FVV_ERR_INVALID_ARG; }
     if (d->host_staging) take(L.mask_stage, pix);
     if (d->host_staging == 1) take(L.rgb_stage, pix * 3);
@@ -361,10 +362,14 @@ fvv_status fvv_create_rig(const fvv_rig_desc* desc, const fvv_recon_params* para
     build_mc_table(ntri.data(), edges.data());
     e = cudaMemcpy(rig->mc_ntri, ntri.data(), ntri.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(rig->mc_edges, edges.data(), edges.size(), cudaMemcpyHostToDevice);
+    // every depth image starts empty; each depth stage then clears only the
+    // box its slot's previous z-buffer wrote
+    if (e == cudaSuccess) e = launch_init_depth(rig->cams, rig->L, rig->max_slots, rig->sms, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         if (rig->own_arena) cudaFree(rig->arena);
         delete rig;
-        return cuda_fail(nullptr, e, "uploading the MC table");
+        return cuda_fail(nullptr, e, "initialising the rig");
     }
     *out = rig;
     return FVV_OK;

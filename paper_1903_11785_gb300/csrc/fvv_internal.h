@@ -114,6 +114,7 @@ struct Layout {
     size_t vrgb;                // uint8 x3, max_verts
     size_t vcam;                // int32, max_verts
     size_t depth;               // uint32 per pixel of all cameras
+    size_t dbox;                // int32 x4 per camera: box of the depth pixels the last z-buffer wrote
     size_t mask_stage;          // uint8 per pixel (host uploads), or 0
     size_t rgb_stage;           // uint8 x3 per pixel (host uploads), or 0
 };
@@ -184,6 +185,9 @@ cudaError_t launch_bisect(const CamSet& cams, const Grid& g, const Layout& L, co
                           const Tuning& tu, cudaStream_t st);
 cudaError_t launch_mc_triangles(const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc, int sms,
                                 const Tuning& tu, cudaStream_t st);
+// Depth images of every slot to empty and their written boxes to none (once,
+// when a rig is created).
+cudaError_t launch_init_depth(const CamSet& cams, const Layout& L, int n_slots, int sms, cudaStream_t st);
 cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
                          int sms, size_t depth_bytes, const Tuning& tu, cudaStream_t st);
 // Colour-call arguments of up to kColourBatch slots, passed by value as a

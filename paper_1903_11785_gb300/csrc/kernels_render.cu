@@ -10,13 +10,88 @@
 namespace fvv {
 namespace {
 
-__global__ void __launch_bounds__(256) k_clear_depth(const __grid_constant__ Layout L,
-                                                     const __grid_constant__ SlotList sl, size_t n16) {
-    const int slot = sl.s[blockIdx.y];
+// The depth images only ever hold values inside each camera's box (x0, x1,
+// y0, y1, none when x1 < x0), which contains every pixel the slot's last
+// z-buffer could write: a depth stage clears the previous box, sets the box
+// for this frame (k_depth_box) and runs the z-buffer, so every pixel outside
+// it is empty (+infinity) without clearing the whole image each frame.
+__global__ void __launch_bounds__(256) k_init_depth(const __grid_constant__ Layout L, size_t n16,
+                                                    int n_cams) {
+    const int slot = blockIdx.y;
     uint4* d = slot_ptr<uint4>(L, slot, L.depth);
     const uint4 v = make_uint4(kEmptyDepth, kEmptyDepth, kEmptyDepth, kEmptyDepth);
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
-        __stcs(d + i, v);
+        d[i] = v;
+    if (blockIdx.x == 0 && threadIdx.x < (unsigned)n_cams) {
+        int4* box = slot_ptr<int4>(L, slot, L.dbox);
+        box[threadIdx.x] = make_int4(INT_MAX, -1, INT_MAX, -1);
+    }
+}
+
+// Clear each camera's written box (grid: blocks, cameras, slots).
+__global__ void __launch_bounds__(256) k_clear_depth(const __grid_constant__ CamSet cams,
+                                                     const __grid_constant__ Layout L,
+                                                     const __grid_constant__ SlotList sl) {
+    const int slot = sl.s[blockIdx.z];
+    const Cam& c = cams.c[blockIdx.y];
+    const int4 b = slot_ptr<int4>(L, slot, L.dbox)[blockIdx.y];
+    if (b.y < b.x || b.w < b.z) return;
+    uint32_t* D = slot_ptr<uint32_t>(L, slot, L.depth) + c.pix_off;
+    for (int y = b.z + (int)blockIdx.x; y <= b.w; y += (int)gridDim.x) {
+        uint32_t* row = D + (size_t)y * (unsigned)c.W;
+        for (int x = b.x + (int)threadIdx.x; x <= b.y; x += (int)blockDim.x) __stcs(row + x, kEmptyDepth);
+    }
+}
+
+// The box each camera's z-buffer can write this frame (after k_clear_depth,
+// before k_zbuffer): every mesh vertex lies in its ROI's fine grid box grown
+// by one fine voxel (padding samples and bisection points), so every covered
+// pixel centre lies in the convex hull of the projections of that box's
+// eight corners; the union over the ROIs, widened by two pixels and clamped
+// to the image, or the whole image if a corner is not in front of the
+// camera.  One block per slot, a thread per (camera, ROI).
+__global__ void k_depth_box(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
+                            const __grid_constant__ Layout L, const __grid_constant__ SlotList sl) {
+    const int slot = sl.s[blockIdx.x];
+    int4* box = slot_ptr<int4>(L, slot, L.dbox);
+    for (int n = threadIdx.x; n < cams.n; n += blockDim.x) box[n] = make_int4(INT_MAX, -1, INT_MAX, -1);
+    __syncthreads();
+    const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const int nrois = info->n_words ? info->n_rois : 0;
+    const DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
+    for (int i = threadIdx.x; i < cams.n * nrois; i += blockDim.x) {
+        const int n = i / nrois, k = i - n * nrois;
+        const Cam& c = cams.c[n];
+        const DRoi& r = rois[k];
+        float lo[3], hi[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = r.fo[a] - g.sf;
+            hi[a] = r.fo[a] + (float)(r.fdim[a] + 1) * g.sf;
+        }
+        float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
+        bool front = true;
+        for (int q = 0; q < 8; ++q) {
+            float xh, yh, wh;
+            project(c.P, (q & 1) ? hi[0] : lo[0], (q & 2) ? hi[1] : lo[1], (q & 4) ? hi[2] : lo[2], xh, yh, wh);
+            front &= wh > 0.0f;
+            const float u = __fdiv_rn(xh, wh), v = __fdiv_rn(yh, wh);
+            umin = fminf(umin, u); umax = fmaxf(umax, u);
+            vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
+        }
+        int x0 = 0, x1 = c.W - 1, y0 = 0, y1 = c.H - 1;
+        if (front && umin > -1.0e6f && umax < 1.0e6f && vmin > -1.0e6f && vmax < 1.0e6f) {
+            x0 = max(0, (int)floorf(umin) - 2);
+            x1 = min(c.W - 1, (int)floorf(umax) + 2);
+            y0 = max(0, (int)floorf(vmin) - 2);
+            y1 = min(c.H - 1, (int)floorf(vmax) + 2);
+        }
+        if (x0 > x1 || y0 > y1) continue;
+        int* b = reinterpret_cast<int*>(box + n);
+        atomicMin(b + 0, x0);
+        atomicMax(b + 1, x1);
+        atomicMin(b + 2, y0);
+        atomicMax(b + 3, y1);
+    }
 }
 
 // Eq. (4) for one triangle (world vertices X, Y, Z, squared centroid-camera
@@ -32,36 +107,57 @@ __global__ void __launch_bounds__(256) k_clear_depth(const __grid_constant__ Lay
 // of p w_j - x_j from one FMA each.
 // `sink(pixel)` is called for each covered pixel (row-major index in c's
 // image).
-template <class Sink>
-__device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const float* Y, const float* Z,
-                                           Sink&& sink) {
+// The first part of the test: the homogeneous image points of the vertices
+// and the candidate pixels (centres within 1/64 px of the box of the
+// approximate projections; their error is below 1e-3 px for images up to
+// 65535 px, and the exact box test in raster_pixels decides).  False if a
+// vertex is not in front of the camera or no pixel centre is a candidate.
+struct TriSetup {
     float xh[3], yh[3], wh[3];
+    int x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ bool raster_setup(const Cam& c, const float* X, const float* Y, const float* Z,
+                                             TriSetup& s) {
     bool ok = true;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        project(c.P, X[j], Y[j], Z[j], xh[j], yh[j], wh[j]);
-        ok &= wh[j] > 0.0f;
+        project(c.P, X[j], Y[j], Z[j], s.xh[j], s.yh[j], s.wh[j]);
+        ok &= s.wh[j] > 0.0f;
     }
-    if (!ok) return;
-    // candidate pixels: centres within 1/64 px of the box of the approximate
-    // projections (their error is below 1e-3 px for images up to 65535 px;
-    // the exact box test below decides)
+    if (!ok) return false;
     float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const float r = rcp_approx(wh[j]);
-        const float u = fmul(xh[j], r), v = fmul(yh[j], r);
+        const float r = rcp_approx(s.wh[j]);
+        const float u = fmul(s.xh[j], r), v = fmul(s.yh[j], r);
         umin = fminf(umin, u); umax = fmaxf(umax, u);
         vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
     }
     constexpr float kSlack = 0.5f + 1.0f / 64.0f;
-    if (!(umax >= 0.0f && vmax >= 0.0f && umin <= c.Wf && vmin <= c.Hf)) return;
-    const int x0 = max(0, (int)ceilf(fsub(umin, kSlack)));
-    const int y0 = max(0, (int)ceilf(fsub(vmin, kSlack)));
-    const int x1 = umax > c.Wf ? c.W - 1 : min(c.W - 1, (int)floorf(fsub(fadd(umax, 1.0f / 64.0f), 0.5f)));
-    const int y1 = vmax > c.Hf ? c.H - 1 : min(c.H - 1, (int)floorf(fsub(fadd(vmax, 1.0f / 64.0f), 0.5f)));
-    if (x0 > x1 || y0 > y1) return;      // no pixel centre near the box
-    // homogeneous edge functions of edges (0,1), (1,2), (2,0): no division
+    if (!(umax >= 0.0f && vmax >= 0.0f && umin <= c.Wf && vmin <= c.Hf)) return false;
+    s.x0 = max(0, (int)ceilf(fsub(umin, kSlack)));
+    s.y0 = max(0, (int)ceilf(fsub(vmin, kSlack)));
+    s.x1 = umax > c.Wf ? c.W - 1 : min(c.W - 1, (int)floorf(fsub(fadd(umax, 1.0f / 64.0f), 0.5f)));
+    s.y1 = vmax > c.Hf ? c.H - 1 : min(c.H - 1, (int)floorf(fsub(fadd(vmax, 1.0f / 64.0f), 0.5f)));
+    return s.x0 <= s.x1 && s.y0 <= s.y1;
+}
+
+// The second part: the triangle is skipped if its projected area is zero;
+// `sink(pixel)` is called for each candidate pixel (row-major index in c's
+// image) whose centre p lies in the closed box of the projection and on the
+// inner side of (or on) all three edges, either winding.  Everything is
+// decided on the homogeneous image points (x', y', w') without dividing: the
+// edge function of edge (i, j) at p is (p_x a - p_y b) + c with
+// a = y_i w_j - w_i y_j, b = x_i w_j - w_i x_j, c = x_i y_j - y_i x_j (its sign
+// is the image-plane one for w > 0), the area is zero iff
+// (x_0 a_12 - y_0 b_12) + w_0 c_12 is, and the box test uses the exact signs
+// of p w_j - x_j from one FMA each.
+template <class Sink>
+__device__ __forceinline__ void raster_pixels(const Cam& c, const TriSetup& s, Sink&& sink) {
+    const float* xh = s.xh;
+    const float* yh = s.yh;
+    const float* wh = s.wh;
     float ea[3], eb[3], ec[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
@@ -72,12 +168,12 @@ __device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const f
     }
     const float det = fadd(fsub(fmul(xh[0], ea[1]), fmul(yh[0], eb[1])), fmul(wh[0], ec[1]));
     if (!(det > 0.0f || det < 0.0f)) return;
-    for (int yy = y0; yy <= y1; ++yy) {
+    for (int yy = s.y0; yy <= s.y1; ++yy) {
         const float pcy = fadd((float)yy, 0.5f);
         const float s0 = __fmaf_rn(pcy, wh[0], -yh[0]), s1 = __fmaf_rn(pcy, wh[1], -yh[1]),
                     s2 = __fmaf_rn(pcy, wh[2], -yh[2]);
         if (!((s0 >= 0.0f || s1 >= 0.0f || s2 >= 0.0f) && (s0 <= 0.0f || s1 <= 0.0f || s2 <= 0.0f))) continue;
-        for (int xx = x0; xx <= x1; ++xx) {
+        for (int xx = s.x0; xx <= s.x1; ++xx) {
             const float pcx = fadd((float)xx, 0.5f);
             const float r0 = __fmaf_rn(pcx, wh[0], -xh[0]), r1 = __fmaf_rn(pcx, wh[1], -xh[1]),
                         r2 = __fmaf_rn(pcx, wh[2], -xh[2]);
@@ -89,6 +185,14 @@ __device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const f
             if (in) sink((size_t)yy * (unsigned)c.W + xx);
         }
     }
+}
+
+// Eq. (4) coverage of one triangle (world vertices X, Y, Z) in camera c.
+template <class Sink>
+__device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const float* Y, const float* Z,
+                                           Sink&& sink) {
+    TriSetup s;
+    if (raster_setup(c, X, Y, Z, s)) raster_pixels(c, s, sink);
 }
 
 // Grid (blocks, cameras, slots): the camera is uniform over a block, so its
@@ -288,11 +392,26 @@ __global__ void k_debug_depth(const __grid_constant__ Layout L, int slot, float*
 
 }  // namespace
 
+cudaError_t launch_init_depth(const CamSet& cams, const Layout& L, int n_slots, int sms, cudaStream_t st) {
+    size_t pix = 0;
+    for (int n = 0; n < cams.n; ++n) pix += (size_t)cams.c[n].W * cams.c[n].H;
+    const size_t n16 = (pix * 4 + 15) / 16;
+    const unsigned gx = (unsigned)std::max<size_t>(1, std::min<size_t>((n16 + 255) / 256, (size_t)sms * 4));
+    for (int s0 = 0; s0 < n_slots; s0 += 65535) {
+        // slots s0.. in one launch (blockIdx.y is at most 65535)
+        Layout Ls = L;
+        Ls.base = L.base + (size_t)s0 * L.stride;
+        k_init_depth<<<dim3(gx, std::min(65535, n_slots - s0)), 256, 0, st>>>(Ls, n16, cams.n);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,
                          size_t depth_bytes, const Tuning& tu, cudaStream_t st) {
-    const size_t n16 = depth_bytes / 16;
-    const int gc = grid_x(sms, sl.n, (long long)n16, 256);
-    k_clear_depth<<<dim3(gc, sl.n), 256, 0, st>>>(L, sl, n16);
+    (void)depth_bytes;
+    const int gc = std::max(1, sms * 4 / std::max(1, sl.n * cams.n));
+    k_clear_depth<<<dim3(gc, cams.n, sl.n), 256, 0, st>>>(cams, L, sl);
+    k_depth_box<<<sl.n, 256, 0, st>>>(cams, g, L, sl);
     const int gz = tuned_grid(tu, FVV_TUNE_ZBUFFER, sms, sl.n, (long long)g.max_tris, cams.n);
     k_zbuffer<<<dim3(gz, cams.n, sl.n), tu.threads[FVV_TUNE_ZBUFFER], 0, st>>>(cams, L, sl);
     return cudaGetLastError();

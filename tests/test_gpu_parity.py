@@ -79,6 +79,34 @@ def test_masks_read_in_place_including_ragged_rows():
     compare(rig, fr, run_gpu(rig, [fr], masks_in_place=True)[0])
 
 
+def test_slot_reuse_leaves_no_stale_depth():
+    """A slot reconstructed again with a different frame: the depth stage
+    clears only the box the previous z-buffer wrote, and every output (the
+    whole depth images included) equals the oracle's for the new frame."""
+    from paper_1903_11785_gb300 import fvv
+    rig = make_rig("tiny")
+    f0, f1 = make_frame("tiny", 0, rig=rig)[1], make_frame("tiny", 5, rig=rig)[1]
+    r = fvv.Rig(rig, max_slots=1, host_staging=0)
+    try:
+        for fr in (f0, f1, f0):
+            r.upload_silhouettes(0, fr.masks.cuda())
+            r.reconstruct([0])
+            r.colour([0], [fr.rgb.cuda()], fr.viewpoint[None])
+            torch.cuda.synchronize()
+            c = r.counts(0)
+            res = r.results(0)
+            g = dict(counts=c, rois=res["rois"], verts=res["verts"].cpu().numpy(), tris=res["tris"].cpu().numpy(),
+                     rgb=res["rgb"].cpu().numpy(), cam=res["cam"].cpu().numpy(),
+                     sil=r.debug(0, fvv.FVV_DEBUG_SIL_BITS).cpu().numpy().view(np.uint32),
+                     coarse=r.debug(0, fvv.FVV_DEBUG_COARSE_BITS).cpu().numpy().view(np.uint32),
+                     labels=r.debug(0, fvv.FVV_DEBUG_LABELS).cpu().numpy(),
+                     fine=r.debug(0, fvv.FVV_DEBUG_FINE_BITS).cpu().numpy().view(np.uint32),
+                     depth=r.debug(0, fvv.FVV_DEBUG_DEPTH).cpu().numpy())
+            compare(rig, fr, g)
+    finally:
+        r.close()
+
+
 def test_batched_slots_each_bit_exact():
     """Three frames in one reconstruct/colour call, slots listed out of order."""
     rig = make_rig("tiny")
