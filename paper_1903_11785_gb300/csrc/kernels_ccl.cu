@@ -63,24 +63,38 @@ __device__ __forceinline__ bool coarse_on(const uint32_t* bits, const Grid& g, i
 }
 
 // Union of every occupied voxel with its 13 occupied neighbours that come
-// before it in linear order (the other 13 see it in turn).
+// before it in linear order (the other 13 see it in turn).  A warp reads 32
+// words of the coarse bitset (a lane each) and then takes its non-empty
+// words one at a time with a lane per voxel, so the chains of dependent
+// loads of a row's voxels run side by side rather than one after another in
+// a thread.
 __global__ void __launch_bounds__(256) k_union(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
                                                const __grid_constant__ SlotList sl) {
     const int slot = sl.s[blockIdx.y];
     const uint32_t* bits = slot_ptr<uint32_t>(L, slot, L.coarse);
     int* parent = slot_ptr<int>(L, slot, L.parent);
     const uint32_t nwords = (uint32_t)g.nz * g.ny * g.nxw;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     int budget = kStepBudget;
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords && budget > 0; w += gridDim.x * blockDim.x) {
-        uint32_t word = __ldg(bits + w);
-        if (!word) continue;
-        const uint32_t row = w / (uint32_t)g.nxw;
-        const int wx = (int)(w - row * g.nxw);
-        const int y = (int)(row % (uint32_t)g.ny), z = (int)(row / (uint32_t)g.ny);
-        while (word) {
-            const int b = __ffs(word) - 1;
-            word &= word - 1;
-            const int x = wx * 32 + b;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (uint32_t base = 0; base < nwords; base += nwarps * 32u) {
+        // words interleaved over the warps (lane l of warp k reads word
+        // base + l * nwarps + k), so that neighbouring words, which often
+        // belong to one object, are worked on by different warps
+        const uint32_t mw = base + (uint32_t)lane * nwarps + gw;
+        const uint32_t mine = mw < nwords ? __ldg(bits + mw) : 0u;
+        uint32_t pending = __ballot_sync(kFull, mine != 0u);
+        while (pending) {
+            const int src = __ffs(pending) - 1;
+            pending &= pending - 1u;
+            const uint32_t w = base + (uint32_t)src * nwarps + gw;
+            const uint32_t word = __shfl_sync(kFull, mine, src);
+            if (!((word >> lane) & 1u) || budget <= 0) continue;
+            const uint32_t row = w / (uint32_t)g.nxw;
+            const int wx = (int)(w - row * g.nxw);
+            const int y = (int)(row % (uint32_t)g.ny), z = (int)(row / (uint32_t)g.ny);
+            const int x = wx * 32 + lane;
             const int Lin = (int)row * g.nx + x;
             for (int dz = -1; dz <= 0; ++dz)
                 for (int dy = -1; dy <= 1; ++dy)
@@ -94,7 +108,8 @@ __global__ void __launch_bounds__(256) k_union(const __grid_constant__ Grid g, c
     if (budget <= 0) atomicOr(&slot_ptr<SlotInfo>(L, slot, L.info)->flags, (unsigned)FVV_FLAG_LOOP);
 }
 
-// Point every voxel at its root and list the roots (unordered).
+// Point every voxel at its root and list the roots (unordered); words are
+// taken as in k_union, a lane per voxel.
 __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
                                                   const __grid_constant__ SlotList sl) {
     const int slot = sl.s[blockIdx.y];
@@ -103,16 +118,26 @@ __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ Grid g
     int* roots = slot_ptr<int>(L, slot, L.roots);
     SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
     const uint32_t nwords = (uint32_t)g.nz * g.ny * g.nxw;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     int budget = kStepBudget;
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords && budget > 0; w += gridDim.x * blockDim.x) {
-        uint32_t word = __ldg(bits + w);
-        if (!word) continue;
-        const uint32_t row = w / (uint32_t)g.nxw;
-        const int wx = (int)(w - row * g.nxw);
-        while (word) {
-            const int b = __ffs(word) - 1;
-            word &= word - 1;
-            const int Lin = (int)row * g.nx + wx * 32 + b;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (uint32_t base = 0; base < nwords; base += nwarps * 32u) {
+        // words interleaved over the warps (lane l of warp k reads word
+        // base + l * nwarps + k), so that neighbouring words, which often
+        // belong to one object, are worked on by different warps
+        const uint32_t mw = base + (uint32_t)lane * nwarps + gw;
+        const uint32_t mine = mw < nwords ? __ldg(bits + mw) : 0u;
+        uint32_t pending = __ballot_sync(kFull, mine != 0u);
+        while (pending) {
+            const int src = __ffs(pending) - 1;
+            pending &= pending - 1u;
+            const uint32_t w = base + (uint32_t)src * nwarps + gw;
+            const uint32_t word = __shfl_sync(kFull, mine, src);
+            if (!((word >> lane) & 1u) || budget <= 0) continue;
+            const uint32_t row = w / (uint32_t)g.nxw;
+            const int wx = (int)(w - row * g.nxw);
+            const int Lin = (int)row * g.nx + wx * 32 + lane;
             const int r = find_root(parent, Lin, budget);
             if (r == Lin) {
                 const int k = atomicAdd(&info->n_roots, 1);
@@ -175,17 +200,12 @@ __global__ void __launch_bounds__(1024) k_sort_roots(const __grid_constant__ Gri
     }
 }
 
-__device__ __forceinline__ void flush_stats(int* s, int cnt, const int* lo, const int* hi) {
-    atomicAdd(s, cnt);
-    for (int a = 0; a < 3; ++a) {
-        atomicMin(s + 1 + a, lo[a]);
-        atomicMax(s + 4 + a, hi[a]);
-    }
-}
-
 // Voxel count and inclusive box of every component (Sec. II-B-2 takes the
-// smallest box holding each labelled set after labelling).  Runs of
-// voxels of one component in a word are merged before the atomics.
+// smallest box holding each labelled set after labelling).  Words are taken
+// as in k_union: a non-empty word (one row segment: y and z are the same for
+// all its voxels) with a lane per voxel; lanes of the same component are
+// merged (__match_any_sync) and the lowest of them makes the atomics for the
+// group, whose x range is the span of its lanes.
 __global__ void __launch_bounds__(256) k_stats(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
                                                const __grid_constant__ SlotList sl) {
     const int slot = sl.s[blockIdx.y];
@@ -195,35 +215,43 @@ __global__ void __launch_bounds__(256) k_stats(const __grid_constant__ Grid g, c
     const int* parent = slot_ptr<int>(L, slot, L.parent);
     int* cstat = slot_ptr<int>(L, slot, L.cstat);
     const uint32_t nwords = (uint32_t)g.nz * g.ny * g.nxw;
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) {
-        uint32_t word = __ldg(bits + w);
-        if (!word) continue;
-        const uint32_t row = w / (uint32_t)g.nxw;
-        const int wx = (int)(w - row * g.nxw);
-        const int y = (int)(row % (uint32_t)g.ny), z = (int)(row / (uint32_t)g.ny);
-        int cur = -1, cnt = 0, lo[3], hi[3];
-        while (word) {
-            const int b = __ffs(word) - 1;
-            word &= word - 1;
-            const int x = wx * 32 + b;
-            const int Lin = (int)row * g.nx + x;
-            const int r = parent[Lin];
-            const int t = r < 0 ? r : parent[r];
-            if (t >= 0) continue;  // roots were not tagged (capacity overflow)
-            const int idx = -t - 1;
-            if (idx != cur) {
-                if (cur >= 0) flush_stats(cstat + 7 * cur, cnt, lo, hi);
-                cur = idx;
-                cnt = 0;
-                lo[0] = lo[1] = lo[2] = 0x7FFFFFFF;
-                hi[0] = hi[1] = hi[2] = -1;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (uint32_t base = 0; base < nwords; base += nwarps * 32u) {
+        // words interleaved over the warps (lane l of warp k reads word
+        // base + l * nwarps + k), so that neighbouring words, which often
+        // belong to one object, are worked on by different warps
+        const uint32_t mw = base + (uint32_t)lane * nwarps + gw;
+        const uint32_t mine = mw < nwords ? __ldg(bits + mw) : 0u;
+        uint32_t pending = __ballot_sync(kFull, mine != 0u);
+        while (pending) {                             // the same in every lane
+            const int src = __ffs(pending) - 1;
+            pending &= pending - 1u;
+            const uint32_t w = base + (uint32_t)src * nwarps + gw;
+            const uint32_t word = __shfl_sync(kFull, mine, src);
+            const uint32_t row = w / (uint32_t)g.nxw;
+            const int wx = (int)(w - row * g.nxw);
+            const int y = (int)(row % (uint32_t)g.ny), z = (int)(row / (uint32_t)g.ny);
+            int idx = -1;
+            if ((word >> lane) & 1u) {
+                const int Lin = (int)row * g.nx + wx * 32 + lane;
+                const int r = parent[Lin];
+                const int t = r < 0 ? r : parent[r];
+                if (t < 0) idx = -t - 1;              // else: roots were not tagged (capacity overflow)
             }
-            ++cnt;
-            lo[0] = min(lo[0], x); hi[0] = max(hi[0], x);
-            lo[1] = min(lo[1], y); hi[1] = max(hi[1], y);
-            lo[2] = min(lo[2], z); hi[2] = max(hi[2], z);
+            const uint32_t grp = __match_any_sync(kFull, idx);
+            if (idx >= 0 && lane == __ffs(grp) - 1) {
+                int* st = cstat + 7 * idx;
+                atomicAdd(st, __popc(grp));
+                atomicMin(st + 1, wx * 32 + lane);
+                atomicMax(st + 4, wx * 32 + 31 - __clz(grp));
+                atomicMin(st + 2, y);
+                atomicMax(st + 5, y);
+                atomicMin(st + 3, z);
+                atomicMax(st + 6, z);
+            }
         }
-        if (cur >= 0) flush_stats(cstat + 7 * cur, cnt, lo, hi);
     }
 }
 
