@@ -41,12 +41,12 @@ METRIC = "frames/s & G voxel-camera tests/s on 1 GB300, batched vs plain; p50/p9
 CONFIG = "volleyball"
 WORKLOAD = ("volleyball-shaped frames: 16 cameras 1920x1080 (f=1800), 12 players + ball, volume 20x11x4 m, "
             "coarse 5 cm (400x220x80), fine 1 cm in ROIs, 10 bisection steps, 0.1% silhouette flips")
-# FP32 operations of one camera test by definition: x', y', w' (9 mul + 9 add),
-# u and v (2 divisions), two floors.
+# FP32 floating-point operations of one camera test by definition: x', y', w'
+# (9 fused multiply-adds, 2 operations each), u and v (2 divisions), two floors.
 FLOPS_PER_TEST = 22
-# FP32 issue peak of GB300: 152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock),
-# counting a multiply or an add as one operation (the path uses no FMA).
-ALU_PEAK_TFLOPS = 152 * 128 * 2.070e9 / 1e12
+# FP32 peak of GB300: 152 SMs x 128 FP32 lanes x 2 (a fused multiply-add per
+# lane per clock) x 2.07 GHz (maximum SM clock).
+ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) per frame of each hull kernel, from one ncu capture
 # of a 4-frame launch of the current kernels (profiles/k_fine_carve_volleyball_batch4.md,
 # profiles/hull_and_depth_kernels_volleyball_batch4.md), scaled to a launch by
@@ -377,8 +377,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        for i in slots:
-            r.upload_silhouettes(i, masks[i])
+        r.upload_silhouettes_batch(slots, masks)
         r.reconstruct(slots)
         r.colour(slots, rgb, vps)
 
@@ -458,7 +457,7 @@ def run_ours(args):
                                            "bisect": "k_bisect"}[dom],
                 "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / ALU_PEAK_TFLOPS,
                 "traffic": traffic * F if traffic is not None else None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (unit counts, max clock)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz (unit counts, max clock)",
                 "launch_ms": launch_ms, "tests_per_launch": tsum["tests_" + dom] if dom != "bisect" else
                 tsum["tests_bisect"], "flops_per_test": FLOPS_PER_TEST}
 
@@ -508,8 +507,7 @@ def run_ours(args):
             # so the next group is queued before the previous one is read back
             def compute(grp, st):
                 with torch.cuda.stream(st):
-                    for i in grp:
-                        r.upload_silhouettes(i, masks_h[i], stream=st, in_place=True)
+                    r.upload_silhouettes_batch(grp, masks_h[grp[0]:grp[-1] + 1], stream=st, in_place=True)
                     r.reconstruct(grp, stream=st)
                     r.colour(grp, rgb_h[grp[0]:grp[-1] + 1], vps[grp[0]:grp[-1] + 1], stream=st, in_place=True)
 
@@ -585,7 +583,11 @@ def run_ours(args):
         per_cfg["volleyball"] = {"ms_per_frame": 1000 * dt / S, "frames": S, "tests_per_frame": tps * dt / S}
         cpu["single_core_per_config"] = per_cfg
 
-    n_launch = args.steps * (F + 16)
+    # kernels per step: one packing launch per 128 frames; the reconstruction's 17
+    # (info reset; coarse hull; 5 for CCL, boxes and filter; fine-grid clear
+    # and fine hull; 3 for MC counts, scan and records; bisection; triangles;
+    # depth clear, box and z-buffer); one colour launch per 48 frames
+    n_launch = args.steps * ((F + 127) // 128 + 17 + (F + 47) // 48)
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -629,8 +631,7 @@ def _timed_reconstruction(fvv, torch, rig, frames, reps=3, keep_results=False):
         vps = np.stack([f.viewpoint for f in frames])
 
         def step():
-            for i in slots:
-                r.upload_silhouettes(i, masks[i])
+            r.upload_silhouettes_batch(slots, masks)
             r.reconstruct(slots)
             r.colour(slots, rgb, vps)
         step()

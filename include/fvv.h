@@ -19,8 +19,10 @@
  * [py, py+1); images are row-major, W pixels per row.  Voxel i of a grid with
  * origin o and step s is tested at its centre o + (i + 1/2) s.  Linear voxel
  * index L = (z*ny + y)*nx + x (x fastest).  All floating point on the device
- * is IEEE binary32, round to nearest, in a fixed order with no fused
- * multiply-add, so results are reproducible bit for bit.
+ * is IEEE binary32, round to nearest, in a fixed order, so results are
+ * reproducible bit for bit; each row of the projection is the three fused
+ * multiply-adds ((p3 + p2 Z) + p1 Y) + p0 X, every other product and sum is
+ * rounded on its own.
  *
  * Memory.  As the paper does (Sec. III-B), all device memory a rig needs is
  * taken once, at fvv_create_rig, as one arena: either a buffer the caller
@@ -214,6 +216,16 @@ fvv_status fvv_destroy_rig(fvv_rig *rig);
  * packing kernel reads them in place from mapped page-locked host memory. */
 fvv_status fvv_upload_silhouettes(fvv_rig *rig, int slot, const uint8_t *const *masks,
                                   int masks_on_device, void *stream);
+
+/* fvv_upload_silhouettes for several frames at once: frame j's masks
+ * (masks[j*n_cams + n] for camera n, memory as for fvv_upload_silhouettes)
+ * go into slots[j], n_slots distinct slots (1..256).  One packing launch
+ * takes up to min(512, 2048 / n_cams) frames, so a batch costs a few
+ * launches instead of one per frame.  Nothing is packed if an argument is
+ * rejected. */
+fvv_status fvv_upload_silhouettes_batch(fvv_rig *rig, const int *slots, int n_slots,
+                                        const uint8_t *const *masks, int masks_on_device,
+                                        void *stream);
 
 /* Reconstruct the frames in `slots` (n_slots distinct slots, each uploaded):
  * coarse hull, CCL, filter and ROIs, fine hull, bisected marching-cubes mesh

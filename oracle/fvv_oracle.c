@@ -12,7 +12,7 @@
  * The file is compiled twice: -DORC_REAL=float is the parity target (all
  * floating point is IEEE binary32 with round-to-nearest, evaluated in the
  * order written) and -DORC_REAL=double gives the flip count.  Build with
- * -ffp-contract=off so that no multiply and add are fused into an FMA.
+ * -ffp-contract=off so that only the explicit fma() calls are fused.
  *
  * Steps, in the paper's order:
  *   Sec. II-B-1  coarse ("sparse") visual hull        orc_coarse
@@ -29,6 +29,9 @@
  * Readings of the paper used here (each is also listed with the design notes):
  *  - A voxel is tested at its centre c = o + (i + 1/2) s (Sec. II-B-1 says
  *    the voxel is projected; the paper does not say which point).
+ *  - The projection (x', y', w') = P (X, Y, Z, 1) is evaluated per row as
+ *    ((p_3 + p_2 Z) + p_1 Y) + p_0 X, three fused multiply-adds (the paper
+ *    fixes no arithmetic; this is the cheapest fixed order).
  *  - A camera votes "foreground" iff w' > 0, the pixel (floor(x'/w'),
  *    floor(y'/w')) -- the floor of the exact quotient of the homogeneous
  *    coordinates as computed -- is inside the image and its silhouette bit
@@ -130,15 +133,24 @@ static int grid_dim(float lo, float hi, float step)
  * the double floor is the exact one. */
 static double pixel_floor(R x, R w) { return floor((double)x / (double)w); }
 
+/* Row r of the homogeneous projection, P_r . (X, Y, Z, 1), evaluated as
+ * ((p_r3 + p_r2 Z) + p_r1 Y) + p_r0 X with every step one fused
+ * multiply-add (one rounding each, from the innermost term out). */
+static R proj_row(const float *p, int r, R X, R Y, R Z)
+{
+    const float *q = p + 4 * r;
+    return fma((R)q[0], X, fma((R)q[1], Y, fma((R)q[2], Z, (R)q[3])));
+}
+
 /* One camera's vote for world point (X,Y,Z): 1 foreground, 0 background,
  * -1 abstain (Sec. II-B-1: project the voxel onto the silhouette). */
 static int camera_vote(const orc_rig *rig, const uint8_t *const *masks, int n,
                        R X, R Y, R Z)
 {
     const float *p = rig->P + 12 * n;
-    R xp = (((R)p[0] * X + (R)p[1] * Y) + (R)p[2] * Z) + (R)p[3];
-    R yp = (((R)p[4] * X + (R)p[5] * Y) + (R)p[6] * Z) + (R)p[7];
-    R wp = (((R)p[8] * X + (R)p[9] * Y) + (R)p[10] * Z) + (R)p[11];
+    R xp = proj_row(p, 0, X, Y, Z);
+    R yp = proj_row(p, 1, X, Y, Z);
+    R wp = proj_row(p, 2, X, Y, Z);
     int off = rig->oob_policy == ORC_ABSTAIN ? -1 : 0;
     if (!(wp > (R)0)) return off;
     double fu = pixel_floor(xp, wp), fv = pixel_floor(yp, wp);
@@ -191,12 +203,12 @@ static R camera_lambda(const orc_rig *rig, const uint8_t *const *masks, int n, c
                        long long *tests)
 {
     const float *p = rig->P + 12 * n;
-    R xa = (((R)p[0] * a[0] + (R)p[1] * a[1]) + (R)p[2] * a[2]) + (R)p[3];
-    R ya = (((R)p[4] * a[0] + (R)p[5] * a[1]) + (R)p[6] * a[2]) + (R)p[7];
-    R wa = (((R)p[8] * a[0] + (R)p[9] * a[1]) + (R)p[10] * a[2]) + (R)p[11];
-    R xb = (((R)p[0] * b[0] + (R)p[1] * b[1]) + (R)p[2] * b[2]) + (R)p[3];
-    R yb = (((R)p[4] * b[0] + (R)p[5] * b[1]) + (R)p[6] * b[2]) + (R)p[7];
-    R wb = (((R)p[8] * b[0] + (R)p[9] * b[1]) + (R)p[10] * b[2]) + (R)p[11];
+    R xa = proj_row(p, 0, a[0], a[1], a[2]);
+    R ya = proj_row(p, 1, a[0], a[1], a[2]);
+    R wa = proj_row(p, 2, a[0], a[1], a[2]);
+    R xb = proj_row(p, 0, b[0], b[1], b[2]);
+    R yb = proj_row(p, 1, b[0], b[1], b[2]);
+    R wb = proj_row(p, 2, b[0], b[1], b[2]);
     if (!(wa > (R)0 && wb > (R)0)) return (R)1;
     int W = rig->width[n], H = rig->height[n];
     long long x = end_pixel(xa, wa, W), y = end_pixel(ya, wa, H);
@@ -885,9 +897,9 @@ typedef struct {
 static int cover_setup(const float *p, int W, int H, const R *X, const R *Y, const R *Z, tri_cover *t)
 {
     for (int j = 0; j < 3; ++j) {
-        t->xh[j] = (((R)p[0] * X[j] + (R)p[1] * Y[j]) + (R)p[2] * Z[j]) + (R)p[3];
-        t->yh[j] = (((R)p[4] * X[j] + (R)p[5] * Y[j]) + (R)p[6] * Z[j]) + (R)p[7];
-        t->wh[j] = (((R)p[8] * X[j] + (R)p[9] * Y[j]) + (R)p[10] * Z[j]) + (R)p[11];
+        t->xh[j] = proj_row(p, 0, X[j], Y[j], Z[j]);
+        t->yh[j] = proj_row(p, 1, X[j], Y[j], Z[j]);
+        t->wh[j] = proj_row(p, 2, X[j], Y[j], Z[j]);
         if (!(t->wh[j] > (R)0)) return 0;
     }
     for (int e = 0; e < 3; ++e) {
@@ -1033,9 +1045,9 @@ static int colour_point(const orc_rig *rig, const uint8_t *const *rgb, const int
     for (int r = 0; r < rig->n_cams; ++r) {
         int n = rank[r];
         const float *p = rig->P + 12 * n;
-        R xp = (((R)p[0] * X + (R)p[1] * Y) + (R)p[2] * Z) + (R)p[3];
-        R yp = (((R)p[4] * X + (R)p[5] * Y) + (R)p[6] * Z) + (R)p[7];
-        R wp = (((R)p[8] * X + (R)p[9] * Y) + (R)p[10] * Z) + (R)p[11];
+        R xp = proj_row(p, 0, X, Y, Z);
+        R yp = proj_row(p, 1, X, Y, Z);
+        R wp = proj_row(p, 2, X, Y, Z);
         if (!(wp > (R)0)) continue;
         double fu = pixel_floor(xp, wp), fv = pixel_floor(yp, wp);
         int W = rig->width[n], H = rig->height[n];

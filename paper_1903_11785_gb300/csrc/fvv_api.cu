@@ -66,10 +66,10 @@ long long um_of(float m) { return llround((double)m * 1e6); }
 // coordinate of the edge (at most 30 midpoints, each rounded by half an ulp)
 // and inside the box B = the grid grown by one coarse and two fine voxels
 // (ROI overshoot and padding samples).  For a row r of P, the computed
-// binary32 value ((p0 X + p1 Y) + p2 Z) + p3 differs from the exact value at
-// the nearest edge point by at most 2^-18 S_r, with S_r = sum |p_rj| max_B
-// |X_j| + |p_r3| (four roundings of at most 2^-24 relative to S_r, plus the
-// point's deviation).  With w' >= w_min - 2^-18 S_w > 0 on B and |u| <= W + 1
+// binary32 value ((p3 + p2 Z) + p1 Y) + p0 X (three fused multiply-adds)
+// differs from the exact value at the nearest edge point by at most
+// 2^-18 S_r, with S_r = sum |p_rj| max_B |X_j| + |p_r3| (three roundings of
+// at most 2^-24 relative to S_r, plus the point's deviation).  With w' >= w_min - 2^-18 S_w > 0 on B and |u| <= W + 1
 // inside the image, the computed u = x'/w' of a tested point lies within
 // 2^-18 (S_x + (W + 1) S_w) / (w_min - 2^-18 S_w) of the exact projection of
 // an edge point, which lies between the exact projections of the ends (a
@@ -409,42 +409,67 @@ static const uint8_t* mapped_host(const uint8_t* p, size_t bytes) {
     return d;
 }
 
-fvv_status fvv_upload_silhouettes(fvv_rig* rig, int slot, const uint8_t* const* masks, int masks_on_device,
-                                  void* stream) {
+// Validates and stages the masks of frames j < n_frames (slots[j], masks
+// masks[j * n_cams + n]), then packs them.
+static fvv_status upload(fvv_rig* rig, int n_frames, const int* slots, const uint8_t* const* masks,
+                         int masks_on_device, void* stream, const char* who) {
     if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
-    if (!check_slot(rig, slot)) return fail(rig, FVV_ERR_INVALID_ARG, "slot out of range");
+    if (!slots || n_frames < 1 || n_frames > FVV_MAX_BATCH)
+        return fail(rig, FVV_ERR_INVALID_ARG, "slots must list 1..256 slots");
     if (!masks) return fail(rig, FVV_ERR_INVALID_ARG, "masks is NULL");
-    const cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const uint8_t* src[FVV_MAX_CAMS];
-    for (int n = 0; n < rig->cams.n; ++n) {
-        if (!masks[n]) return fail(rig, FVV_ERR_INVALID_ARG, "a mask pointer is NULL");
-        src[n] = masks[n];
-    }
     if (masks_on_device < 0 || masks_on_device > FVV_MAPPED_HOST)
         return fail(rig, FVV_ERR_INVALID_ARG, "masks_on_device must be 0, 1 or FVV_MAPPED_HOST");
+    if (!masks_on_device && !rig->host_staging)
+        return fail(rig, FVV_ERR_INVALID_ARG, "host masks need a rig with host_staging");
+    const int N = rig->cams.n;
+    std::vector<char> seen(rig->max_slots, 0);
+    for (int j = 0; j < n_frames; ++j) {
+        if (!check_slot(rig, slots[j])) return fail(rig, FVV_ERR_INVALID_ARG, "slot out of range");
+        if (seen[slots[j]]) return fail(rig, FVV_ERR_INVALID_ARG, "slots must be distinct");
+        seen[slots[j]] = 1;
+        for (int n = 0; n < N; ++n)
+            if (!masks[(size_t)j * N + n]) return fail(rig, FVV_ERR_INVALID_ARG, "a mask pointer is NULL");
+    }
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<const uint8_t*> src(masks, masks + (size_t)n_frames * N);
     if (masks_on_device == FVV_MAPPED_HOST) {
-        for (int n = 0; n < rig->cams.n; ++n) {
-            const Cam& c = rig->cams.c[n];
-            src[n] = mapped_host(masks[n], (size_t)c.W * c.H);
-            if (!src[n]) return fail(rig, FVV_ERR_INVALID_ARG, "a mask is not in mapped page-locked host memory");
-        }
+        for (int j = 0; j < n_frames; ++j)
+            for (int n = 0; n < N; ++n) {
+                const Cam& c = rig->cams.c[n];
+                const uint8_t*& p = src[(size_t)j * N + n];
+                p = mapped_host(p, (size_t)c.W * c.H);
+                if (!p) return fail(rig, FVV_ERR_INVALID_ARG, "a mask is not in mapped page-locked host memory");
+            }
     } else if (!masks_on_device) {
-        if (!rig->host_staging) return fail(rig, FVV_ERR_INVALID_ARG, "host masks need a rig with host_staging");
-        uint8_t* stage = slot_ptr<uint8_t>(rig->L, slot, rig->L.mask_stage);
-        for (int n = 0; n < rig->cams.n; ++n) {
-            const Cam& c = rig->cams.c[n];
-            const cudaError_t e = cudaMemcpyAsync(stage + c.pix_off, masks[n], (size_t)c.W * c.H,
-                                                  cudaMemcpyHostToDevice, st);
-            if (e != cudaSuccess) return cuda_fail(rig, e, "copying masks");
-            src[n] = stage + c.pix_off;
+        for (int j = 0; j < n_frames; ++j) {
+            uint8_t* stage = slot_ptr<uint8_t>(rig->L, slots[j], rig->L.mask_stage);
+            for (int n = 0; n < N; ++n) {
+                const Cam& c = rig->cams.c[n];
+                const uint8_t*& p = src[(size_t)j * N + n];
+                const cudaError_t e = cudaMemcpyAsync(stage + c.pix_off, p, (size_t)c.W * c.H,
+                                                      cudaMemcpyHostToDevice, st);
+                if (e != cudaSuccess) return cuda_fail(rig, e, "copying masks");
+                p = stage + c.pix_off;
+            }
         }
     }
     const int t = stage_begin(rig, FVV_STAGE_PACK, st);
-    const cudaError_t e = launch_pack(rig->cams, rig->L, slot, src, st);
+    const cudaError_t e = launch_pack(rig->cams, rig->L, n_frames, slots, src.data(),
+                                      masks_on_device == FVV_MAPPED_HOST, rig->sms, st);
     stage_end(rig, t, st);
-    if (e != cudaSuccess) return cuda_fail(rig, e, "pack kernel");
-    rig->state[slot] = 1;
+    if (e != cudaSuccess) return cuda_fail(rig, e, who);
+    for (int j = 0; j < n_frames; ++j) rig->state[slots[j]] = 1;
     return FVV_OK;
+}
+
+fvv_status fvv_upload_silhouettes(fvv_rig* rig, int slot, const uint8_t* const* masks, int masks_on_device,
+                                  void* stream) {
+    return upload(rig, 1, &slot, masks, masks_on_device, stream, "fvv_upload_silhouettes");
+}
+
+fvv_status fvv_upload_silhouettes_batch(fvv_rig* rig, const int* slots, int n_slots, const uint8_t* const* masks,
+                                        int masks_on_device, void* stream) {
+    return upload(rig, n_slots, slots, masks, masks_on_device, stream, "fvv_upload_silhouettes_batch");
 }
 
 static fvv_status make_slot_list(fvv_rig* rig, const int* slots, int n_slots, int need_state, SlotList& sl) {

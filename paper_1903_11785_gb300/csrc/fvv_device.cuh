@@ -3,7 +3,8 @@
 //
 // All floating point uses the explicit round-to-nearest intrinsics
 // (__fmul_rn, __fadd_rn, __fdiv_rn, __fsqrt_rn), which the compiler never
-// fuses into an FMA, so every result has one fixed binary32 value.
+// fuses into an FMA, and explicit __fmaf_rn where a fused step is meant, so
+// every result has one fixed binary32 value.
 #pragma once
 
 #include "fvv_internal.h"
@@ -16,12 +17,13 @@ __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 
-// (x', y', w') = P (X, Y, Z, 1), each row evaluated as ((p0 X + p1 Y) + p2 Z) + p3.
+// (x', y', w') = P (X, Y, Z, 1), each row evaluated as ((p3 + p2 Z) + p1 Y) + p0 X
+// with three fused multiply-adds (one rounding per step).
 __device__ __forceinline__ void project(const float* p, float X, float Y, float Z, float& xp, float& yp,
                                         float& wp) {
-    xp = fadd(fadd(fadd(fmul(p[0], X), fmul(p[1], Y)), fmul(p[2], Z)), p[3]);
-    yp = fadd(fadd(fadd(fmul(p[4], X), fmul(p[5], Y)), fmul(p[6], Z)), p[7]);
-    wp = fadd(fadd(fadd(fmul(p[8], X), fmul(p[9], Y)), fmul(p[10], Z)), p[11]);
+    xp = __fmaf_rn(p[0], X, __fmaf_rn(p[1], Y, __fmaf_rn(p[2], Z, p[3])));
+    yp = __fmaf_rn(p[4], X, __fmaf_rn(p[5], Y, __fmaf_rn(p[6], Z, p[7])));
+    wp = __fmaf_rn(p[8], X, __fmaf_rn(p[9], Y, __fmaf_rn(p[10], Z, p[11])));
 }
 
 // Approximate reciprocal (PTX rcp.approx.ftz.f32: at most 1 ulp of error).

@@ -172,8 +172,10 @@ inline int tuned_grid(const Tuning& tu, int knob, int sms, int n_slots, long lon
 void build_mc_table(uint8_t ntri[256], uint8_t edges[256 * kMaxTriPerCell * 3]);
 
 // ---- launchers (all enqueue on `st`)
-cudaError_t launch_pack(const CamSet& cams, const Layout& L, int slot, const uint8_t* const* src,
-                        cudaStream_t st);
+// Packs frame j's masks (src[j * cams.n + n]) into slots[j], j < n_frames;
+// host_src: the sources are mapped page-locked host memory.
+cudaError_t launch_pack(const CamSet& cams, const Layout& L, int n_frames, const int* slots,
+                        const uint8_t* const* src, bool host_src, int sms, cudaStream_t st);
 cudaError_t launch_coarse_carve(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
                                 int sms, const Tuning& tu, cudaStream_t st);
 cudaError_t launch_ccl(const Grid& g, const Layout& L, const SlotList& sl, int sms, cudaStream_t st);

@@ -12,8 +12,12 @@
 namespace fvv {
 namespace {
 
+// The masks of up to kPackFrames frames (frame j: slot[j], camera n:
+// src[j * n_cams + n]) packed by one launch.
+constexpr int kPackPtrs = 2048;
 struct PackSrc {
-    const uint8_t* src[FVV_MAX_CAMS];
+    const uint8_t* src[kPackPtrs];
+    int slot[kPackPtrs / 4];
 };
 
 // High bit of each nonzero byte of w, gathered into 4 bits (byte k -> bit k).
@@ -23,11 +27,13 @@ __device__ __forceinline__ uint32_t nonzero_bytes4(uint32_t w) {
 }
 
 // Step a0: uint8 mask (nonzero = foreground) -> 1 bit per pixel, 32 pixels per
-// word, bit x%32 of word x/32 of its row.  One thread per output word.
+// word, bit x%32 of word x/32 of its row.  One thread per output word; grid
+// (blocks, cameras, frames).
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CamSet cams, const __grid_constant__ PackSrc a,
-                                              uint32_t* __restrict__ sil) {
+                                              const __grid_constant__ Layout L) {
     const Cam& c = cams.c[blockIdx.y];
-    const uint8_t* src = a.src[blockIdx.y];
+    const uint8_t* src = a.src[blockIdx.z * (unsigned)cams.n + blockIdx.y];
+    uint32_t* __restrict__ sil = slot_ptr<uint32_t>(L, a.slot[blockIdx.z], L.sil);
     const size_t words = (size_t)c.H * (unsigned)c.Wq;
     const bool vec = (c.W % 32 == 0) && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (size_t)gridDim.x * blockDim.x) {
@@ -372,15 +378,28 @@ cudaError_t launch_debug_pixels(const CamSet& cams, int cam, long long n, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const CamSet& cams, const Layout& L, int slot, const uint8_t* const* src, cudaStream_t st) {
-    PackSrc a{};
+cudaError_t launch_pack(const CamSet& cams, const Layout& L, int n_frames, const int* slots,
+                        const uint8_t* const* src, bool host_src, int sms, cudaStream_t st) {
     size_t max_words = 0;
-    for (int n = 0; n < cams.n; ++n) {
-        a.src[n] = src[n];
-        max_words = std::max(max_words, (size_t)cams.c[n].H * (unsigned)cams.c[n].Wq);
+    for (int n = 0; n < cams.n; ++n) max_words = std::max(max_words, (size_t)cams.c[n].H * (unsigned)cams.c[n].Wq);
+    const int per_launch = std::min(kPackPtrs / 4, kPackPtrs / std::max(1, cams.n));
+    // Device sources: enough blocks to stream HBM at full rate.  Masks read in
+    // place from host memory are bound by the host link, which about two
+    // blocks per SM keep busy; the rest of the GPU stays free for the work
+    // of other streams meanwhile.
+    const size_t cap = host_src ? (size_t)std::max(1, 2 * sms / std::max(1, cams.n * std::min(n_frames, per_launch)))
+                                : (size_t)2048;
+    const unsigned gx = (unsigned)std::max<size_t>(1, std::min<size_t>((max_words + 255) / 256, cap));
+    static_assert(sizeof(CamSet) + sizeof(PackSrc) + sizeof(Layout) <= 32764, "k_pack parameters");
+    thread_local PackSrc a;   // 18 KB: kept off the stack
+    for (int j0 = 0; j0 < n_frames; j0 += per_launch) {
+        const int nf = std::min(per_launch, n_frames - j0);
+        for (int j = 0; j < nf; ++j) {
+            a.slot[j] = slots[j0 + j];
+            for (int n = 0; n < cams.n; ++n) a.src[j * cams.n + n] = src[(size_t)(j0 + j) * cams.n + n];
+        }
+        k_pack<<<dim3(gx, cams.n, nf), 256, 0, st>>>(cams, a, L);
     }
-    const unsigned gx = (unsigned)std::min<size_t>((max_words + 255) / 256, 2048);
-    k_pack<<<dim3(std::max(1u, gx), cams.n), 256, 0, st>>>(cams, a, slot_ptr<uint32_t>(L, slot, L.sil));
     return cudaGetLastError();
 }
 

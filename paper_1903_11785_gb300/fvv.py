@@ -81,6 +81,7 @@ _sigs = {
     "fvv_create_rig": ([C.POINTER(RigDesc), C.POINTER(ReconParams), _vp, C.c_size_t, C.POINTER(_vp)], C.c_int),
     "fvv_destroy_rig": ([_vp], C.c_int),
     "fvv_upload_silhouettes": ([_vp, C.c_int, C.POINTER(_vp), C.c_int, _vp], C.c_int),
+    "fvv_upload_silhouettes_batch": ([_vp, C.POINTER(C.c_int), C.c_int, C.POINTER(_vp), C.c_int, _vp], C.c_int),
     "fvv_reconstruct": ([_vp, C.POINTER(C.c_int), C.c_int, _vp], C.c_int),
     "fvv_colour": ([_vp, C.POINTER(C.c_int), C.c_int, C.POINTER(_vp), C.c_int, C.POINTER(C.c_float), _vp], C.c_int),
     "fvv_get_counts": ([_vp, C.c_int, C.POINTER(Counts), _vp], C.c_int),
@@ -208,6 +209,24 @@ def fvv_upload_silhouettes(rig_ptr, slot, masks, stream=None, in_place=False):
         assert m.dtype == torch.uint8 and m.is_contiguous() and m.is_cuda == ms[0].is_cuda
     _check(_lib.fvv_upload_silhouettes(rig_ptr, slot, _ptr_array([m.data_ptr() for m in ms]), on_dev,
                                        _stream(stream)), rig_ptr)
+
+
+def fvv_upload_silhouettes_batch(rig_ptr, slots, masks, stream=None, in_place=False):
+    """masks: per slot, a list of per-camera uint8 tensors (H,W) (or one
+    (N,H,W) tensor, or an (F,N,H,W) tensor for all slots); memory kinds as
+    for fvv_upload_silhouettes."""
+    ptrs, ms = [], []
+    for per_slot in masks:
+        imgs = list(per_slot) if not torch.is_tensor(per_slot) else list(per_slot.unbind(0))
+        for m in imgs:
+            assert m.dtype == torch.uint8 and m.is_contiguous()
+            ptrs.append(m.data_ptr())
+            ms.append(m)
+    assert ms and all(m.is_cuda == ms[0].is_cuda for m in ms)
+    on_dev = _rgb_mode(int(ms[0].is_cuda), ms, in_place)
+    arr = (C.c_int * len(slots))(*slots)
+    _check(_lib.fvv_upload_silhouettes_batch(rig_ptr, arr, len(slots), _ptr_array(ptrs), on_dev,
+                                             _stream(stream)), rig_ptr)
 
 
 def fvv_reconstruct(rig_ptr, slots, stream=None):
@@ -357,6 +376,9 @@ class Rig:
 
     def upload_silhouettes(self, slot, masks, stream=None, in_place=False):
         fvv_upload_silhouettes(self.ptr, slot, masks, stream, in_place)
+
+    def upload_silhouettes_batch(self, slots, masks, stream=None, in_place=False):
+        fvv_upload_silhouettes_batch(self.ptr, list(slots), masks, stream, in_place)
 
     def reconstruct(self, slots, stream=None):
         fvv_reconstruct(self.ptr, list(slots), stream)

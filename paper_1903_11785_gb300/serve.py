@@ -127,8 +127,8 @@ class Server:
         r.turn += 1
         slots = [q.slot for q in reqs]
         with torch.cuda.stream(st):
-            for q in reqs:
-                r.rig.upload_silhouettes(q.slot, r.pool.masks[q.frame], stream=st, in_place=r.masks_in_place)
+            r.rig.upload_silhouettes_batch(slots, [r.pool.masks[q.frame] for q in reqs], stream=st,
+                                           in_place=r.masks_in_place)
             r.rig.reconstruct(slots, stream=st)
             rgb = [r.pool.rgb[q.frame] for q in reqs]
             r.rig.colour(slots, rgb, np.stack([r.pool.viewpoints[q.frame] for q in reqs]), stream=st,

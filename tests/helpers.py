@@ -92,3 +92,30 @@ def sphere_rig(n=12, r=6.0, h=2.0, W=640, H=480, f=700.0, vol=1.0, coarse=0.05, 
           for k in range(n)]
     return _make_rig("sphere", cs, [(0, 0, 1.0)] * n, f, W, H, _gen("sphere/rig"),
                      (-vol, -vol, 1.0 - vol), (vol, vol, 1.0 + vol), coarse, fine, steps, jitter_deg=0.0)
+
+
+def fma32(a, b, c):
+    """Correctly rounded binary32 fused multiply-add a*b + c of binary32
+    arrays, in numpy.  The product is exact in binary64 (24 + 24 significant
+    bits); the binary64 sum s and its exact error e (Knuth's TwoSum) give the
+    exact value s + e.  Rounding s to binary32 is correct unless s lies
+    exactly halfway between two binary32 numbers while e != 0; the exact value
+    then lies on e's side of s."""
+    a, b, c = (np.asarray(x, np.float32).astype(np.float64) for x in (a, b, c))
+    p = a * b
+    s = p + c
+    bb = s - p
+    e = (p - (s - bb)) + (c - bb)
+    r = s.astype(np.float32)
+    r64 = r.astype(np.float64)
+    nb = np.nextafter(r, np.where(s > r64, np.float32(np.inf), np.float32(-np.inf)).astype(np.float32))
+    tie = (s != r64) & (np.abs(s - r64) == np.abs(nb.astype(np.float64) - s))
+    return np.where(tie & (e != 0) & ((e > 0) == (s > r64)), nb, r)
+
+
+def project32(P, X, Y, Z):
+    """(x', y', w') of binary32 points through a 3x4 matrix, each row
+    ((p3 + p2 Z) + p1 Y) + p0 X in three fused multiply-adds (binary32)."""
+    P = np.asarray(P, np.float32)
+    X, Y, Z = (np.asarray(v, np.float32) for v in (X, Y, Z))
+    return [fma32(P[r, 0], X, fma32(P[r, 1], Y, fma32(P[r, 2], Z, P[r, 3]))) for r in range(3)]

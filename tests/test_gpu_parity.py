@@ -116,6 +116,39 @@ def test_batched_slots_each_bit_exact():
         compare(rig, fr, g)
 
 
+@pytest.mark.parametrize("mode", ["device", "host", "in_place"])
+def test_batched_upload_each_bit_exact(mode):
+    """Three frames packed by one fvv_upload_silhouettes_batch call, slots
+    out of order, masks on the device, staged from host memory or read in
+    place."""
+    rig = make_rig("tiny")
+    frames = [make_frame("tiny", i, rig=rig)[1] for i in range(3)]
+    outs = run_gpu(rig, frames, slots=[1, 3, 0], upload_batch=True, host=mode == "host",
+                   masks_in_place=mode == "in_place")
+    for fr, g in zip(frames, outs):
+        compare(rig, fr, g)
+
+
+def test_batched_upload_rejects_bad_arguments():
+    from paper_1903_11785_gb300 import fvv
+    rig = make_rig("tiny")
+    frames = [make_frame("tiny", i, rig=rig)[1] for i in range(2)]
+    r = fvv.Rig(rig, max_slots=2, host_staging=0, max_fine_words=1 << 16)
+    try:
+        ms = [fr.masks.cuda() for fr in frames]
+        for bad in ([0, 0], [0, 2], [-1, 1]):
+            with pytest.raises(fvv.FvvError) as e:
+                r.upload_silhouettes_batch(bad, ms)
+            assert e.value.status == fvv.FVV_ERR_INVALID_ARG
+        with pytest.raises(fvv.FvvError):       # host masks need staging
+            r.upload_silhouettes_batch([0, 1], [fr.masks for fr in frames])
+        with pytest.raises(fvv.FvvError) as e:  # nothing was packed
+            r.reconstruct([0])
+        assert e.value.status == fvv.FVV_ERR_NOT_READY
+    finally:
+        r.close()
+
+
 def test_batched_equals_one_by_one():
     rig = make_rig("tiny")
     frames = [make_frame("tiny", i, rig=rig)[1] for i in range(2)]

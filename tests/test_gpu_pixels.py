@@ -1,6 +1,7 @@
 """The projection used by every hull test (Sec. II-B-1), checked through the
-fvv_debug_pixels hook against numpy: x' = ((p0 X + p1 Y) + p2 Z) + p3 (and
-y', w') in binary32, pixel = floor of the exact quotient x'/w'.  Points are
+fvv_debug_pixels hook against numpy: x' = ((p3 + p2 Z) + p1 Y) + p0 X (and
+y', w') in three binary32 fused multiply-adds, pixel = floor of the exact
+quotient x'/w'.  Points are
 placed on rays through pixel corners, so many quotients fall within an ulp
 or two of an integer, where the kernel's approximate reciprocal must be
 corrected by its residual test."""
@@ -11,14 +12,13 @@ import pytest
 import torch
 
 from synth import make_rig
+from tests.helpers import project32
 
 pytestmark = pytest.mark.gpu
 
 
 def _numpy_pixels(P, W, H, pts):
-    P = P.astype(np.float32)
-    X, Y, Z = (pts[:, i].astype(np.float32) for i in range(3))
-    row = [((P[r, 0] * X + P[r, 1] * Y) + P[r, 2] * Z) + P[r, 3] for r in range(3)]
+    row = project32(P, pts[:, 0], pts[:, 1], pts[:, 2])
     xp, yp, wp = (a.astype(np.float64) for a in row)
     with np.errstate(divide="ignore", invalid="ignore"):
         u = np.floor(xp / wp)       # exact floor: see test_oracle_pins.test_pixel_floor_is_exact
@@ -60,10 +60,7 @@ def test_pixel_index_matches_binary32_definition(config):
             np.testing.assert_array_equal(px.cpu().numpy(), ru)
             np.testing.assert_array_equal(py.cpu().numpy(), rv)
             # how many quotients sat within 1e-3 px of an integer (the slow path)
-            P = rig.P[n].astype(np.float32)
-            X, Y, Z = (pts[:, i] for i in range(3))
-            xp = ((P[0, 0] * X + P[0, 1] * Y) + P[0, 2] * Z) + P[0, 3]
-            wp = ((P[2, 0] * X + P[2, 1] * Y) + P[2, 2] * Z) + P[2, 3]
+            xp, _, wp = project32(rig.P[n], pts[:, 0], pts[:, 1], pts[:, 2])
             with np.errstate(divide="ignore", invalid="ignore"):
                 q = xp.astype(np.float64) / wp
             fr = np.abs(q - np.round(q))

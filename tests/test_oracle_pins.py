@@ -12,7 +12,7 @@ from oracle import Oracle
 from oracle.oracle import Roi
 from synth import ABSTAIN, STRICT, make_frame, make_rig, render, sphere_scene, inside_any
 from tests.helpers import (affine_rig, canonical_labels, closed_oriented, edge_use, euler_characteristic,
-                           mesh_shells, signed_volume, sphere_rig)
+                           fma32, mesh_shells, signed_volume, sphere_rig)
 
 
 # ------------------------------------------------------------------ Sec. II-B-1
@@ -77,6 +77,78 @@ def test_pixel_floor_is_exact():
         q32 = np.float32(x) / np.float32(w)
         hits += int(np.floor(q32) != fl)
     assert hits > 0          # binary32 rounding does cross integers on these inputs
+
+
+def test_fma32_is_correctly_rounded():
+    """The numpy fused multiply-add used by the projection pins, against
+    exact rational arithmetic: random operands, sums that cancel, and sums
+    whose binary64 rounding lands exactly halfway between two binary32
+    numbers (where rounding twice would be wrong)."""
+    from fractions import Fraction
+    rng = np.random.default_rng(6)
+    n = 3000
+    a = (rng.standard_normal(n) * 10.0 ** rng.integers(-3, 4, n)).astype(np.float32)
+    b = (rng.standard_normal(n) * 10.0 ** rng.integers(-3, 4, n)).astype(np.float32)
+    c = (rng.standard_normal(n) * 10.0 ** rng.integers(-3, 4, n)).astype(np.float32)
+    c[: n // 3] = (-(a[: n // 3].astype(np.float64) * b[: n // 3])).astype(np.float32)   # cancellation
+    # a b = +-(2^-24 - 2^-60) and c = 2^q (1 + k 2^-23): the exact sum lies 2^-60 2^q
+    # off a binary32 halfway point, which binary64 cannot hold
+    k = np.arange(64)
+    q = rng.integers(-4, 5, 64)
+    sg = np.where(k % 4 < 2, 1.0, -1.0)
+    a = np.concatenate([a, (2.0 ** (-12 + q) * (1 + 2.0 ** -18)).astype(np.float32)])
+    b = np.concatenate([b, (sg * 2.0 ** -12 * (1 - 2.0 ** -18)).astype(np.float32)])
+    c = np.concatenate([c, (2.0 ** q * (1 + k * 2.0 ** -23)).astype(np.float32)])
+    got = fma32(a, b, c)
+    twice = 0
+    for x, y, z, g in zip(a, b, c, got):
+        exact = Fraction(float(x)) * Fraction(float(y)) + Fraction(float(z))
+        lo = np.float32(float(exact))                  # within one binary32 step of the exact value
+        cands = [np.nextafter(lo, np.float32(-np.inf)), lo, np.nextafter(lo, np.float32(np.inf))]
+        dist = [abs(Fraction(float(v)) - exact) for v in cands]
+        near = [v for v, d in zip(cands, dist) if d == min(dist)]
+        want = near[0] if len(near) == 1 else [v for v in near if (v.view(np.uint32) & 1) == 0][0]
+        assert g == want, (x, y, z, g, want)
+        twice += np.float32(np.float64(x) * np.float64(y) + np.float64(z)) != want
+    assert twice > 0         # rounding the binary64 sum again is wrong on some of these
+
+
+def test_projection_is_fused_binary32():
+    """Each row of the projection is ((p3 + p2 Z) + p1 Y) + p0 X in three
+    fused multiply-adds (binary32), and the pixel is the floor of the exact
+    quotient.  Checked through the oracle's vote on a checkerboard
+    silhouette at points on rays through pixel corners (where one rounding
+    decides the pixel); the unfused order puts some of them in other pixels."""
+    from dataclasses import replace
+    from fractions import Fraction
+    from tests.helpers import project32
+    base = make_rig("judo")
+    rig = replace(base, P=base.P[:1], centre=base.centre[:1], width=base.width[:1], height=base.height[:1])
+    W, H = int(rig.width[0]), int(rig.height[0])
+    rng = np.random.default_rng(12)
+    m = 6000
+    uv = np.stack([rng.integers(0, W + 1, m).astype(float), rng.integers(0, H + 1, m).astype(float)], 1)
+    d = (base.R64[0].T @ (np.linalg.inv(base.K64[0]) @ np.concatenate([uv, np.ones((m, 1))], 1).T)).T
+    pts = (base.C64[0] + rng.uniform(2.0, 30.0, (m, 1)) * d).astype(np.float32)
+    yy, xx = np.mgrid[0:H, 0:W]
+    masks = ((xx + yy) % 2 == 0).astype(np.uint8)[None]
+    on, _ = Oracle(rig).points_on(masks, pts.astype(np.float64))
+
+    def vote(xp, wp, yp):
+        out = np.zeros(len(pts), np.uint8)
+        for i in range(len(pts)):
+            if not wp[i] > 0:
+                continue
+            px = math.floor(Fraction(float(xp[i])) / Fraction(float(wp[i])))
+            py = math.floor(Fraction(float(yp[i])) / Fraction(float(wp[i])))
+            out[i] = 0 <= px < W and 0 <= py < H and (px + py) % 2 == 0
+        return out
+    xp, yp, wp = project32(rig.P[0], pts[:, 0], pts[:, 1], pts[:, 2])
+    np.testing.assert_array_equal(np.asarray(on, np.uint8), vote(xp, wp, yp))
+    P = rig.P[0].astype(np.float32)
+    X, Y, Z = pts[:, 0], pts[:, 1], pts[:, 2]
+    ux, uy, uw = (((P[r, 0] * X + P[r, 1] * Y) + P[r, 2] * Z) + P[r, 3] for r in range(3))
+    assert int((vote(ux, uw, uy) != np.asarray(on, np.uint8)).sum()) > 0
 
 
 def test_out_of_image_policy():
