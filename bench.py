@@ -372,7 +372,7 @@ def run_ours(args):
     rig, masks, rgb, vps = make_batch(F, first_frame(rank, F), "cuda")
     mask_bytes, rgb_bytes = masks.numel(), rgb.numel()
     N, H, W = masks.shape[1:]
-    r = fvv.Rig(rig, max_slots=F, host_staging=0 if args.no_e2e else 1)
+    r = fvv.Rig(rig, max_slots=F, host_staging=0 if args.no_e2e else 2)   # 2: mask staging only
     slots = list(range(F))
     stream = torch.cuda.current_stream()
 
@@ -489,17 +489,18 @@ def run_ours(args):
                      rgb=torch.empty((c["n_verts"], 3), dtype=torch.uint8).pin_memory(),
                      cam=torch.empty((c["n_verts"],), dtype=torch.int32).pin_memory()) for c in cnt]
         vp_ = fvv._vp
-        # masks and RGB stay in pinned host memory: the packing kernel reads
-        # every mask byte over the host link, the colour kernel only the RGB
-        # pixels it needs (FVV_MAPPED_HOST)
+        # masks and RGB stay in pinned host memory: the masks are copied to
+        # the slots' staging by the copy engines (which need no SMs, so the
+        # copies overlap other groups' kernels), the colour kernel reads only
+        # the RGB pixels it needs (FVV_MAPPED_HOST)
         h2d = int(masks_h.numel())
         d2h = int(sum(sum(t.numel() * t.element_size() for t in o.values()) for o in outs))
 
-        # groups of frames on two alternating streams, so that one group's
-        # copies overlap another group's kernels (calls on disjoint slots may
-        # run concurrently)
-        E2E_GROUP = 16
-        e2e_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        # groups of frames on three rotating streams, so that one group's
+        # copies (copy engines) overlap the other groups' kernels (calls on
+        # disjoint slots may run concurrently)
+        E2E_GROUP, E2E_STREAMS = 8, 3
+        e2e_streams = [torch.cuda.Stream() for _ in range(E2E_STREAMS)]
         groups = [slots[g:g + E2E_GROUP] for g in range(0, F, E2E_GROUP)]
 
         def e2e_step():
@@ -507,7 +508,7 @@ def run_ours(args):
             # so the next group is queued before the previous one is read back
             def compute(grp, st):
                 with torch.cuda.stream(st):
-                    r.upload_silhouettes_batch(grp, masks_h[grp[0]:grp[-1] + 1], stream=st, in_place=True)
+                    r.upload_silhouettes_batch(grp, masks_h[grp[0]:grp[-1] + 1], stream=st)
                     r.reconstruct(grp, stream=st)
                     r.colour(grp, rgb_h[grp[0]:grp[-1] + 1], vps[grp[0]:grp[-1] + 1], stream=st, in_place=True)
 
@@ -519,10 +520,10 @@ def run_ours(args):
                                                        vp_(o["cam"].data_ptr()), 0, fvv._stream(st)), r.ptr)
             pending = []
             for gi, grp in enumerate(groups):
-                st = e2e_streams[gi % 2]
+                st = e2e_streams[gi % E2E_STREAMS]
                 compute(grp, st)
                 pending.append((grp, st))
-                if len(pending) == 2:
+                if len(pending) == E2E_STREAMS:
                     read_back(*pending.pop(0))
             for grp, st in pending:
                 read_back(grp, st)
@@ -539,11 +540,11 @@ def run_ours(args):
         dt = max_over_ranks(dt, world, "cuda")
         e2e = {"value": job_rate(world, F, dt), "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": ks, "results_match_device": bool(ok),
-               "pipelining": f"{len(groups)} groups of {E2E_GROUP} frames on 2 alternating streams, each group read "
-                             "back while the next one runs",
-               "inputs": f"{masks_h.numel() / 1e9:.2f} GB of pinned host masks per step read in full by the "
-                         f"packing kernel; {rgb_h.numel() / 1e9:.2f} GB of pinned host RGB read in place by the "
-                         "colour kernel (only the pixels it needs cross the host link)"}
+               "pipelining": f"{len(groups)} groups of {E2E_GROUP} frames on {E2E_STREAMS} rotating streams, "
+                             f"each group read back while the next {E2E_STREAMS - 1} run",
+               "inputs": f"{masks_h.numel() / 1e9:.2f} GB of pinned host masks per step copied by the copy engines "
+                         f"into the slots' staging; {rgb_h.numel() / 1e9:.2f} GB of pinned host RGB read in place "
+                         "by the colour kernel (only the pixels it needs cross the host link)"}
 
     S = min(args.cpu_frames, F)
     cpu_sample = (masks[:S].cpu().numpy(), rgb[:S].cpu().numpy(), vps[:S])
