@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--serve-requests", type=int, default=1200,
                     help="requests of the serving leg (4 rigs at 30 Hz each; 0 skips it)")
     ap.add_argument("--serve-pool", type=int, default=8, help="frames per rig in the serving pool")
+    ap.add_argument("--serve-masks", choices=("in_place", "copies"), default="in_place",
+                    help="serving: pinned masks read in place by the packing kernel, or copied by the copy engines")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-cpu", action="store_true")
@@ -299,9 +301,10 @@ def run_serving(args, rank):
                              viewpoints=np.stack([f.viewpoint for f in frames])))
         del frames
         torch.cuda.empty_cache()
-    srv = Server(pools, budget_bytes=40 << 30)
+    srv = Server(pools, budget_bytes=40 << 30, mask_copies=args.serve_masks == "copies")
     try:
-        out = {"rigs": [c for c, _ in SERVE_RIGS], "slots": srv.slots, "budget_gb": 40, "offered_fps": 4 * 30.0}
+        out = {"rigs": [c for c, _ in SERVE_RIGS], "slots": srv.slots, "budget_gb": 40, "offered_fps": 4 * 30.0,
+               "masks": args.serve_masks}
         warm = poisson_schedule(len(pools), 30.0, 40, seed=7, pool_sizes=[args.serve_pool] * len(pools))
         srv.run(warm, time_scale=1000.0)
         reqs = poisson_schedule(len(pools), 30.0, args.serve_requests, seed=1903,

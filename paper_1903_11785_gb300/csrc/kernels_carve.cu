@@ -2,11 +2,12 @@
 // visual hulls (Sec. II-B-1 and II-B-3).
 //
 // Silhouettes are kept as 1 bit per pixel (a 1080p camera is 260 KB, a
-// 16-camera frame 4 MB, so a frame's silhouettes stay in L2).  A carve warp
-// owns one 32-voxel word of the occupancy bitset: lane i tests voxel 32w+i,
-// the warp walks the cameras in index order and stops as soon as a ballot
-// shows no lane is still occupied, so the warp's loads stay coherent (the 32
-// voxels of a row project close together) and empty space costs one camera.
+// 16-camera frame 4 MB, so a frame's silhouettes stay in L2).  A coarse
+// carve warp takes a row of the occupancy bitset one 32-voxel word at a time:
+// lane i tests voxel 32w+i, the warp walks the cameras in index order and
+// stops as soon as a ballot shows no lane is still occupied, so the warp's
+// loads stay coherent (the 32 voxels of a word project close together) and
+// empty space costs one camera.
 #include "fvv_device.cuh"
 
 namespace fvv {
@@ -68,27 +69,29 @@ __global__ void __launch_bounds__(256) k_coarse_carve(const __grid_constant__ Ca
     const uint32_t* __restrict__ sil = slot_ptr<uint32_t>(L, slot, L.sil);
     uint32_t* bits = slot_ptr<uint32_t>(L, slot, L.coarse);
     int* parent = slot_ptr<int>(L, slot, L.parent);
-    const uint32_t nwords = (uint32_t)g.nz * (uint32_t)g.ny * (uint32_t)g.nxw;
+    const uint32_t nrows = (uint32_t)g.nz * (uint32_t)g.ny;
     const int lane = threadIdx.x & 31;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     uint32_t tests = 0, on_count = 0;
-    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords; w += nwarps) {
-        const uint32_t row = w / (uint32_t)g.nxw;
-        const int wx = (int)(w - row * (uint32_t)g.nxw);
+    // a warp takes a whole row (y, z) and walks its words, so the row is
+    // decoded once and Y, Z are formed once
+    for (uint32_t row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < nrows; row += nwarps) {
         const int y = (int)(row % (uint32_t)g.ny), z = (int)(row / (uint32_t)g.ny);
-        const int x = wx * 32 + lane;
-        const float X = fadd(g.o[0], fmul(fadd((float)x, 0.5f), g.sc));
         const float Y = fadd(g.o[1], fmul(fadd((float)y, 0.5f), g.sc));
         const float Z = fadd(g.o[2], fmul(fadd((float)z, 0.5f), g.sc));
-        const bool on = warp_test<NC>(cams, sil, X, Y, Z, x < g.nx, tests);
-        const uint32_t word = __ballot_sync(kFull, on);
-        if (on) {
-            const int Lin = (int)(row * (uint32_t)g.nx) + x;
-            parent[Lin] = Lin;
-        }
-        if (lane == 0) {
-            bits[w] = word;
-            on_count += __popc(word);
+        for (int wx = 0; wx < g.nxw; ++wx) {
+            const int x = wx * 32 + lane;
+            const float X = fadd(g.o[0], fmul(fadd((float)x, 0.5f), g.sc));
+            const bool on = warp_test<NC>(cams, sil, X, Y, Z, x < g.nx, tests);
+            const uint32_t word = __ballot_sync(kFull, on);
+            if (on) {
+                const int Lin = (int)(row * (uint32_t)g.nx) + x;
+                parent[Lin] = Lin;
+            }
+            if (lane == 0) {
+                bits[row * (uint32_t)g.nxw + (uint32_t)wx] = word;
+                on_count += __popc(word);
+            }
         }
     }
     const unsigned long long t = block_sum<unsigned long long>(tests, sh_t);
@@ -219,7 +222,7 @@ template <int NC, bool ABSTAIN>
 __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, const SmemCam* sc, int ncam,
                                            uint32_t ntiles, int nrois, const DRoi* rois,
                                            const uint32_t* __restrict__ sil, uint32_t* fine,
-                                           uint32_t& tests, uint32_t& reads) {
+                                           uint64_t* tile_fg, uint32_t& tests, uint32_t& reads) {
     const int lane = threadIdx.x & 31, half = lane & 1;
     const int xi = lane & 3, yi = (lane >> 2) & 1, zi = lane >> 3;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -271,6 +274,7 @@ __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, co
             fgm |= (uint64_t)even_bits(__ballot_sync(kFull, fg)) << cg;
             bgm |= (uint64_t)even_bits(__ballot_sync(kFull, bg)) << cg;
         }
+        if (lane == 0) tile_fg[t] = fgm;      // for the bisection of the edges inside the tile
         // the tile's samples, one sub-tile of 4 x 2 x 4 (one per lane) at a time
         const int nb = bgm ? __ffsll((long long)bgm) - 1 : ncam;
         const uint64_t before = nb >= 64 ? ~0ull : (1ull << nb) - 1ull;
@@ -345,12 +349,13 @@ __global__ void __launch_bounds__(256) k_fine_carve(const __grid_constant__ CamS
     const DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
     const uint32_t* __restrict__ sil = slot_ptr<uint32_t>(L, slot, L.sil);
     uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
+    uint64_t* tile_fg = slot_ptr<uint64_t>(L, slot, L.tile_fg);
     // per-lane counts stay below 2^30 (at most 2^24 tiles of 64 tests each)
     uint32_t tests = 0, reads = 0;
     if (cams.oob == FVV_OOB_ABSTAIN)
-        fine_tiles<NC, true>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tests, reads);
+        fine_tiles<NC, true>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tile_fg, tests, reads);
     else
-        fine_tiles<NC, false>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tests, reads);
+        fine_tiles<NC, false>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tile_fg, tests, reads);
     const unsigned long long t = block_sum<unsigned long long>((unsigned long long)tests, sh_t);
     const unsigned long long rd = block_sum<unsigned long long>((unsigned long long)reads, sh_t);
     if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_fine, t);
@@ -405,9 +410,9 @@ cudaError_t launch_pack(const CamSet& cams, const Layout& L, int n_frames, const
 
 cudaError_t launch_coarse_carve(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,
                                 const Tuning& tu, cudaStream_t st) {
-    const long long words = (long long)g.nz * g.ny * g.nxw;
+    const long long rows = (long long)g.nz * g.ny;    // a warp per row
     const int th = tu.threads[FVV_TUNE_COARSE];
-    const int gx = tuned_grid(tu, FVV_TUNE_COARSE, sms, sl.n, words * 32);
+    const int gx = tuned_grid(tu, FVV_TUNE_COARSE, sms, sl.n, rows * 32);
 #define FVV_LAUNCH(NC) k_coarse_carve<NC><<<dim3(gx, sl.n), th, 0, st>>>(cams, g, L, sl)
     FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH

@@ -50,12 +50,13 @@ class RigPool:
     viewpoints: np.ndarray  # (F,3) float32
 
 
-def _staging(pool) -> int:
+def _staging(pool, mask_copies: bool = False) -> int:
     """Host staging a rig's slots need: none when the pool's masks and RGB are
-    pinned (read in place by the kernels), masks only when only the RGB is,
-    else masks and RGB."""
+    pinned and the masks are read in place by the packing kernel, masks only
+    when the RGB is pinned and the masks are copied (mask_copies, or not
+    pinned), else masks and RGB."""
     if _rgb_pinned(pool):
-        return 0 if _masks_pinned(pool) else 2
+        return 0 if _masks_pinned(pool) and not mask_copies else 2
     return 1
 
 
@@ -90,11 +91,11 @@ def poisson_schedule(n_rigs, rate_hz, n_requests, seed, pool_sizes):
 
 
 class _RigState:
-    def __init__(self, pool: RigPool, n_slots: int, n_streams: int, caps: dict):
+    def __init__(self, pool: RigPool, n_slots: int, n_streams: int, caps: dict, mask_copies: bool):
         self.pool = pool
         self.rgb_in_place = _rgb_pinned(pool)
-        self.masks_in_place = self.rgb_in_place and _masks_pinned(pool)
-        self.rig = fvv.Rig(pool.scene_rig, max_slots=n_slots, host_staging=_staging(pool), **caps)
+        self.masks_in_place = _staging(pool, mask_copies) == 0
+        self.rig = fvv.Rig(pool.scene_rig, max_slots=n_slots, host_staging=_staging(pool, mask_copies), **caps)
         self.free = list(range(n_slots))
         self.queue = []            # waiting requests
         self.pending = []          # admitted, not yet issued
@@ -104,18 +105,22 @@ class _RigState:
 
 
 class Server:
-    def __init__(self, pools, budget_bytes: int, max_slots_per_rig: int = 32, n_streams: int = 2, caps=None):
-        """Give every rig an equal share of the memory budget, in whole slots."""
+    def __init__(self, pools, budget_bytes: int, max_slots_per_rig: int = 32, n_streams: int = 2, caps=None,
+                 mask_copies: bool = False):
+        """Give every rig an equal share of the memory budget, in whole slots.
+        mask_copies: pinned masks are copied to the slots by the copy engines
+        (which need no SMs) instead of being read in place by the packing
+        kernel."""
         caps = dict(caps or {})
         share = budget_bytes // max(1, len(pools))
         self.rigs = []
         self.slots = []
         for p in pools:
-            n = int(min(max_slots_per_rig, share // slot_bytes(p.scene_rig, _staging(p), **caps)))
+            n = int(min(max_slots_per_rig, share // slot_bytes(p.scene_rig, _staging(p, mask_copies), **caps)))
             if n < 1:
                 raise MemoryError("memory budget too small for one slot of a rig")
             self.slots.append(n)
-            self.rigs.append(_RigState(p, n, n_streams, caps))
+            self.rigs.append(_RigState(p, n, n_streams, caps, mask_copies))
 
     def close(self):
         for r in self.rigs:

@@ -32,14 +32,15 @@ def _alone(rig, fr, caps):
         r.close()
 
 
-def test_served_results_equal_alone():
+@pytest.mark.parametrize("mask_copies", [False, True])
+def test_served_results_equal_alone(mask_copies):
     from paper_1903_11785_gb300.build import build
     build()
     from paper_1903_11785_gb300.serve import Server, poisson_schedule, summarize
     caps = dict(max_fine_words=1 << 18, max_verts=1 << 19, max_tris=1 << 20)
     pa, fa = _pool("tiny", 4)
     pb, fb = _pool("hd720", 3)
-    srv = Server([pa, pb], budget_bytes=3 << 30, max_slots_per_rig=3, caps=caps)
+    srv = Server([pa, pb], budget_bytes=3 << 30, max_slots_per_rig=3, caps=caps, mask_copies=mask_copies)
     got = {}
 
     def on_done(rs, q):
