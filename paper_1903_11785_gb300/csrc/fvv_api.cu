@@ -235,7 +235,7 @@ fvv_status make_plan(const fvv_rig_desc* d, const fvv_recon_params* p, Plan& pl,
     take(L.vrec, (size_t)mv * 8);
     take(L.verts, (size_t)mv * 12);
     take(L.tris, (size_t)mt * 12);
-    take(L.tcen, (size_t)mt * 12);
+    take(L.tsoup, (size_t)mt * 48);
     take(L.trec, (size_t)mt * 8);
     take(L.vrgb, (size_t)mv * 3);
     take(L.vcam, (size_t)mv * 4);

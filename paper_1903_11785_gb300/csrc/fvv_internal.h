@@ -109,7 +109,8 @@ struct Layout {
     size_t vrec;                // uint64 vertex records, max_verts
     size_t verts;               // float x3, max_verts
     size_t tris;                // uint32 x3, max_tris
-    size_t tcen;                // float x3 triangle centroids, max_tris
+    size_t tsoup;               // float4 x3 per triangle: its vertices and centroid
+                                // (v0 xyz, v1 xyz, v2 xyz, centroid xyz), max_tris
     size_t trec;                // uint64 triangle records (word, cell, case, triangle, ROI), max_tris
     size_t vrgb;                // uint8 x3, max_verts
     size_t vcam;                // int32, max_verts

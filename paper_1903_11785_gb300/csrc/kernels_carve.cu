@@ -222,7 +222,7 @@ template <int NC, bool ABSTAIN>
 __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, const SmemCam* sc, int ncam,
                                            uint32_t ntiles, int nrois, const DRoi* rois,
                                            const uint32_t* __restrict__ sil, uint32_t* fine,
-                                           uint64_t* tile_fg, uint32_t& tests, uint32_t& reads) {
+                                           uint32_t& tests, uint32_t& reads) {
     const int lane = threadIdx.x & 31, half = lane & 1;
     const int xi = lane & 3, yi = (lane >> 2) & 1, zi = lane >> 3;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -274,7 +274,6 @@ __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, co
             fgm |= (uint64_t)even_bits(__ballot_sync(kFull, fg)) << cg;
             bgm |= (uint64_t)even_bits(__ballot_sync(kFull, bg)) << cg;
         }
-        if (lane == 0) tile_fg[t] = fgm;      // for the bisection of the edges inside the tile
         // the tile's samples, one sub-tile of 4 x 2 x 4 (one per lane) at a time
         const int nb = bgm ? __ffsll((long long)bgm) - 1 : ncam;
         const uint64_t before = nb >= 64 ? ~0ull : (1ull << nb) - 1ull;
@@ -349,13 +348,12 @@ __global__ void __launch_bounds__(256) k_fine_carve(const __grid_constant__ CamS
     const DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
     const uint32_t* __restrict__ sil = slot_ptr<uint32_t>(L, slot, L.sil);
     uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
-    uint64_t* tile_fg = slot_ptr<uint64_t>(L, slot, L.tile_fg);
     // per-lane counts stay below 2^30 (at most 2^24 tiles of 64 tests each)
     uint32_t tests = 0, reads = 0;
     if (cams.oob == FVV_OOB_ABSTAIN)
-        fine_tiles<NC, true>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tile_fg, tests, reads);
+        fine_tiles<NC, true>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tests, reads);
     else
-        fine_tiles<NC, false>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tile_fg, tests, reads);
+        fine_tiles<NC, false>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tests, reads);
     const unsigned long long t = block_sum<unsigned long long>((unsigned long long)tests, sh_t);
     const unsigned long long rd = block_sum<unsigned long long>((unsigned long long)reads, sh_t);
     if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_fine, t);

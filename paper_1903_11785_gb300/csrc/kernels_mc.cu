@@ -589,7 +589,7 @@ __global__ void __launch_bounds__(256) k_mc_triangles(const __grid_constant__ La
     const uint64_t* trec = slot_ptr<uint64_t>(L, slot, L.trec);
     uint32_t* tris = slot_ptr<uint32_t>(L, slot, L.tris);
     const float* verts = slot_ptr<float>(L, slot, L.verts);
-    float* tcen = slot_ptr<float>(L, slot, L.tcen);
+    float4* tsoup = slot_ptr<float4>(L, slot, L.tsoup);
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         const uint64_t rec = trec[t];
         const uint32_t w = (uint32_t)(rec & 0x3FFFFFFu);
@@ -618,12 +618,18 @@ __global__ void __launch_bounds__(256) k_mc_triangles(const __grid_constant__ La
         tris[3 * (size_t)t + 0] = id[0];
         tris[3 * (size_t)t + 1] = id[1];
         tris[3 * (size_t)t + 2] = id[2];
+        // the triangle's vertices and centroid ((v0 + v1) + v2) / 3, stored
+        // together for the kernels that draw it
+        float v[12];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const float s = fadd(fadd(verts[3 * (size_t)id[0] + d], verts[3 * (size_t)id[1] + d]),
-                                 verts[3 * (size_t)id[2] + d]);
-            tcen[3 * (size_t)t + d] = __fdiv_rn(s, 3.0f);
-        }
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) v[3 * q + d] = verts[3 * (size_t)id[q] + d];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[9 + d] = __fdiv_rn(fadd(fadd(v[d], v[3 + d]), v[6 + d]), 3.0f);
+        tsoup[3 * (size_t)t + 0] = make_float4(v[0], v[1], v[2], v[3]);
+        tsoup[3 * (size_t)t + 1] = make_float4(v[4], v[5], v[6], v[7]);
+        tsoup[3 * (size_t)t + 2] = make_float4(v[8], v[9], v[10], v[11]);
     }
 }
 

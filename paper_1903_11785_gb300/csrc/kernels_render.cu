@@ -206,22 +206,16 @@ __global__ void __launch_bounds__(256) k_zbuffer(const __grid_constant__ CamSet 
     const Cam& c = cams.c[blockIdx.y];
     const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
     const uint32_t nt = info->n_words ? info->n_tris : 0u;
-    const float* verts = slot_ptr<float>(L, slot, L.verts);
-    const uint32_t* tris = slot_ptr<uint32_t>(L, slot, L.tris);
-    const float* tcen = slot_ptr<float>(L, slot, L.tcen);
+    const float4* tsoup = slot_ptr<float4>(L, slot, L.tsoup);
     uint32_t* depth = slot_ptr<uint32_t>(L, slot, L.depth);
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-        float X[3], Y[3], Z[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const uint32_t vi = __ldg(tris + 3 * (size_t)t + j);
-            X[j] = __ldg(verts + 3 * (size_t)vi);
-            Y[j] = __ldg(verts + 3 * (size_t)vi + 1);
-            Z[j] = __ldg(verts + 3 * (size_t)vi + 2);
-        }
-        const float dx = fsub(__ldg(tcen + 3 * (size_t)t), c.C[0]);
-        const float dy = fsub(__ldg(tcen + 3 * (size_t)t + 1), c.C[1]);
-        const float dz = fsub(__ldg(tcen + 3 * (size_t)t + 2), c.C[2]);
+        const float4 r0 = __ldg(tsoup + 3 * (size_t)t), r1 = __ldg(tsoup + 3 * (size_t)t + 1);
+        const float X[3] = {r0.x, r0.w, r1.z}, Y[3] = {r0.y, r1.x, r1.w};
+        const float4 r2 = __ldg(tsoup + 3 * (size_t)t + 2);
+        const float Z[3] = {r0.z, r1.y, r2.x};
+        const float dx = fsub(r2.y, c.C[0]);
+        const float dy = fsub(r2.z, c.C[1]);
+        const float dz = fsub(r2.w, c.C[2]);
         const uint32_t d2 = __float_as_uint(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
         // the buffer keeps the minimum of the squared distance: sqrt is
         // monotone, so the square root of that minimum is the minimum
@@ -327,21 +321,14 @@ __global__ void __launch_bounds__(256) k_view_raster(const __grid_constant__ Lay
     const Cam& v = va.v;
     const SlotInfo* info = slot_ptr<SlotInfo>(L, va.slot, L.info);
     const uint32_t nt = info->n_words ? info->n_tris : 0u;
-    const float* verts = slot_ptr<float>(L, va.slot, L.verts);
-    const uint32_t* tris = slot_ptr<uint32_t>(L, va.slot, L.tris);
-    const float* tcen = slot_ptr<float>(L, va.slot, L.tcen);
+    const float4* tsoup = slot_ptr<float4>(L, va.slot, L.tsoup);
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-        float X[3], Y[3], Z[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const uint32_t vi = __ldg(tris + 3 * (size_t)t + j);
-            X[j] = __ldg(verts + 3 * (size_t)vi);
-            Y[j] = __ldg(verts + 3 * (size_t)vi + 1);
-            Z[j] = __ldg(verts + 3 * (size_t)vi + 2);
-        }
-        const float dx = fsub(__ldg(tcen + 3 * (size_t)t), v.C[0]);
-        const float dy = fsub(__ldg(tcen + 3 * (size_t)t + 1), v.C[1]);
-        const float dz = fsub(__ldg(tcen + 3 * (size_t)t + 2), v.C[2]);
+        const float4 r0 = __ldg(tsoup + 3 * (size_t)t), r1 = __ldg(tsoup + 3 * (size_t)t + 1),
+                     r2 = __ldg(tsoup + 3 * (size_t)t + 2);
+        const float X[3] = {r0.x, r0.w, r1.z}, Y[3] = {r0.y, r1.x, r1.w}, Z[3] = {r0.z, r1.y, r2.x};
+        const float dx = fsub(r2.y, v.C[0]);
+        const float dy = fsub(r2.z, v.C[1]);
+        const float dz = fsub(r2.w, v.C[2]);
         const unsigned long long k =
             (unsigned long long)__float_as_uint(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz))) << 32 | t;
         raster_tri(v, X, Y, Z, [&](size_t pix) {
@@ -364,16 +351,15 @@ __global__ void __launch_bounds__(256) k_view_shade(const __grid_constant__ CamS
     rank_cameras(cams, va.v.C, rank_cam);
     __syncthreads();
     const uint32_t* depth = slot_ptr<uint32_t>(L, va.slot, L.depth);
-    const float* tcen = slot_ptr<float>(L, va.slot, L.tcen);
+    const float4* tsoup = slot_ptr<float4>(L, va.slot, L.tsoup);
     const size_t npix = (size_t)va.v.W * (unsigned)va.v.H;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (size_t)gridDim.x * blockDim.x) {
         const unsigned long long k = key[i];
         uint8_t col[3] = {0, 0, 0};
         int chosen = -1;
         if (k != ~0ull) {
-            const size_t t = (size_t)(uint32_t)k;
-            chosen = colour_point(cams, rank_cam, depth, va.rgb, g.t_v, __ldg(tcen + 3 * t), __ldg(tcen + 3 * t + 1),
-                                  __ldg(tcen + 3 * t + 2), col);
+            const float4 r2 = __ldg(tsoup + 3 * (size_t)(uint32_t)k + 2);   // (v2 z, centroid xyz)
+            chosen = colour_point(cams, rank_cam, depth, va.rgb, g.t_v, r2.y, r2.z, r2.w, col);
         }
         out_rgb[3 * i] = col[0];
         out_rgb[3 * i + 1] = col[1];

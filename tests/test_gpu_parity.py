@@ -129,6 +129,32 @@ def test_batched_upload_each_bit_exact(mode):
         compare(rig, fr, g)
 
 
+@pytest.mark.parametrize("W", [96, 100])
+def test_batched_upload_spans_launches(W):
+    """64 cameras (the most a rig takes), so one packing launch holds 32
+    frames: 40 frames in one call, slots in reverse order, take two launches.
+    Every slot's silhouette bits equal its masks packed 32 pixels per word
+    (W = 96: whole 16-byte loads; W = 100: ragged rows)."""
+    from paper_1903_11785_gb300 import fvv
+    n, H, F = 64, 48, 40
+    cs = [(6.0 * math.cos(2 * math.pi * k / n), 6.0 * math.sin(2 * math.pi * k / n), 3.0 + 0.3 * (k % 3))
+          for k in range(n)]
+    rig = _make_rig(f"ring64w{W}", cs, [(0, 0, 0.9)] * n, 60.0, W, H, _gen(f"ring64w{W}/rig"),
+                    (-1.0, -1.0, 0.0), (1.0, 1.0, 2.0), 0.1, 0.05, 2)
+    g = torch.Generator().manual_seed(W)
+    masks = (torch.rand((F, n, H, W), generator=g) < 0.3).to(torch.uint8)
+    r = fvv.Rig(rig, max_slots=F, host_staging=0, max_fine_words=1 << 12, max_verts=1 << 12, max_tris=1 << 12)
+    try:
+        slots = list(range(F))[::-1]
+        r.upload_silhouettes_batch(slots, masks.cuda())
+        torch.cuda.synchronize()
+        for j, s in enumerate(slots):
+            bits = r.debug(s, fvv.FVV_DEBUG_SIL_BITS).cpu().numpy().view(np.uint32)
+            np.testing.assert_array_equal(unpack_rows(bits, (n, H), W), masks[j].numpy())
+    finally:
+        r.close()
+
+
 def test_batched_upload_rejects_bad_arguments():
     from paper_1903_11785_gb300 import fvv
     rig = make_rig("tiny")
