@@ -44,14 +44,21 @@ WORKLOAD = ("volleyball-shaped frames: 16 cameras 1920x1080 (f=1800), 12 players
 # FP32 floating-point operations of one camera test by definition: x', y', w'
 # (9 fused multiply-adds, 2 operations each), u and v (2 divisions), two floors.
 FLOPS_PER_TEST = 22
+# FP32 floating-point operations of one (triangle, camera) pair of the depth
+# images by definition: three vertex projections (27 fused multiply-adds), the
+# squared centroid distance (3 subtractions, 3 multiplications, 2 additions),
+# u and v of the three vertices (6 divisions).  The per-pixel edge tests are
+# not counted (they depend on how many pixel centres a triangle covers).
+FLOPS_PER_PAIR = 68
 # FP32 peak of GB300: 152 SMs x 128 FP32 lanes x 2 (a fused multiply-add per
 # lane per clock) x 2.07 GHz (maximum SM clock).
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# DRAM bytes (read + write) per frame of each hull kernel, from one ncu capture
-# of a 4-frame launch of the current kernels (profiles/k_fine_carve_volleyball_batch4.md,
-# profiles/hull_and_depth_kernels_volleyball_batch4.md), scaled to a launch by
-# its frame count.  None for a kernel changed since that capture.
-DRAM_BYTES_PER_FRAME = {"fine": 7.212544e6 / 4, "bisect": (17.208832e6 + 3584) / 4, "coarse": None}
+# DRAM bytes (read + write) per frame of each large kernel, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of a 4-frame launch of
+# the current kernels, scaled to a launch by its frame count.  None for a
+# kernel changed since that capture.
+DRAM_BYTES_PER_FRAME = {"fine": 7.212288e6 / 4, "bisect": (17.209856e6 + 15104) / 4,
+                        "coarse": (4.331008e6 + 7680) / 4, "depth": (185.491968e6 + 13.184512e6) / 4}
 
 
 def parse_args():
@@ -444,25 +451,34 @@ def run_ours(args):
     torch.cuda.synchronize()
     plain_fps = len(lat) / (sum(lat) / 1000.0)
 
-    # ---- per-stage times and roofline of the dominant kernel
+    # ---- per-stage times and the rooflines of the four large kernels; the
+    # `roofline` object is the one of the stage that takes longest
     per_step = {k: v[0] / args.steps for k, v in stages.items()}
     launches = {k: v[1] / args.steps for k, v in stages.items()}
-    work = {  # algorithmic FP32 operations per step
-        "coarse": tsum["tests_coarse"] * FLOPS_PER_TEST,
-        "fine": tsum["tests_fine"] * FLOPS_PER_TEST,
-        "bisect": tsum["tests_bisect"] * FLOPS_PER_TEST + tsum["n_verts"] * 6 * (rig.bisect_steps + 1),
+    units = {  # algorithmic units per step, and FP32 operations per unit
+        "coarse": (tsum["tests_coarse"], FLOPS_PER_TEST, "camera tests"),
+        "fine": (tsum["tests_fine"], FLOPS_PER_TEST, "camera tests"),
+        "bisect": (tsum["tests_bisect"] + tsum["n_verts"] * 6 * (rig.bisect_steps + 1) / FLOPS_PER_TEST,
+                   FLOPS_PER_TEST, "camera tests (+ midpoints as test equivalents)"),
+        "depth": (tsum["n_tris"] * rig.n_cams, FLOPS_PER_PAIR, "(triangle, camera) pairs"),
     }
-    dom = max(work, key=lambda k: per_step[k])
-    launch_ms = per_step[dom] / max(launches[dom], 1)
-    achieved = work[dom] / max(launches[dom], 1) / (launch_ms / 1000.0) / 1e12
-    traffic = DRAM_BYTES_PER_FRAME.get(dom)
-    roofline = {"bound": "alu", "kernel": {"coarse": "k_coarse_carve", "fine": "k_fine_carve",
-                                           "bisect": "k_bisect"}[dom],
-                "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / ALU_PEAK_TFLOPS,
+    kernel_of = {"coarse": "k_coarse_carve", "fine": "k_fine_carve", "bisect": "k_bisect", "depth": "k_zbuffer"}
+
+    def alu_roofline(k):
+        n_units, fpu, what = units[k]
+        launch_ms = per_step[k] / max(launches[k], 1)
+        achieved = n_units * fpu / max(launches[k], 1) / (launch_ms / 1000.0) / 1e12
+        traffic = DRAM_BYTES_PER_FRAME.get(k)
+        return {"bound": "alu", "kernel": kernel_of[k], "achieved": achieved, "peak": ALU_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / ALU_PEAK_TFLOPS,
                 "traffic": traffic * F if traffic is not None else None,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz (unit counts, max clock)",
-                "launch_ms": launch_ms, "tests_per_launch": tsum["tests_" + dom] if dom != "bisect" else
-                tsum["tests_bisect"], "flops_per_test": FLOPS_PER_TEST}
+                "launch_ms": launch_ms, "units_per_launch": n_units / max(launches[k], 1), "unit_of_work": what,
+                "flops_per_unit": fpu}
+    rooflines = {k: alu_roofline(k) for k in units}
+    roofline = rooflines[max(units, key=lambda k: per_step[k])]
+    dom = max(("coarse", "fine", "bisect"), key=lambda k: per_step[k])   # the largest hull kernel
+    launch_ms = rooflines[dom]["launch_ms"]
 
     # ---- memory side: the silhouette words the dominant kernel actually
     # read (the fine hull and the bisection settle most tests for a whole tile
@@ -472,7 +488,7 @@ def run_ours(args):
     reads_dom = {"coarse": tsum["tests_coarse"], "fine": tsum["lookups_fine"], "bisect": tsum["lookups_bisect"]}[dom]
     gathers = reads_dom / max(launches[dom], 1) / (launch_ms / 1000.0)
     tests_rate = tsum["tests_" + dom] / max(launches[dom], 1) / (launch_ms / 1000.0)
-    l2_roofline = {"bound": "l2", "kernel": roofline["kernel"], "achieved": gathers / 1e9,
+    l2_roofline = {"bound": "l2", "kernel": kernel_of[dom], "achieved": gathers / 1e9,
                    "peak": l2["gather_Gwords_per_s"], "unit": "G silhouette-word gathers/s",
                    "frac": gathers / 1e9 / l2["gather_Gwords_per_s"],
                    "algorithmic_tests_G_per_s": tests_rate / 1e9,
@@ -534,7 +550,7 @@ def run_ours(args):
 
         e2e_step()
         ok = all(torch.equal(o["verts"], r.results(i)["verts"].cpu()) for i, o in zip(slots[:2], outs[:2]))
-        ks = max(1, min(args.steps, 3))
+        ks = max(1, min(args.steps, 10))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(ks):
@@ -605,7 +621,8 @@ def run_ours(args):
                       "latency_ms_p99": float(np.percentile(lat, 99)), "frames": len(lat), "cuda_graph": True},
             "tuning": tuning,
             "stages_ms_per_frame": {k: v / F for k, v in per_step.items()},
-            "roofline": roofline, "l2_roofline": l2_roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "gpu_launches": n_launch,
+            "roofline": roofline, "rooflines": {kernel_of[k]: v for k, v in rooflines.items()},
+            "l2_roofline": l2_roofline, "cpu_baseline": cpu, "e2e": e2e, "serving": serving, "gpu_launches": n_launch,
             "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
