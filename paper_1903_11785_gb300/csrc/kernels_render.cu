@@ -195,36 +195,101 @@ __device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const f
     if (raster_setup(c, X, Y, Z, s)) raster_pixels(c, s, sink);
 }
 
+// A warp's queue of (triangle, camera) pairs whose candidate box is not
+// empty: the homogeneous vertices, the box and the squared distance.
+constexpr int kZQueue = 64;
+struct ZQueue {
+    float xh[3][kZQueue], yh[3][kZQueue], wh[3][kZQueue];
+    int x0[kZQueue], x1[kZQueue], y0[kZQueue], y1[kZQueue];
+    uint32_t d2[kZQueue];
+};
+
+__device__ __forceinline__ void zq_put(ZQueue& q, int i, const TriSetup& s, uint32_t d2) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        q.xh[j][i] = s.xh[j];
+        q.yh[j][i] = s.yh[j];
+        q.wh[j][i] = s.wh[j];
+    }
+    q.x0[i] = s.x0;
+    q.x1[i] = s.x1;
+    q.y0[i] = s.y0;
+    q.y1[i] = s.y1;
+    q.d2[i] = d2;
+}
+
+// Eq. (4) for the queued pair i: its covered pixels keep the minimum of the
+// squared distance (sqrt is monotone, so the square root of that minimum is
+// the minimum distance itself, taken where the depth is read).
+__device__ __forceinline__ void zq_draw(const Cam& c, const ZQueue& q, int i, uint32_t* D) {
+    TriSetup s;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        s.xh[j] = q.xh[j][i];
+        s.yh[j] = q.yh[j][i];
+        s.wh[j] = q.wh[j][i];
+    }
+    s.x0 = q.x0[i];
+    s.x1 = q.x1[i];
+    s.y0 = q.y0[i];
+    s.y1 = q.y1[i];
+    const uint32_t d2 = q.d2[i];
+    raster_pixels(c, s, [&](size_t pix) {
+        uint32_t* p = D + pix;
+        if (__ldcg(p) > d2) atomicMin(p, d2);   // skip the atomic when already nearer
+    });
+}
+
 // Grid (blocks, cameras, slots): the camera is uniform over a block, so its
 // matrix is read through uniform registers, and blocks are issued frame by
-// frame, so one frame's depth images are worked on together.  One thread per
-// triangle; the centroid ((v0 + v1) + v2) / 3 was formed once per triangle
-// when the triangle was emitted.
+// frame, so one frame's depth images are worked on together.  A warp takes 32
+// triangles at a time, one per lane, and sets them up (raster_setup); the
+// centroid ((v0 + v1) + v2) / 3 was formed once per triangle when the
+// triangle was emitted.  About 70% of the pairs have no candidate pixel
+// centre, so the others go to a per-warp queue and are drawn 32 at a time,
+// one per lane, instead of by 30% of the lanes while the rest wait.
 __global__ void __launch_bounds__(256) k_zbuffer(const __grid_constant__ CamSet cams, const __grid_constant__ Layout L,
                                                  const __grid_constant__ SlotList sl) {
+    __shared__ ZQueue zq[8];   // one per warp (at most 256 threads)
     const int slot = sl.s[blockIdx.z];
     const Cam& c = cams.c[blockIdx.y];
     const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
     const uint32_t nt = info->n_words ? info->n_tris : 0u;
     const float4* tsoup = slot_ptr<float4>(L, slot, L.tsoup);
-    uint32_t* depth = slot_ptr<uint32_t>(L, slot, L.depth);
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-        const float4 r0 = __ldg(tsoup + 3 * (size_t)t), r1 = __ldg(tsoup + 3 * (size_t)t + 1);
-        const float X[3] = {r0.x, r0.w, r1.z}, Y[3] = {r0.y, r1.x, r1.w};
-        const float4 r2 = __ldg(tsoup + 3 * (size_t)t + 2);
-        const float Z[3] = {r0.z, r1.y, r2.x};
-        const float dx = fsub(r2.y, c.C[0]);
-        const float dy = fsub(r2.z, c.C[1]);
-        const float dz = fsub(r2.w, c.C[2]);
-        const uint32_t d2 = __float_as_uint(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
-        // the buffer keeps the minimum of the squared distance: sqrt is
-        // monotone, so the square root of that minimum is the minimum
-        // distance itself, taken where the depth is read
-        uint32_t* D = depth + c.pix_off;
-        raster_tri(c, X, Y, Z, [&](size_t pix) {
-            uint32_t* p = D + pix;
-            if (__ldcg(p) > d2) atomicMin(p, d2);   // skip the atomic when already nearer
-        });
+    uint32_t* D = slot_ptr<uint32_t>(L, slot, L.depth) + c.pix_off;
+    const int lane = threadIdx.x & 31;
+    ZQueue& q = zq[threadIdx.x >> 5];
+    int qn = 0;   // queued pairs, the same in every lane
+    uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    for (;;) {                                    // warp-uniform
+        const bool more = t0 < nt;
+        const uint32_t t = t0 + (uint32_t)lane;
+        TriSetup s;
+        uint32_t d2 = 0;
+        bool ok = false;
+        if (more && t < nt) {
+            const float4 r0 = __ldg(tsoup + 3 * (size_t)t), r1 = __ldg(tsoup + 3 * (size_t)t + 1);
+            const float X[3] = {r0.x, r0.w, r1.z}, Y[3] = {r0.y, r1.x, r1.w};
+            const float4 r2 = __ldg(tsoup + 3 * (size_t)t + 2);
+            const float Z[3] = {r0.z, r1.y, r2.x};
+            const float dx = fsub(r2.y, c.C[0]);
+            const float dy = fsub(r2.z, c.C[1]);
+            const float dz = fsub(r2.w, c.C[2]);
+            d2 = __float_as_uint(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
+            ok = raster_setup(c, X, Y, Z, s);
+        }
+        const unsigned m = __ballot_sync(kFull, ok);
+        if (ok) zq_put(q, qn + __popc(m & ((1u << lane) - 1u)), s, d2);
+        qn += __popc(m);                          // < 32 before, so < 64 now
+        __syncwarp();
+        if (qn >= 32 || (!more && qn > 0)) {      // draw the last (up to) 32 queued, one per lane
+            const int k = min(qn, 32);
+            qn -= k;
+            if (lane < k) zq_draw(c, q, qn + lane, D);
+            __syncwarp();                         // read before the slots are reused
+        }
+        if (!more && qn == 0) break;
+        if (more) t0 += gridDim.x * blockDim.x;
     }
 }
 
