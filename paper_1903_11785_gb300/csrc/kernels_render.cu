@@ -94,20 +94,9 @@ __global__ void k_depth_box(const __grid_constant__ CamSet cams, const __grid_co
     }
 }
 
-// Eq. (4) for one triangle (world vertices X, Y, Z, squared centroid-camera
-// distance d2 as float bits) in camera c.  The triangle is skipped if a vertex
-// is not in front of the camera (w' <= 0) or its projected area is zero; its
-// value goes into each pixel whose centre p lies in the closed box of the
-// projection and on the inner side of (or on) all three edges, either winding.
-// Everything is decided on the homogeneous image points (x', y', w') without
-// dividing: the edge function of edge (i, j) at p is (p_x a - p_y b) + c with
-// a = y_i w_j - w_i y_j, b = x_i w_j - w_i x_j, c = x_i y_j - y_i x_j (its
-// sign is the image-plane one for w > 0), the area is zero iff
-// (x_0 a_12 - y_0 b_12) + w_0 c_12 is, and the box test uses the exact signs
-// of p w_j - x_j from one FMA each.
-// `sink(pixel)` is called for each covered pixel (row-major index in c's
-// image).
-// The first part of the test: the homogeneous image points of the vertices
+// Eq. (4) coverage of one triangle (world vertices X, Y, Z) in camera c, in
+// two parts, raster_setup and raster_pixels (below).
+// The first part: the homogeneous image points of the vertices
 // and the candidate pixels (centres within 1/64 px of the box of the
 // approximate projections; their error is below 1e-3 px for images up to
 // 65535 px, and the exact box test in raster_pixels decides).  False if a
