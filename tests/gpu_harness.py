@@ -38,23 +38,26 @@ def run_gpu(rig, frames, host=False, caps=None, slots=None, batch=True, rgb_in_p
         vps = np.stack([fr.viewpoint for fr in frames])
         r.colour(slots, rgbs, vps, in_place=rgb_in_place)
         torch.cuda.synchronize()
-        outs = []
-        for s in slots:
-            c = r.counts(s, allow_capacity=True)
-            o = dict(counts=c)
-            if c["flags"] == 0:
-                res = r.results(s)
-                o.update(rois=res["rois"], verts=res["verts"].cpu().numpy(), tris=res["tris"].cpu().numpy(),
-                         rgb=res["rgb"].cpu().numpy(), cam=res["cam"].cpu().numpy())
-                o["sil"] = r.debug(s, fvv.FVV_DEBUG_SIL_BITS).cpu().numpy().view(np.uint32)
-                o["coarse"] = r.debug(s, fvv.FVV_DEBUG_COARSE_BITS).cpu().numpy().view(np.uint32)
-                o["labels"] = r.debug(s, fvv.FVV_DEBUG_LABELS).cpu().numpy()
-                o["fine"] = r.debug(s, fvv.FVV_DEBUG_FINE_BITS).cpu().numpy().view(np.uint32)
-                o["depth"] = r.debug(s, fvv.FVV_DEBUG_DEPTH).cpu().numpy()
-            outs.append(o)
-        return outs
+        return [fetch_outputs(r, s) for s in slots]
     finally:
         r.close()
+
+
+def fetch_outputs(r, s):
+    """Every output of slot s of rig r (an fvv.Rig), as numpy arrays."""
+    from paper_1903_11785_gb300 import fvv
+    c = r.counts(s, allow_capacity=True)
+    o = dict(counts=c)
+    if c["flags"] == 0:
+        res = r.results(s)
+        o.update(rois=res["rois"], verts=res["verts"].cpu().numpy(), tris=res["tris"].cpu().numpy(),
+                 rgb=res["rgb"].cpu().numpy(), cam=res["cam"].cpu().numpy())
+        o["sil"] = r.debug(s, fvv.FVV_DEBUG_SIL_BITS).cpu().numpy().view(np.uint32)
+        o["coarse"] = r.debug(s, fvv.FVV_DEBUG_COARSE_BITS).cpu().numpy().view(np.uint32)
+        o["labels"] = r.debug(s, fvv.FVV_DEBUG_LABELS).cpu().numpy()
+        o["fine"] = r.debug(s, fvv.FVV_DEBUG_FINE_BITS).cpu().numpy().view(np.uint32)
+        o["depth"] = r.debug(s, fvv.FVV_DEBUG_DEPTH).cpu().numpy()
+    return o
 
 
 def run_oracle(rig, fr):

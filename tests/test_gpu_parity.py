@@ -13,7 +13,7 @@ import torch
 
 from synth import ABSTAIN, make_frame, make_rig, render, scene_objects
 from synth.scenes import _gen, _make_rig
-from tests.gpu_harness import compare, run_gpu, run_oracle, unpack_rows
+from tests.gpu_harness import compare, fetch_outputs, run_gpu, run_oracle, unpack_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -190,6 +190,30 @@ def test_volleyball_frame_bit_exact():
     g = run_gpu(rig, [fr])[0]
     ref = compare(rig, fr, g)
     assert len(ref.rois) == 13
+
+
+def test_bench_batch_sampled_frames_bit_exact():
+    """The benchmark's step at full size: 64 volleyball-shaped frames packed
+    by one upload call and reconstructed and coloured by one call each, with
+    the launch shapes the autotuner picks on that batch; frames 0, 21, 42
+    and 63 are then compared with the oracle, output by output."""
+    import bench
+    from paper_1903_11785_gb300 import fvv
+    from synth import Frame
+    rig, masks, rgb, vps = bench.make_batch(64, 0, "cuda")
+    r = fvv.Rig(rig, max_slots=64, host_staging=0)
+    try:
+        slots = list(range(64))
+        r.upload_silhouettes_batch(slots, masks)
+        r.reconstruct(slots)
+        r.autotune(slots)                 # times the shapes, then reconstructs once more
+        r.colour(slots, rgb, vps)
+        torch.cuda.synchronize()
+        for i in (0, 21, 42, 63):
+            fr = Frame(masks=masks[i].cpu(), rgb=rgb[i].cpu(), ellipsoids=[], viewpoint=vps[i])
+            compare(rig, fr, fetch_outputs(r, i))
+    finally:
+        r.close()
 
 
 def test_judo_frame_bit_exact():
