@@ -70,7 +70,7 @@ struct SlotInfo {
     uint32_t n_words;           // fine words in use
     uint32_t n_chunks;
     uint32_t n_tiles;           // fine-carve tiles of all ROIs
-    uint32_t pad_;
+    uint32_t next_tile;         // the fine carve's next unclaimed tile
     uint32_t n_verts, n_tris;
     uint32_t n_on;
     unsigned long long tests_coarse, tests_fine, tests_bisect;

@@ -103,12 +103,15 @@ __global__ void __launch_bounds__(256) k_coarse_carve(const __grid_constant__ Ca
     }
 }
 
+// Clears the fine grids and resets the fine carve's tile counter.
 __global__ void __launch_bounds__(256) k_clear_fine(const __grid_constant__ Layout L,
                                                     const __grid_constant__ SlotList sl) {
     const int slot = sl.s[blockIdx.y];
-    const uint32_t nwords = slot_ptr<SlotInfo>(L, slot, L.info)->n_words;
+    SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const uint32_t nwords = info->n_words;
     uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) fine[w] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) info->next_tile = 0u;
 }
 
 // The ROI holding fine-carve tile t: the last ROI whose first tile is <= t.
@@ -222,15 +225,20 @@ template <int NC, bool ABSTAIN>
 __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, const SmemCam* sc, int ncam,
                                            uint32_t ntiles, int nrois, const DRoi* rois,
                                            const uint32_t* __restrict__ sil, uint32_t* fine,
-                                           uint32_t& tests, uint32_t& reads) {
+                                           uint32_t* next_tile, uint32_t& tests, uint32_t& reads) {
     const int lane = threadIdx.x & 31, half = lane & 1;
     const int xi = lane & 3, yi = (lane >> 2) & 1, zi = lane >> 3;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     // ROI of the current tile (the same in every lane)
     uint32_t lo = 0, hi = 0, woff = 0;
     int fx = 1, fy = 1, fz = 1, nxw = 1, ntx = 1, nty = 1;
     float fo0 = 0.f, fo1 = 0.f, fo2 = 0.f;
-    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += nwarps) {
+    // tiles differ a lot in cost (a surface tile tests many cameras, an
+    // empty one few), so each warp claims its next tile from a counter
+    for (;;) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(next_tile, 1u);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= ntiles) break;
         if (t >= hi || t < lo) {
             const DRoi& r = rois[roi_of_tile(rois, nrois, t)];
             lo = r.tile_off;
@@ -348,12 +356,13 @@ __global__ void __launch_bounds__(256) k_fine_carve(const __grid_constant__ CamS
     const DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
     const uint32_t* __restrict__ sil = slot_ptr<uint32_t>(L, slot, L.sil);
     uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
+    uint32_t* next_tile = &slot_ptr<SlotInfo>(L, slot, L.info)->next_tile;
     // per-lane counts stay below 2^30 (at most 2^24 tiles of 64 tests each)
     uint32_t tests = 0, reads = 0;
     if (cams.oob == FVV_OOB_ABSTAIN)
-        fine_tiles<NC, true>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tests, reads);
+        fine_tiles<NC, true>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, next_tile, tests, reads);
     else
-        fine_tiles<NC, false>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, tests, reads);
+        fine_tiles<NC, false>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, next_tile, tests, reads);
     const unsigned long long t = block_sum<unsigned long long>((unsigned long long)tests, sh_t);
     const unsigned long long rd = block_sum<unsigned long long>((unsigned long long)reads, sh_t);
     if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_fine, t);
