@@ -57,7 +57,9 @@ __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CamSet cam
 }
 
 // Sec. II-B-1: the coarse hull over the whole volume.  Occupied voxels also
-// start their union-find tree (parent = own linear index) for Sec. II-B-2.
+// start the union-find forest of Sec. II-B-2: each run of consecutive
+// occupied voxels within a 32-voxel word is one tree, rooted at the run's
+// first voxel (in this word), which is its smallest linear index.
 template <int NC>
 __global__ void __launch_bounds__(256) k_coarse_carve(const __grid_constant__ CamSet cams,
                                                       const __grid_constant__ Grid g,
@@ -85,8 +87,9 @@ __global__ void __launch_bounds__(256) k_coarse_carve(const __grid_constant__ Ca
             const bool on = warp_test<NC>(cams, sil, X, Y, Z, x < g.nx, tests);
             const uint32_t word = __ballot_sync(kFull, on);
             if (on) {
-                const int Lin = (int)(row * (uint32_t)g.nx) + x;
-                parent[Lin] = Lin;
+                const uint32_t starts = word & ~(word << 1);   // first voxel of each run
+                const int run0 = 31 - __clz(starts & (0xFFFFFFFFu >> (31 - lane)));
+                parent[(int)(row * (uint32_t)g.nx) + x] = (int)(row * (uint32_t)g.nx) + wx * 32 + run0;
             }
             if (lane == 0) {
                 bits[row * (uint32_t)g.nxw + (uint32_t)wx] = word;

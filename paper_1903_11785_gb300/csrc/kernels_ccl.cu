@@ -57,17 +57,31 @@ __device__ __forceinline__ void unite(int* parent, int a, int b, int& budget) {
     }
 }
 
-__device__ __forceinline__ bool coarse_on(const uint32_t* bits, const Grid& g, int x, int y, int z) {
-    if (x < 0 || y < 0 || z < 0 || x >= g.nx || y >= g.ny || z >= g.nz) return false;
-    return (__ldg(bits + ((size_t)z * g.ny + y) * g.nxw + (x >> 5)) >> (x & 31)) & 1u;
+// Bit i of row `row` (y, z), word wx of the coarse bitset as seen from the
+// 26-neighbourhood: 0 outside the grid.
+__device__ __forceinline__ uint32_t coarse_word(const uint32_t* bits, const Grid& g, int y, int z, int wx) {
+    if (y < 0 || z < 0 || y >= g.ny || z >= g.nz || wx < 0 || wx >= g.nxw) return 0u;
+    return __ldg(bits + ((size_t)z * g.ny + y) * g.nxw + wx);
 }
 
-// Union of every occupied voxel with its 13 occupied neighbours that come
-// before it in linear order (the other 13 see it in turn).  A warp reads 32
-// words of the coarse bitset (a lane each) and then takes its non-empty
-// words one at a time with a lane per voxel, so the chains of dependent
-// loads of a row's voxels run side by side rather than one after another in
-// a thread.
+// The unions of Sec. II-B-2 (26-connectivity), a word at a time.  The coarse
+// carve made each run of consecutive occupied voxels within a word one tree
+// rooted at its first voxel, so what is left is to join runs:
+//  - across a word boundary in the same row (the word's first voxel with
+//    the last voxel of the word before it);
+//  - with the four rows before it that touch it, (y-1, z) and (y-1..y+1,
+//    z-1): a run R of this row and a run S of such a row N are 26-adjacent
+//    iff some voxel l of R has a voxel of S among N's voxels l-1, l, l+1.
+// For each pair (R, S) one union suffices.  Let l0 be R's first voxel whose
+// window meets S.  Either l0 is R's first voxel, and S holds the leftmost
+// occupied of N's l0-1, l0 or, failing both, starts at l0+1; or l0 is
+// later, the window of l0-1 misses S, and S starts exactly at l0+1 with l0
+// empty in N.  So each voxel l of R unites R with the run of N's leftmost
+// occupied voxel among l-1, l if l starts R, and with the run starting at
+// l+1 if N has l empty and l+1 occupied: at most two unions per voxel and
+// row, almost all of them at run starts.  A warp reads 32 words of the
+// bitset (a lane each) and then takes its non-empty words one at a time
+// with a lane per voxel.
 __global__ void __launch_bounds__(256) k_union(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
                                                const __grid_constant__ SlotList sl) {
     const int slot = sl.s[blockIdx.y];
@@ -94,15 +108,25 @@ __global__ void __launch_bounds__(256) k_union(const __grid_constant__ Grid g, c
             const uint32_t row = w / (uint32_t)g.nxw;
             const int wx = (int)(w - row * g.nxw);
             const int y = (int)(row % (uint32_t)g.ny), z = (int)(row / (uint32_t)g.ny);
-            const int x = wx * 32 + lane;
-            const int Lin = (int)row * g.nx + x;
-            for (int dz = -1; dz <= 0; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        if (dz == 0 && (dy > 0 || (dy == 0 && dx >= 0))) continue;
-                        if (!coarse_on(bits, g, x + dx, y + dy, z + dz)) continue;
-                        unite(parent, Lin, ((z + dz) * g.ny + (y + dy)) * g.nx + (x + dx), budget);
-                    }
+            const int x0 = wx * 32;
+            const uint32_t starts = word & ~(word << 1);
+            const bool first = (starts >> lane) & 1u;                      // lane starts its run
+            const int run0 = (int)row * g.nx + x0 + (31 - __clz(starts & (0xFFFFFFFFu >> (31 - lane))));
+            // the run across the boundary with the word before, same row
+            if (lane == 0 && (coarse_word(bits, g, y, z, wx - 1) >> 31))
+                unite(parent, run0, run0 - 1, budget);
+            for (int k = 0; k < 4; ++k) {
+                const int dy = k == 0 ? -1 : k - 2, dz = k == 0 ? 0 : -1;
+                const uint32_t n = coarse_word(bits, g, y + dy, z + dz, wx);
+                const uint32_t np = coarse_word(bits, g, y + dy, z + dz, wx - 1);
+                const uint32_t nn = coarse_word(bits, g, y + dy, z + dz, wx + 1);
+                const bool left = lane > 0 ? (n >> (lane - 1)) & 1u : np >> 31;
+                const bool mid = (n >> lane) & 1u;
+                const bool right = lane < 31 ? (n >> (lane + 1)) & 1u : nn & 1u;
+                const int nrow = ((z + dz) * g.ny + (y + dy)) * g.nx + x0;
+                if (first && (left || mid)) unite(parent, run0, nrow + (left ? lane - 1 : lane), budget);
+                if (!mid && right) unite(parent, run0, nrow + lane + 1, budget);
+            }
         }
     }
     if (budget <= 0) atomicOr(&slot_ptr<SlotInfo>(L, slot, L.info)->flags, (unsigned)FVV_FLAG_LOOP);
