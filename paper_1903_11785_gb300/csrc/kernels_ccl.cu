@@ -5,7 +5,9 @@
 // Union-find over the occupied voxels with atomics (Playne & Hawick style):
 // parents live in a dense int32 array indexed by the linear voxel index and
 // are only ever touched at occupied voxels (the coarse carve initialised
-// them), so nothing is cleared per frame.  A union links the larger root
+// them, each run of consecutive occupied voxels of a 32-voxel word as one
+// tree rooted at its first voxel), so nothing is cleared per frame.  A
+// union links the larger root
 // below the smaller with atomicMin, so every root is the smallest linear
 // index of its component; sorting the roots therefore numbers components in
 // order of their smallest index, the canonical order of the oracle.  The
