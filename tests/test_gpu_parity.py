@@ -277,11 +277,12 @@ def test_abstain_policy_with_bisection():
     assert ref.tests_bisect > 0
 
 
-@pytest.mark.parametrize("n_cams", [5, 20])
+@pytest.mark.parametrize("n_cams", [5, 20, 64])
 def test_generic_and_large_camera_counts(n_cams):
-    """5 cameras (no unrolled instantiation: the generic camera loops) and 20
-    cameras (two camera groups in the fine hull's per-tile decisions), with
-    bisection and with the paper's walk."""
+    """5 cameras (no unrolled instantiation: the generic camera loops), 20
+    cameras (two camera groups in the fine hull's per-tile decisions) and 64
+    (the most a rig takes: four groups, every camera bit of the 64-bit
+    masks), with bisection and with the paper's walk."""
     r, h = 6.0, 3.0
     cs = [(r * math.cos(2 * math.pi * k / n_cams), r * math.sin(2 * math.pi * k / n_cams), h + 0.3 * (k % 3))
           for k in range(n_cams)]
