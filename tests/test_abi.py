@@ -95,5 +95,8 @@ def test_null_arguments_are_rejected(fvv):
     assert lib.fvv_query_arena(None, None, None) == fvv.FVV_ERR_INVALID_ARG
     assert fvv._lib.fvv_destroy_rig(None) == fvv.FVV_OK
     assert fvv._lib.fvv_reconstruct(None, None, 0, None) == fvv.FVV_ERR_INVALID_ARG
+    assert fvv._lib.fvv_upload_silhouettes(None, 0, None, 1, None) == fvv.FVV_ERR_INVALID_ARG
+    assert fvv._lib.fvv_upload_silhouettes_batch(None, None, 0, None, 1, None) == fvv.FVV_ERR_INVALID_ARG
+    assert fvv._lib.fvv_colour(None, None, 0, None, 1, None, None) == fvv.FVV_ERR_INVALID_ARG
     assert fvv._lib.fvv_get_counts(None, 0, None, None) == fvv.FVV_ERR_INVALID_ARG
     assert fvv._lib.fvv_mc_table(None, None) == fvv.FVV_ERR_INVALID_ARG
