@@ -58,7 +58,7 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # the current kernels, scaled to a launch by its frame count.  None for a
 # kernel changed since that capture.
 DRAM_BYTES_PER_FRAME = {"fine": 7.290368e6 / 4, "bisect": (17.209856e6 + 15104) / 4,
-                        "coarse": (4.331008e6 + 7680) / 4, "depth": (178.862848e6 + 11.137536e6) / 4}
+                        "coarse": None, "depth": (178.862848e6 + 11.137536e6) / 4}
 
 
 def parse_args():
