@@ -270,6 +270,22 @@ fvv_status fvv_get_debug(fvv_rig *rig, int slot, int what, void *dst, size_t byt
 fvv_status fvv_debug_pixels(fvv_rig *rig, int cam, long long n, const float *pts, int32_t *px, int32_t *py,
                             void *stream);
 
+/* Test hook for the labelling of Sec. II-B-2 on a grid that is given rather
+ * than carved, so that the parity tests can feed it random and adversarial
+ * occupancy (percolating random grids, long chains, spirals) that no set of
+ * silhouettes produces.  coarse_bits is a device array in the
+ * FVV_DEBUG_COARSE_BITS layout of the rig's grid (nz*ny rows of ceil(nx/32)
+ * uint32, bit x%32 of word x/32; bits past nx are ignored).  The call copies
+ * it into slot's coarse grid, starts the union-find forest as the coarse hull
+ * does, and runs the same labelling, box, Eq. (1) filter and ROI kernels as
+ * fvv_reconstruct.  Afterwards fvv_get_counts (components, ROIs, occupied
+ * voxels, flags), fvv_get_results (rois only) and FVV_DEBUG_LABELS read the
+ * outcome; the slot's fine grids, mesh and depth images are not computed
+ * (zero vertices and triangles) and its silhouettes are left as they were.
+ * Work is enqueued on `stream`; a NULL rig or grid, or a bad slot, gives
+ * FVV_ERR_INVALID_ARG with nothing launched. */
+fvv_status fvv_debug_label_coarse(fvv_rig *rig, int slot, const uint32_t *coarse_bits, void *stream);
+
 /* Allocation-free labelling (the paper has no counterpart; it is a service of
  * this library).  For callers that cannot call cudaMalloc: code that runs
  * inside a host framework which owns all device memory, or real-time loops

@@ -886,6 +886,22 @@ fvv_status fvv_debug_pixels(fvv_rig* rig, int cam, long long n, const float* pts
     return FVV_OK;
 }
 
+fvv_status fvv_debug_label_coarse(fvv_rig* rig, int slot, const uint32_t* coarse_bits, void* stream) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    if (!check_slot(rig, slot) || !coarse_bits) return fail(rig, FVV_ERR_INVALID_ARG, "bad slot or NULL grid");
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SlotList sl;
+    sl.n = 1;
+    sl.s[0] = slot;
+    k_zero_info<<<1, 32, 0, st>>>(rig->L, sl);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_debug_seed(rig->grid, rig->L, slot, coarse_bits, st);
+    if (e == cudaSuccess) e = launch_ccl(rig->grid, rig->L, sl, rig->sms, st);
+    if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_debug_label_coarse");
+    rig->state[slot] = 2;
+    return FVV_OK;
+}
+
 fvv_status fvv_debug_bytes(fvv_rig* rig, int slot, int what, size_t* bytes) {
     if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
     if (!check_slot(rig, slot) || !bytes) return fail(rig, FVV_ERR_INVALID_ARG, "bad slot or NULL bytes");

@@ -219,6 +219,9 @@ cudaError_t launch_render_view(const CamSet& cams, const Grid& g, const Layout& 
 cudaError_t launch_debug_pixels(const CamSet& cams, int cam, long long n, const float* pts, int32_t* px,
                                 int32_t* py, cudaStream_t st);
 cudaError_t launch_debug_labels(const Grid& g, const Layout& L, int slot, int32_t* dst, cudaStream_t st);
+// Writes a given coarse grid into slot and seeds its union-find forest as the
+// coarse hull does (the slot's SlotInfo must be zeroed first).
+cudaError_t launch_debug_seed(const Grid& g, const Layout& L, int slot, const uint32_t* src, cudaStream_t st);
 cudaError_t launch_debug_depth(const CamSet& cams, const Layout& L, int slot, float* dst, size_t npix,
                                cudaStream_t st);
 

@@ -23,11 +23,14 @@ namespace {
 // FVV_FLAG_LOOP and returns, so no launch can run unbounded.
 constexpr int kStepBudget = 1 << 22;
 
-// Root of x, shortening the path on the way (each visited node is pointed at
-// its grandparent).  Parents only ever point to smaller indices of the same
-// tree, so the plain stores are benign: a store that overwrites a concurrent
-// atomicMin link is made good by that union, which retries from the old
-// parent it got back.
+// Root of x during the union step, shortening the path on the way (each
+// visited node is pointed at its grandparent).  Parents only ever point to
+// smaller indices of the same tree, so while unions run the plain stores are
+// benign: a store that overwrites a concurrent atomicMin link is made good by
+// that union, which retries from the old parent it got back.  This holds for
+// k_union only: once k_compress writes a voxel's final root, a shortening
+// store from another thread's stale walk could replace it with an
+// intermediate node, so k_compress uses find_root_readonly instead.
 __device__ __forceinline__ int find_root(int* parent, int x, int& budget) {
     int cur = __ldcg(parent + x);
     if (cur == x || cur < 0) return x;
@@ -38,6 +41,23 @@ __device__ __forceinline__ int find_root(int* parent, int x, int& budget) {
         if (next == cur || next < 0) return cur;
         __stcg(parent + prev, next);
         prev = cur;
+        cur = next;
+    }
+    return cur;
+}
+
+// Root of x once every union is done, without writing anything.  In
+// k_compress the only store to parent[v] is v's own thread writing v's root,
+// so a parent entry only ever changes from an ancestor to the root: a walk
+// that reads either value still ends at the root, and the root that thread
+// writes stays (each non-root voxel ends pointing straight at its root, which
+// the two-step lookups of k_stats and k_debug_labels rely on).
+__device__ __forceinline__ int find_root_readonly(const int* parent, int x, int& budget) {
+    int cur = x;
+    while (budget > 0) {
+        --budget;
+        const int next = __ldcg(parent + cur);
+        if (next == cur || next < 0) return cur;
         cur = next;
     }
     return cur;
@@ -135,7 +155,8 @@ __global__ void __launch_bounds__(256) k_union(const __grid_constant__ Grid g, c
 }
 
 // Point every voxel at its root and list the roots (unordered); words are
-// taken as in k_union, a lane per voxel.
+// taken as in k_union, a lane per voxel.  A thread writes only its own
+// voxel's entry (see find_root_readonly).
 __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
                                                   const __grid_constant__ SlotList sl) {
     const int slot = sl.s[blockIdx.y];
@@ -164,7 +185,7 @@ __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ Grid g
             const uint32_t row = w / (uint32_t)g.nxw;
             const int wx = (int)(w - row * g.nxw);
             const int Lin = (int)row * g.nx + wx * 32 + lane;
-            const int r = find_root(parent, Lin, budget);
+            const int r = find_root_readonly(parent, Lin, budget);
             if (r == Lin) {
                 const int k = atomicAdd(&info->n_roots, 1);
                 if (k < g.max_comp) roots[k] = Lin;
@@ -421,6 +442,40 @@ __global__ void k_debug_labels(const __grid_constant__ Grid g, const __grid_cons
     }
 }
 }  // namespace
+
+// A given coarse grid (parity tests of the labelling): copies the words into
+// the slot with the bits past nx cleared, and starts the union-find forest
+// exactly as k_coarse_carve does (each run of a word one tree rooted at its
+// first voxel), counting the occupied voxels.  One thread per word.
+namespace {
+__global__ void k_debug_seed(const __grid_constant__ Grid g, const __grid_constant__ Layout L, int slot,
+                             const uint32_t* src) {
+    uint32_t* bits = slot_ptr<uint32_t>(L, slot, L.coarse);
+    int* parent = slot_ptr<int>(L, slot, L.parent);
+    SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const uint32_t nwords = (uint32_t)g.nz * g.ny * g.nxw;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) {
+        const uint32_t row = w / (uint32_t)g.nxw;
+        const int wx = (int)(w - row * g.nxw);
+        uint32_t word = src[w];
+        if (wx == g.nxw - 1 && (g.nx & 31)) word &= (1u << (g.nx & 31)) - 1u;
+        bits[w] = word;
+        if (word) atomicAdd(&info->n_on, (uint32_t)__popc(word));
+        const uint32_t starts = word & ~(word << 1);
+        for (uint32_t m = word; m; m &= m - 1u) {
+            const int b = __ffs(m) - 1;
+            const int run0 = 31 - __clz(starts & (0xFFFFFFFFu >> (31 - b)));
+            parent[(int)row * g.nx + wx * 32 + b] = (int)row * g.nx + wx * 32 + run0;
+        }
+    }
+}
+}  // namespace
+
+cudaError_t launch_debug_seed(const Grid& g, const Layout& L, int slot, const uint32_t* src, cudaStream_t st) {
+    const long long words = (long long)g.nz * g.ny * g.nxw;
+    k_debug_seed<<<(unsigned)std::min<long long>((words + 255) / 256, 4096), 256, 0, st>>>(g, L, slot, src);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_debug_labels(const Grid& g, const Layout& L, int slot, int32_t* dst, cudaStream_t st) {
     const long long words = (long long)g.nz * g.ny * g.nxw;

@@ -43,6 +43,8 @@ struct NaGrid {
 
 constexpr int kNaBudget = 1 << 22;
 
+// Root of x while unions run, shortening the path on the way; its plain
+// stores are safe only in k_na_union (see na_find_readonly).
 __device__ __forceinline__ int na_find(int* parent, int x, int& budget) {
     int cur = __ldcg(parent + x);
     if (cur == x || cur < 0) return x;
@@ -53,6 +55,22 @@ __device__ __forceinline__ int na_find(int* parent, int x, int& budget) {
         if (next == cur || next < 0) return cur;
         __stcg(parent + prev, next);
         prev = cur;
+        cur = next;
+    }
+    return cur;
+}
+
+// Root of x after the unions, writing nothing.  In k_na_compress each thread
+// stores only its own voxel's root, so every entry changes at most once, from
+// an ancestor to the root; no other store can overwrite that root afterwards
+// (a shortening store here could, which would leave the voxel pointing at an
+// intermediate node and out of its component's count and box).
+__device__ __forceinline__ int na_find_readonly(const int* parent, int x, int& budget) {
+    int cur = x;
+    while (budget > 0) {
+        --budget;
+        const int next = __ldcg(parent + cur);
+        if (next == cur || next < 0) return cur;
         cur = next;
     }
     return cur;
@@ -138,7 +156,7 @@ __global__ void k_na_compress(NaGrid g, int* sc) {
             const int b = __ffs(word) - 1;
             word &= word - 1;
             const int L = (int)row * g.nx + wx * 32 + b;
-            const int r = na_find(parent, L, budget);
+            const int r = na_find_readonly(parent, L, budget);
             if (r == L) {
                 const int k = atomicAdd(sc, 1);
                 if (k < kNaMaxComponents) sc[kNaRoots + k] = L;

@@ -90,6 +90,7 @@ _sigs = {
     "fvv_get_debug": ([_vp, C.c_int, C.c_int, _vp, C.c_size_t, _vp], C.c_int),
     "fvv_mc_table": ([_vp, _vp], C.c_int),
     "fvv_debug_pixels": ([_vp, C.c_int, C.c_longlong, _vp, _vp, _vp, _vp], C.c_int),
+    "fvv_debug_label_coarse": ([_vp, C.c_int, _vp, _vp], C.c_int),
     "fvv_label_components_noalloc": ([_vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp], C.c_int),
     "fvv_set_timing": ([_vp, C.c_int], C.c_int),
     "fvv_autotune": ([_vp, C.POINTER(C.c_int), C.c_int, _vp, C.POINTER(C.c_int)], C.c_int),
@@ -339,6 +340,13 @@ def fvv_probe_l2(mode: int, buf: torch.Tensor, reps: int, out: torch.Tensor, blo
     _check(_lib.fvv_probe_l2(mode, buf.data_ptr(), nbytes, reps, out.data_ptr(), blocks, threads, _stream(stream)))
 
 
+def fvv_debug_label_coarse(rig_ptr, slot, coarse_bits: torch.Tensor, stream=None):
+    """Label a given coarse grid (device int32/uint32 words in the
+    FVV_DEBUG_COARSE_BITS layout) in `slot` with the library's CCL kernels."""
+    assert coarse_bits.is_cuda and coarse_bits.is_contiguous() and coarse_bits.element_size() == 4
+    _check(_lib.fvv_debug_label_coarse(rig_ptr, slot, _vp(coarse_bits.data_ptr()), _stream(stream)), rig_ptr)
+
+
 def fvv_get_debug(rig_ptr, slot, what, stream=None) -> torch.Tensor:
     n = C.c_size_t(0)
     _check(_lib.fvv_debug_bytes(rig_ptr, slot, what, C.byref(n)), rig_ptr)
@@ -397,6 +405,9 @@ class Rig:
 
     def debug(self, slot, what, stream=None):
         return fvv_get_debug(self.ptr, slot, what, stream)
+
+    def debug_label_coarse(self, slot, coarse_bits, stream=None):
+        fvv_debug_label_coarse(self.ptr, slot, coarse_bits, stream)
 
     def set_timing(self, enable=True):
         fvv_set_timing(self.ptr, enable)

@@ -100,3 +100,4 @@ def test_null_arguments_are_rejected(fvv):
     assert fvv._lib.fvv_colour(None, None, 0, None, 1, None, None) == fvv.FVV_ERR_INVALID_ARG
     assert fvv._lib.fvv_get_counts(None, 0, None, None) == fvv.FVV_ERR_INVALID_ARG
     assert fvv._lib.fvv_mc_table(None, None) == fvv.FVV_ERR_INVALID_ARG
+    assert fvv._lib.fvv_debug_label_coarse(None, 0, None, None) == fvv.FVV_ERR_INVALID_ARG

@@ -6,9 +6,11 @@ that owns all device memory, or a real-time loop in which an allocation
 offers a labelling call whose scratch is a static device array inside the
 library.  These tests check, through the C ABI, that it gives exactly the
 labels and component counts that fvv_reconstruct computes for the same
-coarse grid, on two calls in a row (the second call must not see the
-first's leftovers), and that grids larger than the static scratch are
-refused before anything runs.
+coarse grid, and that the CPU oracle computes from the same silhouettes, on
+two calls in a row (the second call must not see the first's leftovers),
+and that grids larger than the static scratch are refused before anything
+runs.  (Random and adversarial grids are run through both labellers many
+times over in test_gpu_ccl_stress.py.)
 
 The file is named to be collected last, so that a run stopping at the first
 failure has already run every other test."""
@@ -31,8 +33,11 @@ def _lib():
 
 
 def _reference(fvv, config, index):
-    """Coarse bits, canonical labels and counts as fvv_reconstruct gives them."""
+    """Coarse bits, canonical labels and counts as fvv_reconstruct gives them;
+    the labels and counts are checked against the oracle's on the way."""
+    from oracle import Oracle
     rig, fr = make_frame(config, index)
+    ref = Oracle(rig).reconstruct(fr.masks.numpy())
     r = fvv.Rig(rig, max_slots=1, host_staging=0)
     try:
         r.upload_silhouettes(0, fr.masks.cuda())
@@ -42,6 +47,8 @@ def _reference(fvv, config, index):
         labels = r.debug(0, fvv.FVV_DEBUG_LABELS).clone()
     finally:
         r.close()
+    np.testing.assert_array_equal(labels.cpu().numpy().reshape(ref.labels.shape), ref.labels)
+    assert (c["n_components"], c["n_rois"]) == (ref.n_components, len(ref.rois))
     return rig, bits, labels, c
 
 
