@@ -119,3 +119,76 @@ def project32(P, X, Y, Z):
     P = np.asarray(P, np.float32)
     X, Y, Z = (np.asarray(v, np.float32) for v in (X, Y, Z))
     return [fma32(P[r, 0], X, fma32(P[r, 1], Y, fma32(P[r, 2], Z, P[r, 3]))) for r in range(3)]
+
+
+# ---- exact binary32 arithmetic on rationals (an emulation independent of numpy
+# and of the C library: every operation is done exactly in Fractions and then
+# rounded once, to nearest with ties to even, as IEEE binary32 prescribes)
+
+def round32(q):
+    """The binary32 number nearest to the rational q (ties to even), as a
+    Fraction; normal and subnormal ranges (no overflow handling)."""
+    from fractions import Fraction
+    q = Fraction(q)
+    if q == 0:
+        return Fraction(0)
+    a = abs(q)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    # now 2^e <= a < 2^(e+1)
+    e = max(e, -126)
+    quantum = Fraction(2) ** (e - 23)
+    m = a / quantum
+    n = m.numerator // m.denominator
+    r = m - n
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and n % 2 == 1):
+        n += 1
+    out = n * quantum
+    return out if q > 0 else -out
+
+
+def fma_exact32(a, b, c):
+    """Correctly rounded binary32 fused multiply-add a*b + c of rationals."""
+    return round32(a * b + c)
+
+
+def cover_binary32_exact(P, X, Y, Z, px, py):
+    """The depth-image coverage reading, evaluated exactly as written with
+    Fractions: is the centre of pixel (px, py) covered by the triangle with
+    binary32 vertices (X[j], Y[j], Z[j]) in the view of the binary32 3x4
+    matrix P?  Homogeneous points: each row ((p3 + p2 Z) + p1 Y) + p0 X in
+    three fused multiply-adds; a vertex with w <= 0 or a zero determinant
+    skips the triangle; the centre p must lie in the closed box of the
+    projections (signs of p_x w_j - x_j and p_y w_j - y_j, one fused rounding
+    each) and on the same side of the three edge functions
+    (p_x a - p_y b) + c, with a = y_i w_j - w_i y_j, b = x_i w_j - w_i x_j,
+    c = x_i y_j - y_i x_j for edges (0,1), (1,2), (2,0), every product and
+    difference rounded on its own; all >= 0 or all <= 0 counts."""
+    from fractions import Fraction as F
+    p = [[F(float(v)) for v in row] for row in np.asarray(P, np.float32).reshape(3, 4)]
+    r, m = round32, round32
+    h = []
+    for j in range(3):
+        xj, yj, zj = F(float(X[j])), F(float(Y[j])), F(float(Z[j]))
+        h.append([fma_exact32(p[k][0], xj, fma_exact32(p[k][1], yj, fma_exact32(p[k][2], zj, p[k][3])))
+                  for k in range(3)])
+    if any(hj[2] <= 0 for hj in h):
+        return False
+    ea, eb, ec = [], [], []
+    for i, j in ((0, 1), (1, 2), (2, 0)):
+        xi, yi, wi = h[i]
+        xj, yj, wj = h[j]
+        ea.append(r(m(yi * wj) - m(wi * yj)))
+        eb.append(r(m(xi * wj) - m(wi * xj)))
+        ec.append(r(m(xi * yj) - m(yi * xj)))
+    det = r(r(m(h[0][0] * ea[1]) - m(h[0][1] * eb[1])) + m(h[0][2] * ec[1]))
+    if det == 0:
+        return False
+    pcx, pcy = F(int(px)) + F(1, 2), F(int(py)) + F(1, 2)
+    for c, k in ((pcx, 0), (pcy, 1)):
+        s = [fma_exact32(c, h[j][2], -h[j][k]) for j in range(3)]
+        if not (any(v >= 0 for v in s) and any(v <= 0 for v in s)):
+            return False
+    e = [r(r(m(pcx * ea[k]) - m(pcy * eb[k])) + ec[k]) for k in range(3)]
+    return all(v >= 0 for v in e) or all(v <= 0 for v in e)

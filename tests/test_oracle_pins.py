@@ -11,8 +11,8 @@ from scipy import ndimage
 from oracle import Oracle
 from oracle.oracle import Roi
 from synth import ABSTAIN, STRICT, make_frame, make_rig, render, sphere_scene, inside_any
-from tests.helpers import (affine_rig, canonical_labels, closed_oriented, edge_use, euler_characteristic,
-                           fma32, mesh_shells, signed_volume, sphere_rig)
+from tests.helpers import (affine_rig, canonical_labels, closed_oriented, cover_binary32_exact, edge_use,
+                           euler_characteristic, fma32, mesh_shells, round32, signed_volume, sphere_rig)
 
 
 # ------------------------------------------------------------------ Sec. II-B-1
@@ -111,6 +111,27 @@ def test_fma32_is_correctly_rounded():
         assert g == want, (x, y, z, g, want)
         twice += np.float32(np.float64(x) * np.float64(y) + np.float64(z)) != want
     assert twice > 0         # rounding the binary64 sum again is wrong on some of these
+
+
+def test_round32_is_binary32_rounding():
+    """The rational emulation's rounding (used to pin the depth coverage in
+    its edge band) equals IEEE binary32 conversion of binary64 values (one
+    rounding, so numpy's conversion is exact there), including halfway cases
+    (ties to even) and subnormals."""
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    x = rng.normal(0, 1, 4000) * np.exp2(rng.integers(-140, 100, 4000).astype(np.float64))
+    for v in x:
+        assert round32(Fraction(float(v))) == Fraction(float(np.float32(v)))
+    one = Fraction(1)
+    ulp = Fraction(1, 2 ** 23)
+    assert round32(one + ulp / 2) == one                      # tie, even below
+    assert round32(one + 3 * ulp / 2) == one + 2 * ulp        # tie, even above
+    assert round32(one + ulp / 2 + Fraction(1, 2 ** 80)) == one + ulp
+    assert round32(-(one + 3 * ulp / 2)) == -(one + 2 * ulp)
+    assert round32(Fraction(3, 2 ** 150)) == Fraction(4, 2 ** 150)   # 1.5 subnormal quanta: tie to even
+    assert round32(Fraction(3, 2 ** 151)) == Fraction(2, 2 ** 150)   # 0.75 quanta: up to the smallest
+    assert round32(Fraction(1, 3)) == Fraction(float(np.float32(1 / 3)))
 
 
 def test_projection_is_fused_binary32():
@@ -540,14 +561,54 @@ def test_depth_matches_brute_force():
     assert np.isfinite(D).sum() > 50
 
 
+def _perspective_coverage(rig, n, verts, tris, band=1e-3):
+    """Predicted coverage of the union of `tris` in camera n: at pixel centres
+    farther than `band` px from every edge line of a triangle, float64
+    image-plane geometry of its projection (exact far beyond its rounding
+    error); at the others, the reading itself evaluated exactly
+    (cover_binary32_exact).  Returns (coverage, number of (triangle, pixel)
+    decisions taken by each route, band pixels covered)."""
+    W, H = int(rig.width[n]), int(rig.height[n])
+    P = rig.P[n].astype(np.float64)
+    hv = np.concatenate([verts, np.ones((len(verts), 1))], 1) @ P.T
+    uv = hv[:, :2] / hv[:, 2:3]
+    cover = np.zeros((H, W), bool)
+    n_geo = n_band = band_in = 0
+    for t in tris:
+        q = uv[t]
+        x0, x1 = int(max(0, np.floor(q[:, 0].min()) - 2)), int(min(W - 1, np.ceil(q[:, 0].max()) + 2))
+        y0, y1 = int(max(0, np.floor(q[:, 1].min()) - 2)), int(min(H - 1, np.ceil(q[:, 1].max()) + 2))
+        if x0 > x1 or y0 > y1:
+            continue
+        ys, xs = np.mgrid[y0:y1 + 1, x0:x1 + 1]
+        px, py = xs + 0.5, ys + 0.5
+        e, dist = [], []
+        for i in range(3):
+            a, b = q[i], q[(i + 1) % 3]
+            ei = (b[0] - a[0]) * (py - a[1]) - (b[1] - a[1]) * (px - a[0])
+            e.append(ei)
+            dist.append(np.abs(ei) / max(np.hypot(*(b - a)), 1e-12))
+        inside = ((e[0] >= 0) & (e[1] >= 0) & (e[2] >= 0)) | ((e[0] <= 0) & (e[1] <= 0) & (e[2] <= 0))
+        near = np.min(np.stack(dist), 0) < band
+        n_geo += int((~near).sum())
+        for yy, xx in zip(*np.nonzero(near)):
+            n_band += 1
+            c = cover_binary32_exact(rig.P[n], verts[t, 0], verts[t, 1], verts[t, 2], x0 + xx, y0 + yy)
+            inside[yy, xx] = c
+            band_in += int(c)
+        cover[y0:y1 + 1, x0:x1 + 1] |= inside
+    return cover, n_geo, n_band, band_in
+
+
 def test_depth_perspective_matches_exact_geometry():
-    """Perspective view, random triangles of a few pixels: the binary32
-    homogeneous coverage test agrees with exact (float64) image-plane
-    geometry except at pixel centres within 1e-3 px of a triangle edge."""
+    """Perspective view, random triangles of a few pixels: the oracle's
+    coverage equals exact image-plane geometry at every pixel centre farther
+    than 1e-3 px from a triangle edge, and, at the centres nearer than that,
+    the binary32 homogeneous test of the reading evaluated exactly with
+    rationals (no pixel is exempt)."""
     rig = make_rig("tiny")
     rng = np.random.default_rng(3)
     n = 0
-    C = rig.C64[n]
     base = np.array([0.2, -0.3, 1.0])
     tris = []
     verts = []
@@ -559,32 +620,61 @@ def test_depth_perspective_matches_exact_geometry():
     verts = np.array(verts, np.float32).astype(np.float64)
     tris = np.array(tris, np.uint32)
     D = Oracle(rig).depth(verts, tris)[n]
-    W, H = int(rig.width[n]), int(rig.height[n])
-    P = rig.P[n].astype(np.float64)
-    hv = np.concatenate([verts, np.ones((len(verts), 1))], 1) @ P.T
-    uv = hv[:, :2] / hv[:, 2:3]
-    cover = np.zeros((H, W), bool)
-    near_edge = np.zeros((H, W), bool)
-    for t in tris:
-        q = uv[t]
-        x0, x1 = int(max(0, np.floor(q[:, 0].min()) - 1)), int(min(W - 1, np.ceil(q[:, 0].max()) + 1))
-        y0, y1 = int(max(0, np.floor(q[:, 1].min()) - 1)), int(min(H - 1, np.ceil(q[:, 1].max()) + 1))
-        ys, xs = np.mgrid[y0:y1 + 1, x0:x1 + 1]
-        px, py = xs + 0.5, ys + 0.5
-        e, dist = [], []
-        for i in range(3):
-            a, b = q[i], q[(i + 1) % 3]
-            ei = (b[0] - a[0]) * (py - a[1]) - (b[1] - a[1]) * (px - a[0])
-            e.append(ei)
-            dist.append(np.abs(ei) / max(np.hypot(*(b - a)), 1e-12))
-        inside = ((e[0] >= 0) & (e[1] >= 0) & (e[2] >= 0)) | ((e[0] <= 0) & (e[1] <= 0) & (e[2] <= 0))
-        cover[y0:y1 + 1, x0:x1 + 1] |= inside
-        near_edge[y0:y1 + 1, x0:x1 + 1] |= np.min(np.stack(dist), 0) < 1e-3
-    got = np.isfinite(D)
-    assert cover.sum() > 500
-    diff = got != cover
-    assert np.all(near_edge[diff])
-    assert diff.sum() <= max(3, cover.sum() // 1000)
+    cover, n_geo, n_band, _ = _perspective_coverage(rig, n, verts, tris)
+    assert cover.sum() > 500 and n_geo > 5000
+    np.testing.assert_array_equal(np.isfinite(D), cover)
+
+
+def _on_centres(rig, n, pix, depth):
+    """World points (binary32 values, as float64) that camera n sees at the
+    image points `pix` (k, 2) at distance `depth` along each ray."""
+    K, R, C = rig.K64[n], rig.R64[n], rig.C64[n]
+    pts = []
+    for (u, v), d in zip(pix, depth):
+        ray = R.T @ np.linalg.solve(K, np.array([u, v, 1.0]))
+        pts.append(C + d * ray / np.linalg.norm(ray))
+    return np.array(pts, np.float32).astype(np.float64)
+
+
+def test_depth_edge_band_matches_exact_binary32_reading():
+    """Triangles whose edges run through rows, columns and diagonals of pixel
+    centres (vertices projected within about 1e-5 px of pixel centres), so
+    that hundreds of centres lie within 1e-3 px of an edge and rounding
+    decides them: the oracle's coverage of every pixel equals the reading
+    evaluated exactly with rationals there, and exact geometry elsewhere."""
+    import dataclasses
+    rig0 = make_rig("tiny")
+    n = 0
+    rig = dataclasses.replace(rig0, P=rig0.P[:1], centre=rig0.centre[:1], width=rig0.width[:1],
+                              height=rig0.height[:1])
+    rng = np.random.default_rng(11)
+    verts, tris = [], []
+    shapes = [((0, 0), (12, 0), (0, 7)), ((0, 0), (9, 9), (0, 9)), ((0, 0), (9, 9), (9, 0)),
+              ((0, 0), (10, 5), (0, 5)), ((0, 0), (6, 0), (6, 6)), ((3, 0), (0, 4), (6, 4)),
+              ((0, 0), (1, 0), (0, 1)), ((0, 0), (8, 3), (2, 7))]
+    for k in range(40):
+        u0, v0 = int(rng.integers(40, 580)), int(rng.integers(30, 320))
+        a, b, c = shapes[k % len(shapes)]
+        if k % 2:
+            a, b, c = a, c, b                  # both windings
+        pix = [(u0 + x + 0.5, v0 + y + 0.5) for x, y in (a, b, c)]
+        depth = 6.0 + rng.uniform(-0.5, 0.5, 3) * (k % 3 != 0)
+        verts.extend(_on_centres(rig, n, pix, depth))
+        tris.append([3 * k, 3 * k + 1, 3 * k + 2])
+    verts = np.array(verts)
+    tris = np.array(tris, np.uint32)
+    got = np.zeros((int(rig.height[0]), int(rig.width[0])), bool)
+    cover = np.zeros_like(got)
+    n_band = band_in = 0
+    o = Oracle(rig)
+    for t in tris:                              # one triangle at a time: no overlap hides a decision
+        got |= np.isfinite(o.depth(verts, t[None])[0])
+        c, _, nb, bi = _perspective_coverage(rig, 0, verts, t[None])
+        cover |= c
+        n_band += nb
+        band_in += bi
+    assert n_band > 200 and 50 < band_in < n_band - 50
+    np.testing.assert_array_equal(got, cover)
 
 
 def test_depth_perspective_behind_camera_skipped():
