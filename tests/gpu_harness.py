@@ -128,3 +128,70 @@ def compare(rig, fr, g, oracle_out=None):
     np.testing.assert_array_equal(g["rgb"], col)
     np.testing.assert_array_equal(g["cam"], cam)
     return ref
+
+
+# ---- digests: every output of a frame in the oracle's layouts, hashed, so
+# that many frames can be compared without moving the arrays between processes
+
+def _h(a) -> str:
+    import hashlib
+    a = np.ascontiguousarray(a)
+    return hashlib.blake2b(a.view(np.uint8).reshape(-1).tobytes(), digest_size=16).hexdigest() + str(a.dtype) + \
+        str(a.shape)
+
+
+def oracle_digest(rig, masks, rgb, viewpoint) -> dict:
+    """The oracle's outputs for one frame (numpy inputs), hashed."""
+    o = Oracle(rig)
+    ref = o.reconstruct(masks)
+    depth = o.depth(ref.verts, ref.tris)
+    col, cam = o.colour(rgb, viewpoint, depth, ref.verts)
+    rois = [(r.cmin, r.cmax, r.gmin, r.gmax, r.fdim, r.count,
+             tuple(np.asarray(r.forigin, np.float32).view(np.uint32).tolist())) for r in ref.rois]
+    fine = np.concatenate([f.ravel() for f in ref.fine]) if ref.fine else np.zeros(0, np.uint8)
+    return dict(counts=(ref.n_components, len(ref.rois), int(ref.coarse.sum()), ref.tests_coarse, ref.tests_fine,
+                        ref.tests_bisect, len(ref.verts), len(ref.tris)),
+                coarse=_h(ref.coarse.astype(np.uint8)), labels=_h(ref.labels.astype(np.int32)), rois=rois,
+                fine=_h(fine.astype(np.uint8)), verts=_h(ref.verts.astype(np.float32)), tris=_h(ref.tris.astype(np.uint32)),
+                depth=_h(np.concatenate([np.asarray(d, np.float32).ravel() for d in depth])),
+                rgb=_h(col.astype(np.uint8)), cam=_h(cam.astype(np.int32)))
+
+
+def gpu_digest(rig, g) -> dict:
+    """The same digest of the GPU outputs `g` (fetch_outputs), converted to
+    the oracle's layouts."""
+    c = g["counts"]
+    nx, ny, nz = rig.grid_dims()
+    rois = [(tuple(r["cmin"]), tuple(r["cmax"]), tuple(r["gmin"]), tuple(r["gmax"]), tuple(r["fdim"]), r["count"],
+             tuple(np.asarray(r["forigin"], np.float32).view(np.uint32).tolist())) for r in g["rois"]]
+    fine, off = [], 0
+    for r in g["rois"]:
+        fx, fy, fz = r["fdim"]
+        nw = ((fx + 2 + 31) // 32) * (fy + 2) * (fz + 2)
+        bits = unpack_rows(g["fine"][off:off + nw], (fz + 2, fy + 2), fx + 2)
+        off += nw
+        fine.append(bits[1:-1, 1:-1, 1:-1].ravel())
+    fine = np.concatenate(fine) if fine else np.zeros(0, np.uint8)
+    return dict(counts=(c["n_components"], c["n_rois"], c["n_coarse_on"], c["tests_coarse"], c["tests_fine"],
+                        c["tests_bisect"], c["n_verts"], c["n_tris"]),
+                coarse=_h(unpack_rows(g["coarse"], (nz, ny), nx).astype(np.uint8)),
+                labels=_h(g["labels"].reshape(nz, ny, nx).astype(np.int32)), rois=rois, fine=_h(fine.astype(np.uint8)),
+                verts=_h(g["verts"].astype(np.float32)), tris=_h(g["tris"].astype(np.uint32)),
+                depth=_h(g["depth"].astype(np.float32)), rgb=_h(g["rgb"].astype(np.uint8)),
+                cam=_h(g["cam"].astype(np.int32)))
+
+
+def _oracle_digest_job(job):
+    """Worker: digest of frame i of the arrays saved at `path` (spawned pool)."""
+    import os
+    import sys
+    path, config, i = job
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from synth import make_rig
+    rig = make_rig(config)
+    masks = np.load(os.path.join(path, "masks.npy"), mmap_mode="r")
+    rgb = np.load(os.path.join(path, "rgb.npy"), mmap_mode="r")
+    vps = np.load(os.path.join(path, "vps.npy"))
+    return i, oracle_digest(rig, np.array(masks[i]), np.array(rgb[i]), vps[i])

@@ -64,3 +64,18 @@ def test_probe_rejects_bad_arguments(fvv):
         fvv.fvv_probe_l2(2, buf, 1, out, 1, 256)
     with pytest.raises(fvv.FvvError):
         fvv.fvv_probe_l2(0, buf, 1, out, 1, 48)                    # threads not a multiple of 32
+
+
+def test_fma_probe_computes_its_chains(fvv):
+    """With a = 1 and b = 0.5 every chain adds 0.5 per step, exactly (small
+    binary32 values): thread t's sum is the sum over chains k of
+    ((t + k) mod 8) + reps / 2."""
+    blocks, threads, reps = 5, 96, 37
+    out = torch.empty(blocks * threads, dtype=torch.float32, device="cuda")
+    fvv.fvv_probe_fma(reps, 1.0, 0.5, out, blocks, threads)
+    torch.cuda.synchronize()
+    t = np.arange(blocks * threads)
+    want = sum(((t + k) % 8) + reps * 0.5 for k in range(16))
+    assert np.array_equal(out.cpu().numpy(), want.astype(np.float32))
+    with pytest.raises(fvv.FvvError):
+        fvv.fvv_probe_fma(0, 1.0, 0.5, out, blocks, threads)

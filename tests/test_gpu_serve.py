@@ -48,8 +48,10 @@ def test_served_results_equal_alone(mask_copies):
         got[q.rid] = {k: out[k].cpu() for k in ("verts", "tris", "rgb", "cam")}
 
     try:
+        # arrivals compressed 50x (20,000 requests/s per rig), so that requests
+        # arrive while earlier batches are still on the GPU
         reqs = poisson_schedule(2, 400.0, 36, seed=3, pool_sizes=[4, 3])
-        done = srv.run(reqs, on_done=on_done)
+        done = srv.run(reqs, on_done=on_done, time_scale=50.0)
     finally:
         srv.close()
     assert all(q.t_done > 0 and q.slot >= 0 for q in done)
