@@ -420,6 +420,18 @@ fvv_status fvv_mc_table(uint8_t *ntri, uint8_t *edges);
 fvv_status fvv_probe_l2(int mode, const void *buf, size_t bytes, int reps, uint32_t *out, int blocks, int threads,
                         void *stream);
 
+/* FP32 micro-benchmark (no counterpart in the paper): the arithmetic ceiling
+ * of the hull and depth kernels, whose camera tests and triangle set-ups are
+ * chains of binary32 fused multiply-adds on the plain ALUs.  Launches
+ * `blocks` x `threads` threads on `stream`; each runs 16 independent chains
+ * x = fma(x, a, b) of `reps` steps (x starting at (thread + k) mod 8 for
+ * chain k) and writes the sum of its chains (added in chain order, binary32)
+ * to out[thread]: blocks*threads*reps*16 fused multiply-adds, two
+ * floating-point operations each.  out is a device pointer of
+ * blocks*threads floats.  Bad arguments give FVV_ERR_INVALID_ARG with
+ * nothing launched.  Time it with events on `stream`. */
+fvv_status fvv_probe_fma(int reps, float a, float b, float *out, int blocks, int threads, void *stream);
+
 /* Message of the last failure on rig (or of the last failed create if rig is
  * NULL).  The string stays valid until the next call on the rig. */
 const char *fvv_last_error(const fvv_rig *rig);

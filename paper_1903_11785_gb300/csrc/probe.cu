@@ -1,5 +1,8 @@
-// probe.cu -- two L2 micro-benchmarks that give the memory side of the hull
-// tests' roofline (no counterpart in the paper): a coalesced read of an
+// probe.cu -- micro-benchmarks behind the rooflines (no counterpart in the
+// paper).  An FP32 fused multiply-add loop gives the arithmetic ceiling of
+// the hull and depth kernels, whose camera tests and triangle set-ups are
+// chains of binary32 fused multiply-adds on the plain ALUs.  Two L2 probes
+// give the memory side of the hull tests' roofline: a coalesced read of an
 // L2-resident buffer and a random gather of 32-bit words from one.  A camera
 // test gathers one 32-bit silhouette word (Sec. II-B-1 reads one silhouette
 // pixel per projection), so the gather rate measured here is the rate of
@@ -48,7 +51,32 @@ __global__ void k_probe_gather(const uint32_t* __restrict__ buf, uint32_t mask, 
     out[tid] = acc;
 }
 
+// kFmaChains independent chains x = fma(x, a, b) per thread, `reps` steps
+// each; a and b come in as parameters so nothing is folded at compile time.
+constexpr int kFmaChains = 16;
+__global__ void k_probe_fma(int reps, float a, float b, float* out) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    float x[kFmaChains];
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) x[k] = (float)((tid + (uint32_t)k) & 7u);
+    for (int r = 0; r < reps; ++r) {
+#pragma unroll
+        for (int k = 0; k < kFmaChains; ++k) x[k] = __fmaf_rn(x[k], a, b);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) s = __fadd_rn(s, x[k]);
+    out[tid] = s;
+}
+
 }  // namespace
+
+extern "C" fvv_status fvv_probe_fma(int reps, float a, float b, float* out, int blocks, int threads, void* stream) {
+    if (!out || reps < 1 || blocks < 1 || threads < 32 || threads > 1024 || threads % 32) return FVV_ERR_INVALID_ARG;
+    if ((unsigned long long)blocks * threads > 0xFFFFFFFFull) return FVV_ERR_INVALID_ARG;
+    k_probe_fma<<<blocks, threads, 0, (cudaStream_t)stream>>>(reps, a, b, out);
+    return cudaGetLastError() == cudaSuccess ? FVV_OK : FVV_ERR_CUDA;
+}
 
 extern "C" fvv_status fvv_probe_l2(int mode, const void* buf, size_t bytes, int reps, uint32_t* out, int blocks,
                                    int threads, void* stream) {

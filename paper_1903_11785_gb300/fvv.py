@@ -101,6 +101,7 @@ _sigs = {
     "fvv_render_view": ([_vp, C.c_int, C.POINTER(_vp), C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int,
                          C.c_int, _vp, _vp, _vp, _vp], C.c_int),
     "fvv_probe_l2": ([C.c_int, _vp, C.c_size_t, C.c_int, _vp, C.c_int, C.c_int, _vp], C.c_int),
+    "fvv_probe_fma": ([C.c_int, C.c_float, C.c_float, _vp, C.c_int, C.c_int, _vp], C.c_int),
     "fvv_last_error": ([_vp], C.c_char_p),
     "fvv_status_string": ([C.c_int], C.c_char_p),
     "fvv_version": ([], C.c_int),
@@ -345,6 +346,15 @@ def fvv_debug_label_coarse(rig_ptr, slot, coarse_bits: torch.Tensor, stream=None
     FVV_DEBUG_COARSE_BITS layout) in `slot` with the library's CCL kernels."""
     assert coarse_bits.is_cuda and coarse_bits.is_contiguous() and coarse_bits.element_size() == 4
     _check(_lib.fvv_debug_label_coarse(rig_ptr, slot, _vp(coarse_bits.data_ptr()), _stream(stream)), rig_ptr)
+
+
+def fvv_probe_fma(reps: int, a: float, b: float, out: torch.Tensor, blocks: int, threads: int, stream=None):
+    """FP32 micro-benchmark: blocks*threads threads, 16 chains x = fma(x, a, b)
+    of `reps` steps each; out (float32, blocks*threads elements) receives each
+    thread's sum of its chains."""
+    if out.device.type != "cuda" or out.dtype != torch.float32 or out.numel() < blocks * threads:
+        raise ValueError("fvv_probe_fma: a float32 device buffer of blocks*threads elements")
+    _check(_lib.fvv_probe_fma(reps, a, b, out.data_ptr(), blocks, threads, _stream(stream)))
 
 
 def fvv_get_debug(rig_ptr, slot, what, stream=None) -> torch.Tensor:
