@@ -379,16 +379,27 @@ enum {
     FVV_N_TUNE = 5
 };
 
+/* Fine-hull tile shapes (x by y by z samples) the autotuner chooses among; a
+ * tile is classified per camera once and tested 4 x 2 x 4 samples at a time. */
+enum { FVV_TILE_4x4x8 = 0, FVV_TILE_4x4x4 = 1, FVV_TILE_4x8x8 = 2, FVV_N_TILES = 3 };
+
+/* Ints of a tuning configuration: threads per block of each FVV_TUNE_*
+ * kernel, then its resident blocks per SM, then the fine-hull tile shape
+ * (FVV_TILE_*). */
+#define FVV_TUNE_INTS (2 * FVV_N_TUNE + 1)
+
 /* Time candidate launch shapes (threads per block 64/128/256 x resident
- * blocks per SM 2/4/8/16/32) of each tunable kernel on the given slots, which
- * must hold reconstructed frames, keep the fastest, then reconstruct the
- * slots once more with it so that their results and counts are those of one
- * reconstruction.  Synchronises `stream`.  config (may be NULL) receives
- * 2*FVV_N_TUNE ints: threads per block of each kernel, then blocks per SM. */
+ * blocks per SM 2/4/8/16/32) of each tunable kernel, and for the fine hull
+ * each tile shape too, on the given slots, which must hold reconstructed
+ * frames; keep the fastest, then reconstruct the slots once more with it so
+ * that their results and counts are those of one reconstruction.  Results
+ * never depend on the choice.  Synchronises `stream`.  config (may be NULL)
+ * receives FVV_TUNE_INTS ints. */
 fvv_status fvv_autotune(fvv_rig *rig, const int *slots, int n_slots, void *stream, int *config);
 
-/* Read or set the launch shapes (2*FVV_N_TUNE ints as for fvv_autotune);
- * threads must be 32..256 in steps of 32 and blocks per SM 1..64. */
+/* Read or set the configuration (FVV_TUNE_INTS ints as for fvv_autotune);
+ * threads must be 32..256 in steps of 32, blocks per SM 1..64, the tile
+ * shape one of FVV_TILE_*. */
 fvv_status fvv_get_tuning(fvv_rig *rig, int *config);
 fvv_status fvv_set_tuning(fvv_rig *rig, const int *config);
 

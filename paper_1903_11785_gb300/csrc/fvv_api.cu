@@ -211,6 +211,8 @@ fvv_status make_plan(const fvv_rig_desc* d, const fvv_recon_params* p, Plan& pl,
     g.max_chunks = (uint32_t)((fw + kChunk - 1) / kChunk);
     g.max_verts = (uint32_t)mv;
     g.max_tris = (uint32_t)mt;
+    g.tile_y = kFineTiles[FVV_TILE_4x4x8][0];
+    g.tile_z = kFineTiles[FVV_TILE_4x4x8][1];
 
     Layout& L = pl.L;
     std::memset(&L, 0, sizeof(L));
@@ -489,8 +491,8 @@ static fvv_status make_slot_list(fvv_rig* rig, const int* slots, int n_slots, in
 
 // The launch sequence of one reconstruction of the slots in `sl`.
 static cudaError_t enqueue_reconstruct(fvv_rig* rig, const SlotList& sl, cudaStream_t st) {
-    const Grid& g = rig->grid;
     const Tuning& tu = rig->tune;
+    const Grid g = tuned_grid_params(rig->grid, tu);
     const McTable mc{rig->mc_ntri, rig->mc_edges};
     k_zero_info<<<sl.n, 32, 0, st>>>(rig->L, sl);
     cudaError_t e = cudaGetLastError();
@@ -578,6 +580,7 @@ fvv_status fvv_get_tuning(fvv_rig* rig, int* config) {
         config[k] = rig->tune.threads[k];
         config[FVV_N_TUNE + k] = rig->tune.waves[k];
     }
+    config[2 * FVV_N_TUNE] = rig->tune.fine_tile;
     return FVV_OK;
 }
 
@@ -588,10 +591,13 @@ fvv_status fvv_set_tuning(fvv_rig* rig, const int* config) {
         if (th < 32 || th > 256 || th % 32 || wv < 1 || wv > 64)
             return fail(rig, FVV_ERR_INVALID_ARG, "threads must be 32..256 in steps of 32, blocks per SM 1..64");
     }
+    const int tile = config[2 * FVV_N_TUNE];
+    if (tile < 0 || tile >= FVV_N_TILES) return fail(rig, FVV_ERR_INVALID_ARG, "tile shape must be one of FVV_TILE_*");
     for (int k = 0; k < FVV_N_TUNE; ++k) {
         rig->tune.threads[k] = config[k];
         rig->tune.waves[k] = config[FVV_N_TUNE + k];
     }
+    rig->tune.fine_tile = tile;
     cudaDeviceSynchronize();
     drop_graphs(rig);
     return FVV_OK;
@@ -605,13 +611,14 @@ fvv_status fvv_autotune(fvv_rig* rig, const int* slots, int n_slots, void* strea
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool timing = rig->timing;
     rig->timing = false;
-    const Grid& g = rig->grid;
     const McTable mc{rig->mc_ntri, rig->mc_edges};
     cudaEvent_t a = nullptr, b = nullptr;
     cudaError_t e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
-    // one stage on its own, on the inputs the last reconstruction left
+    // one stage on its own, on the inputs the last reconstruction left (the
+    // fine hull after the ROI table was laid out for its tile shape)
     auto run = [&](int knob, const Tuning& tu) -> cudaError_t {
+        const Grid g = tuned_grid_params(rig->grid, tu);
         switch (knob) {
             case FVV_TUNE_COARSE: return launch_coarse_carve(rig->cams, g, rig->L, sl, rig->sms, tu, st);
             case FVV_TUNE_FINE: return launch_fine_carve(rig->cams, g, rig->L, sl, rig->sms, tu, st);
@@ -626,11 +633,19 @@ fvv_status fvv_autotune(fvv_rig* rig, const int* slots, int n_slots, void* strea
     for (int knob = 0; knob < FVV_N_TUNE && e == cudaSuccess; ++knob) {
         float best = 1e30f;
         Tuning keep = rig->tune;
+        const int n_tiles = knob == FVV_TUNE_FINE ? FVV_N_TILES : 1;
+        for (int tile = 0; tile < n_tiles && e == cudaSuccess; ++tile)
         for (int th : threads)
             for (int wv : waves) {
                 Tuning tu = rig->tune;
                 tu.threads[knob] = th;
                 tu.waves[knob] = wv;
+                if (knob == FVV_TUNE_FINE) {
+                    tu.fine_tile = tile;
+                    // the ROI table's tile offsets for this shape (not timed)
+                    if (th == threads[0] && wv == waves[0]) e = launch_filter(tuned_grid_params(rig->grid, tu), rig->L, sl, st);
+                    if (e != cudaSuccess) break;
+                }
                 e = run(knob, tu);  // warm
                 if (e == cudaSuccess) e = cudaEventRecord(a, st);
                 for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = run(knob, tu);
@@ -643,6 +658,7 @@ fvv_status fvv_autotune(fvv_rig* rig, const int* slots, int n_slots, void* strea
                     best = ms;
                     keep.threads[knob] = th;
                     keep.waves[knob] = wv;
+                    keep.fine_tile = tu.fine_tile;
                 }
             }
         rig->tune = keep;

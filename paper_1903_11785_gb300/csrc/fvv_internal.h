@@ -54,13 +54,15 @@ struct Grid {
     int max_comp, max_rois;
     uint32_t max_fine_words, max_chunks;
     uint32_t max_verts, max_tris;
+    int tile_y, tile_z;  // fine-carve tile shape of this launch sequence (kFineTiles)
 };
 
-// Fine-carve tiles: kTileX x kTileY x kTileZ interior samples, classified
-// per camera once and tested in kSubTiles sub-tiles of 4 x kSubY x kSubZ
-// samples, one per lane.
-constexpr int kTileX = 4, kTileY = 4, kTileZ = 8;
-constexpr int kSubY = 2, kSubZ = 4, kSubTiles = (kTileY / kSubY) * (kTileZ / kSubZ);
+// Fine-carve tiles: kTileX x tile_y x tile_z interior samples, classified
+// per camera once and tested in sub-tiles of 4 x kSubY x kSubZ samples, one
+// per lane.  The autotuner picks the shape among kFineTiles (FVV_TILE_*).
+constexpr int kTileX = 4;
+constexpr int kSubY = 2, kSubZ = 4;
+constexpr int kFineTiles[FVV_N_TILES][2] = {{4, 8}, {4, 4}, {8, 8}};   // (tile_y, tile_z)
 
 // Per-slot device bookkeeping (zeroed at the start of each reconstruction).
 struct SlotInfo {
@@ -149,7 +151,16 @@ inline int grid_x(int sms, int n_slots, long long work_items, int per_block) {
 struct Tuning {
     int threads[FVV_N_TUNE];
     int waves[FVV_N_TUNE];
+    int fine_tile;       // index into kFineTiles
 };
+
+// The grid with the tuned fine-carve tile shape.
+inline Grid tuned_grid_params(const Grid& g, const Tuning& tu) {
+    Grid out = g;
+    out.tile_y = kFineTiles[tu.fine_tile][0];
+    out.tile_z = kFineTiles[tu.fine_tile][1];
+    return out;
+}
 
 inline Tuning default_tuning() {
     Tuning t;
@@ -158,6 +169,7 @@ inline Tuning default_tuning() {
         t.waves[k] = 8;
     }
     t.waves[FVV_TUNE_ZBUFFER] = 16;
+    t.fine_tile = FVV_TILE_4x4x8;
     return t;
 }
 
@@ -180,6 +192,8 @@ cudaError_t launch_pack(const CamSet& cams, const Layout& L, int n_frames, const
 cudaError_t launch_coarse_carve(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
                                 int sms, const Tuning& tu, cudaStream_t st);
 cudaError_t launch_ccl(const Grid& g, const Layout& L, const SlotList& sl, int sms, cudaStream_t st);
+// The filter and ROI table alone (k_filter), e.g. again for another fine-carve tile shape.
+cudaError_t launch_filter(const Grid& g, const Layout& L, const SlotList& sl, cudaStream_t st);
 cudaError_t launch_fine_carve(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl,
                               int sms, const Tuning& tu, cudaStream_t st);
 cudaError_t launch_mc_prefix(const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc, int sms,

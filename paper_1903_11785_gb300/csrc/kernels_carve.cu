@@ -224,7 +224,7 @@ __device__ __forceinline__ void classify_tile_camera(const SmemCam& c, const uin
 // only at those undecided cameras, and its test count (first background
 // camera + 1, or N when occupied) and occupancy are those of the plain
 // per-sample loop.
-template <int NC, bool ABSTAIN>
+template <int NC, bool ABSTAIN, int TY, int TZ>
 __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, const SmemCam* sc, int ncam,
                                            uint32_t ntiles, int nrois, const DRoi* rois,
                                            const uint32_t* __restrict__ sil, uint32_t* fine,
@@ -249,8 +249,8 @@ __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, co
             fy = r.fdim[1];
             fz = r.fdim[2];
             ntx = (fx + kTileX - 1) / kTileX;
-            nty = (fy + kTileY - 1) / kTileY;
-            hi = lo + (uint32_t)ntx * (uint32_t)nty * (uint32_t)((fz + kTileZ - 1) / kTileZ);
+            nty = (fy + TY - 1) / TY;
+            hi = lo + (uint32_t)ntx * (uint32_t)nty * (uint32_t)((fz + TZ - 1) / TZ);
             woff = r.word_off;
             nxw = r.nxw;
             fo0 = r.fo[0];
@@ -260,11 +260,11 @@ __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, co
         const uint32_t lt = t - lo;
         const uint32_t r1 = lt / (uint32_t)ntx;
         const int tx = (int)(lt - r1 * (uint32_t)ntx), ty = (int)(r1 % (uint32_t)nty), tz = (int)(r1 / (uint32_t)nty);
-        const int x0 = tx * kTileX, y0 = ty * kTileY, z0 = tz * kTileZ;
+        const int x0 = tx * kTileX, y0 = ty * TY, z0 = tz * TZ;
         // the tile's extreme samples
         const int xs[2] = {x0, min(x0 + kTileX - 1, fx - 1)};
-        const int ys[2] = {y0, min(y0 + kTileY - 1, fy - 1)};
-        const int zs[2] = {z0, min(z0 + kTileZ - 1, fz - 1)};
+        const int ys[2] = {y0, min(y0 + TY - 1, fy - 1)};
+        const int zs[2] = {z0, min(z0 + TZ - 1, fz - 1)};
         float cx[2], cy[2], cz[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
@@ -289,8 +289,9 @@ __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, co
         const int nb = bgm ? __ffsll((long long)bgm) - 1 : ncam;
         const uint64_t before = nb >= 64 ? ~0ull : (1ull << nb) - 1ull;
 #pragma unroll 1
+        constexpr int kSubsY = TY / kSubY, kSubTiles = kSubsY * (TZ / kSubZ);
         for (int sub = 0; sub < kSubTiles; ++sub) {
-            const int sy0 = y0 + (sub & 1) * kSubY, sz0 = z0 + (sub >> 1) * kSubZ;
+            const int sy0 = y0 + (sub % kSubsY) * kSubY, sz0 = z0 + (sub / kSubsY) * kSubZ;
             if (sy0 >= fy || sz0 >= fz) continue;          // the same in every lane
             // this lane's sample
             const int x = x0 + xi, y = sy0 + yi, z = sz0 + zi;
@@ -342,7 +343,7 @@ __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, co
     }
 }
 
-template <int NC>
+template <int NC, int TY, int TZ>
 __global__ void __launch_bounds__(256) k_fine_carve(const __grid_constant__ CamSet cams,
                                                     const __grid_constant__ Grid g,
                                                     const __grid_constant__ Layout L,
@@ -363,9 +364,9 @@ __global__ void __launch_bounds__(256) k_fine_carve(const __grid_constant__ CamS
     // per-lane counts stay below 2^30 (at most 2^24 tiles of 64 tests each)
     uint32_t tests = 0, reads = 0;
     if (cams.oob == FVV_OOB_ABSTAIN)
-        fine_tiles<NC, true>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, next_tile, tests, reads);
+        fine_tiles<NC, true, TY, TZ>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, next_tile, tests, reads);
     else
-        fine_tiles<NC, false>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, next_tile, tests, reads);
+        fine_tiles<NC, false, TY, TZ>(cams, g, sc, ncam, ntiles, nrois, rois, sil, fine, next_tile, tests, reads);
     const unsigned long long t = block_sum<unsigned long long>((unsigned long long)tests, sh_t);
     const unsigned long long rd = block_sum<unsigned long long>((unsigned long long)reads, sh_t);
     if (threadIdx.x == 0 && t) atomicAdd(&slot_ptr<SlotInfo>(L, slot, L.info)->tests_fine, t);
@@ -435,9 +436,20 @@ cudaError_t launch_fine_carve(const CamSet& cams, const Grid& g, const Layout& L
     k_clear_fine<<<dim3(gc, sl.n), 256, 0, st>>>(L, sl);
     const int th = tu.threads[FVV_TUNE_FINE];
     const int gx = tuned_grid(tu, FVV_TUNE_FINE, sms, sl.n, (long long)g.max_fine_words * 32);
-#define FVV_LAUNCH(NC) k_fine_carve<NC><<<dim3(gx, sl.n), th, 0, st>>>(cams, g, L, sl)
-    FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
+    // the tile shape (tile_y, tile_z) the k_filter of this sequence counted tiles with
+    if (g.tile_y == 4 && g.tile_z == 4) {
+#define FVV_LAUNCH(NC) k_fine_carve<NC, 4, 4><<<dim3(gx, sl.n), th, 0, st>>>(cams, g, L, sl)
+        FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
+    } else if (g.tile_y == 8 && g.tile_z == 8) {
+#define FVV_LAUNCH(NC) k_fine_carve<NC, 8, 8><<<dim3(gx, sl.n), th, 0, st>>>(cams, g, L, sl)
+        FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
+#undef FVV_LAUNCH
+    } else {
+#define FVV_LAUNCH(NC) k_fine_carve<NC, 4, 8><<<dim3(gx, sl.n), th, 0, st>>>(cams, g, L, sl)
+        FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
+#undef FVV_LAUNCH
+    }
     return cudaGetLastError();
 }
 

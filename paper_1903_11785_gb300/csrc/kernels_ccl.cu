@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(1024) k_filter(const __grid_constant__ Grid g,
         const unsigned long long nw = i < K ? rois[i].n_words : 0ull;
         const unsigned long long ns =
             i < K ? (unsigned long long)((rois[i].fdim[0] + kTileX - 1) / kTileX) *
-                        ((rois[i].fdim[1] + kTileY - 1) / kTileY) * ((rois[i].fdim[2] + kTileZ - 1) / kTileZ)
+                        ((rois[i].fdim[1] + g.tile_y - 1) / g.tile_y) * ((rois[i].fdim[2] + g.tile_z - 1) / g.tile_z)
                   : 0ull;
         unsigned long long tw, ts;
         const unsigned long long ew = block_exclusive_scan64(nw, sh64, tw);
@@ -412,6 +412,11 @@ cudaError_t launch_ccl(const Grid& g, const Layout& L, const SlotList& sl, int s
     k_compress<<<dim3(gx, sl.n), 256, 0, st>>>(g, L, sl);
     k_sort_roots<<<sl.n, 1024, 0, st>>>(g, L, sl);
     k_stats<<<dim3(gx, sl.n), 256, 0, st>>>(g, L, sl);
+    k_filter<<<sl.n, 1024, 0, st>>>(g, L, sl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter(const Grid& g, const Layout& L, const SlotList& sl, cudaStream_t st) {
     k_filter<<<sl.n, 1024, 0, st>>>(g, L, sl);
     return cudaGetLastError();
 }

@@ -37,11 +37,16 @@ FLAG_NAMES = {1: "ROOTS", 2: "ROIS", 4: "FINE", 8: "VERTS", 16: "TRIS", 32: "LOO
 STAGES = ("pack", "coarse", "ccl", "fine", "mc", "bisect", "depth", "colour")
 TUNE_KNOBS = ("coarse", "fine", "bisect", "zbuffer", "triangles")
 N_TUNE = len(TUNE_KNOBS)
+FINE_TILES = ((4, 4, 8), (4, 4, 4), (4, 8, 8))   # FVV_TILE_*: fine-hull tile (x, y, z) samples
+TUNE_INTS = 2 * N_TUNE + 1
 
 
 def tuning_dict(cfg):
-    """{kernel: (threads per block, blocks per SM)} from the flat C layout."""
-    return {k: (cfg[i], cfg[N_TUNE + i]) for i, k in enumerate(TUNE_KNOBS)}
+    """{kernel: (threads per block, blocks per SM)} and the fine-hull tile
+    shape ("fine_tile": (x, y, z)) from the flat C layout."""
+    d = {k: (cfg[i], cfg[N_TUNE + i]) for i, k in enumerate(TUNE_KNOBS)}
+    d["fine_tile"] = FINE_TILES[cfg[2 * N_TUNE]]
+    return d
 
 
 class RigDesc(C.Structure):
@@ -428,17 +433,21 @@ class Rig:
     def autotune(self, slots, stream=None):
         """Pick the fastest launch shapes on reconstructed slots; returns them."""
         arr = (C.c_int * len(slots))(*slots)
-        cfg = (C.c_int * (2 * N_TUNE))()
+        cfg = (C.c_int * TUNE_INTS)()
         _check(_lib.fvv_autotune(self.ptr, arr, len(slots), _stream(stream), cfg), self.ptr)
         return tuning_dict(list(cfg))
 
     def get_tuning(self):
-        cfg = (C.c_int * (2 * N_TUNE))()
+        cfg = (C.c_int * TUNE_INTS)()
         _check(_lib.fvv_get_tuning(self.ptr, cfg), self.ptr)
         return tuning_dict(list(cfg))
 
     def set_tuning(self, tuning):
-        cfg = [tuning[k][0] for k in TUNE_KNOBS] + [tuning[k][1] for k in TUNE_KNOBS]
+        """tuning: as get_tuning returns it; "fine_tile" may be left out
+        (4 x 4 x 8) and may be given as an (x, y, z) shape or an FVV_TILE_* index."""
+        tile = tuning.get("fine_tile", FINE_TILES[0])
+        tile = FINE_TILES.index(tuple(tile)) if not isinstance(tile, int) else tile
+        cfg = [tuning[k][0] for k in TUNE_KNOBS] + [tuning[k][1] for k in TUNE_KNOBS] + [tile]
         _check(_lib.fvv_set_tuning(self.ptr, (C.c_int * len(cfg))(*cfg)), self.ptr)
 
     def set_graphs(self, enable=True):

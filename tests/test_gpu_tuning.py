@@ -29,9 +29,15 @@ def _run(r, frames, stream=None):
     return out
 
 
+def _results(c):
+    """Counts that are results of the method: everything but the silhouette
+    words the kernels read (lookups_*), which depend on the tile shape."""
+    return {k: v for k, v in c.items() if not k.startswith("lookups_")}
+
+
 def _same(a, b):
     for x, y in zip(a, b):
-        assert x["counts"] == y["counts"]
+        assert _results(x["counts"]) == _results(y["counts"])
         for k in ("verts", "tris", "rgb", "cam"):
             assert torch.equal(x[k], y[k]), k
 
@@ -46,18 +52,26 @@ def test_autotune_and_shapes_keep_results():
     try:
         ref = _run(r, frames)
         chosen = r.autotune([0, 1, 2])
-        assert set(chosen) == set(fvv.TUNE_KNOBS)
-        for th, wv in chosen.values():
+        assert set(chosen) == set(fvv.TUNE_KNOBS) | {"fine_tile"}
+        assert chosen["fine_tile"] in fvv.FINE_TILES
+        for k in fvv.TUNE_KNOBS:
+            th, wv = chosen[k]
             assert th in (64, 128, 256) and wv in (2, 4, 8, 16, 32)
         # the autotuner leaves the slots freshly reconstructed
         after = [{k: r.results(s)[k].cpu() for k in ("verts", "tris")} | {"counts": r.counts(s)} for s in range(3)]
         for x, y in zip(after, ref):
-            assert x["counts"] == y["counts"] and torch.equal(x["verts"], y["verts"])
+            assert _results(x["counts"]) == _results(y["counts"]) and torch.equal(x["verts"], y["verts"])
         _same(_run(r, frames), ref)
         r.set_tuning({k: (32, 1) for k in fvv.TUNE_KNOBS})
         _same(_run(r, frames), ref)
         r.set_tuning({k: (64, 64) for k in fvv.TUNE_KNOBS})
         _same(_run(r, frames), ref)
+        for tile in fvv.FINE_TILES:            # every fine-hull tile shape: the same bits
+            r.set_tuning({k: (128, 8) for k in fvv.TUNE_KNOBS} | {"fine_tile": tile})
+            assert r.get_tuning()["fine_tile"] == tile
+            _same(_run(r, frames), ref)
+        with pytest.raises(fvv.FvvError):
+            r.set_tuning({k: (128, 8) for k in fvv.TUNE_KNOBS} | {"fine_tile": 3})
         with pytest.raises(fvv.FvvError):
             r.set_tuning({k: (48, 8) for k in fvv.TUNE_KNOBS})
     finally:
