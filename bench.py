@@ -71,7 +71,7 @@ def parse_args():
     ap.add_argument("--plain-frames", type=int, default=16)
     ap.add_argument("--cpu-frames", type=int, default=4, help="frames in the CPU-oracle sample")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--serve-requests", type=int, default=1200,
+    ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests of the serving leg (4 rigs at 30 Hz each; 0 skips it)")
     ap.add_argument("--serve-pool", type=int, default=8, help="frames per rig in the serving pool")
     ap.add_argument("--serve-masks", choices=("in_place", "copies"), default="in_place",
@@ -293,12 +293,14 @@ SERVE_RIGS = (("volleyball", 1000), ("volleyball", 2000), ("judo", 0), ("hd720",
 
 
 def run_serving(args, rank):
-    """Requests from four rigs (two volleyball-shaped 16x1080p, one judo-shaped
-    12x4K, one 8x720p), Poisson arrivals at 30 Hz per rig, admitted under a
-    40 GB memory budget and served with continuous batching.  Run once at the
-    offered rate and once with all arrivals compressed 1000x (saturation)."""
+    """Requests from four rigs (two volleyball-shaped 16x1080p with one
+    calibration, one judo-shaped 12x4K, one 8x720p), Poisson arrivals at 30 Hz
+    per rig, admitted under a 40 GB memory budget with slot capacities fitted
+    to each rig's frames, and served with continuous batching (the two
+    volleyball rigs share batches).  Run once at the offered rate and once
+    with all arrivals compressed 1000x (saturation)."""
     import torch
-    from paper_1903_11785_gb300.serve import RigPool, Server, poisson_schedule, summarize
+    from paper_1903_11785_gb300.serve import RigPool, Server, poisson_schedule, summarize, summarize_per_rig
     from synth import make_frame, make_rig
     pools = []
     for cfg, first in SERVE_RIGS:
@@ -311,21 +313,20 @@ def run_serving(args, rank):
         torch.cuda.empty_cache()
     srv = Server(pools, budget_bytes=40 << 30, mask_copies=args.serve_masks == "copies")
     try:
-        out = {"rigs": [c for c, _ in SERVE_RIGS], "slots": srv.slots, "budget_gb": 40, "offered_fps": 4 * 30.0,
-               "masks": args.serve_masks}
+        out = {"rigs": [c for c, _ in SERVE_RIGS], "offered_fps": 4 * 30.0, "masks": args.serve_masks}
+        out.update(srv.describe())
         warm = poisson_schedule(len(pools), 30.0, 40, seed=7, pool_sizes=[args.serve_pool] * len(pools))
         srv.run(warm, time_scale=1000.0)
         reqs = poisson_schedule(len(pools), 30.0, args.serve_requests, seed=1903,
                                 pool_sizes=[args.serve_pool] * len(pools))
-        out.update(summarize(srv.run(reqs)))
+        done = srv.run(reqs)
+        out.update(summarize(done))
+        out["per_rig"] = summarize_per_rig(done, len(pools))
         reqs = poisson_schedule(len(pools), 30.0, args.serve_requests, seed=1904,
                                 pool_sizes=[args.serve_pool] * len(pools))
-        out["saturated"] = summarize(srv.run(reqs, time_scale=1000.0), time_scale=1000.0)
-        per_rig = {}
-        for k, (cfg, _) in enumerate(SERVE_RIGS):
-            lat = [(q.t_done - q.t_arrival) * 1000 for q in reqs if q.rig == k]
-            per_rig[f"{k}:{cfg}"] = {"frames": len(lat)}
-        out["saturated"]["per_rig_frames"] = per_rig
+        sat = srv.run(reqs, time_scale=1000.0)
+        out["saturated"] = summarize(sat, time_scale=1000.0)
+        out["saturated"]["per_rig"] = summarize_per_rig(sat, len(pools), time_scale=1000.0)
         return out
     finally:
         srv.close()
