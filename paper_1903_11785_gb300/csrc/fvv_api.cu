@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "fvv_internal.h"
+#include "fvv_device.cuh"
 
 using namespace fvv;
 
@@ -279,6 +279,7 @@ void stage_end(fvv_rig* rig, int idx, cudaStream_t st) {
 }
 
 __global__ void k_zero_info(const __grid_constant__ Layout L, const __grid_constant__ SlotList sl) {
+    pdl_begin();
     uint32_t* p = reinterpret_cast<uint32_t*>(slot_ptr<SlotInfo>(L, sl.s[blockIdx.x], L.info));
     for (unsigned i = threadIdx.x; i < sizeof(SlotInfo) / 4; i += blockDim.x) p[i] = 0u;
 }
@@ -494,8 +495,7 @@ static cudaError_t enqueue_reconstruct(fvv_rig* rig, const SlotList& sl, cudaStr
     const Tuning& tu = rig->tune;
     const Grid g = tuned_grid_params(rig->grid, tu);
     const McTable mc{rig->mc_ntri, rig->mc_edges};
-    k_zero_info<<<sl.n, 32, 0, st>>>(rig->L, sl);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_zero_info, dim3(sl.n), dim3(32), 0, st, rig->L, sl);
     int t;
 #define FVV_STAGE(stage, call)                  \
     if (e == cudaSuccess) {                     \

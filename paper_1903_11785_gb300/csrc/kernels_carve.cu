@@ -32,6 +32,7 @@ __device__ __forceinline__ uint32_t nonzero_bytes4(uint32_t w) {
 // (blocks, cameras, frames).
 __global__ void __launch_bounds__(256) k_pack(const __grid_constant__ CamSet cams, const __grid_constant__ PackSrc a,
                                               const __grid_constant__ Layout L) {
+    pdl_begin();
     const Cam& c = cams.c[blockIdx.y];
     const uint8_t* src = a.src[blockIdx.z * (unsigned)cams.n + blockIdx.y];
     uint32_t* __restrict__ sil = slot_ptr<uint32_t>(L, a.slot[blockIdx.z], L.sil);
@@ -65,6 +66,7 @@ __global__ void __launch_bounds__(256) k_coarse_carve(const __grid_constant__ Ca
                                                       const __grid_constant__ Grid g,
                                                       const __grid_constant__ Layout L,
                                                       const __grid_constant__ SlotList sl) {
+    pdl_begin();
     __shared__ unsigned long long sh_t[32];
     __shared__ unsigned long long sh_n[32];
     const int slot = sl.s[blockIdx.y];
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(256) k_coarse_carve(const __grid_constant__ Ca
 // Clears the fine grids and resets the fine carve's tile counter.
 __global__ void __launch_bounds__(256) k_clear_fine(const __grid_constant__ Layout L,
                                                     const __grid_constant__ SlotList sl) {
+    pdl_begin();
     const int slot = sl.s[blockIdx.y];
     SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
     const uint32_t nwords = info->n_words;
@@ -348,6 +351,7 @@ __global__ void __launch_bounds__(256) k_fine_carve(const __grid_constant__ CamS
                                                     const __grid_constant__ Grid g,
                                                     const __grid_constant__ Layout L,
                                                     const __grid_constant__ SlotList sl) {
+    pdl_begin();
     __shared__ unsigned long long sh_t[32];
     __shared__ SmemCam sc[FVV_MAX_CAMS];
     const int ncam = NC > 0 ? NC : cams.n;
@@ -414,7 +418,8 @@ cudaError_t launch_pack(const CamSet& cams, const Layout& L, int n_frames, const
             a.slot[j] = slots[j0 + j];
             for (int n = 0; n < cams.n; ++n) a.src[j * cams.n + n] = src[(size_t)(j0 + j) * cams.n + n];
         }
-        k_pack<<<dim3(gx, cams.n, nf), 256, 0, st>>>(cams, a, L);
+        const cudaError_t e = launch_pdl(k_pack, dim3(gx, cams.n, nf), dim3(256), 0, st, cams, a, L);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -424,7 +429,7 @@ cudaError_t launch_coarse_carve(const CamSet& cams, const Grid& g, const Layout&
     const long long rows = (long long)g.nz * g.ny;    // a warp per row
     const int th = tu.threads[FVV_TUNE_COARSE];
     const int gx = tuned_grid(tu, FVV_TUNE_COARSE, sms, sl.n, rows * 32);
-#define FVV_LAUNCH(NC) k_coarse_carve<NC><<<dim3(gx, sl.n), th, 0, st>>>(cams, g, L, sl)
+#define FVV_LAUNCH(NC) launch_pdl(k_coarse_carve<NC>, dim3(gx, sl.n), dim3(th), 0, st, cams, g, L, sl)
     FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
     return cudaGetLastError();
@@ -433,20 +438,20 @@ cudaError_t launch_coarse_carve(const CamSet& cams, const Grid& g, const Layout&
 cudaError_t launch_fine_carve(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,
                               const Tuning& tu, cudaStream_t st) {
     const int gc = grid_x(sms, sl.n, (long long)g.max_fine_words, 256);
-    k_clear_fine<<<dim3(gc, sl.n), 256, 0, st>>>(L, sl);
+    launch_pdl(k_clear_fine, dim3(gc, sl.n), dim3(256), 0, st, L, sl);
     const int th = tu.threads[FVV_TUNE_FINE];
     const int gx = tuned_grid(tu, FVV_TUNE_FINE, sms, sl.n, (long long)g.max_fine_words * 32);
     // the tile shape (tile_y, tile_z) the k_filter of this sequence counted tiles with
     if (g.tile_y == 4 && g.tile_z == 4) {
-#define FVV_LAUNCH(NC) k_fine_carve<NC, 4, 4><<<dim3(gx, sl.n), th, 0, st>>>(cams, g, L, sl)
+#define FVV_LAUNCH(NC) launch_pdl(k_fine_carve<NC, 4, 4>, dim3(gx, sl.n), dim3(th), 0, st, cams, g, L, sl)
         FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
     } else if (g.tile_y == 8 && g.tile_z == 8) {
-#define FVV_LAUNCH(NC) k_fine_carve<NC, 8, 8><<<dim3(gx, sl.n), th, 0, st>>>(cams, g, L, sl)
+#define FVV_LAUNCH(NC) launch_pdl(k_fine_carve<NC, 8, 8>, dim3(gx, sl.n), dim3(th), 0, st, cams, g, L, sl)
         FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
     } else {
-#define FVV_LAUNCH(NC) k_fine_carve<NC, 4, 8><<<dim3(gx, sl.n), th, 0, st>>>(cams, g, L, sl)
+#define FVV_LAUNCH(NC) launch_pdl(k_fine_carve<NC, 4, 8>, dim3(gx, sl.n), dim3(th), 0, st, cams, g, L, sl)
         FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
     }

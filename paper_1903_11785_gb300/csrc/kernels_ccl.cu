@@ -106,6 +106,7 @@ __device__ __forceinline__ uint32_t coarse_word(const uint32_t* bits, const Grid
 // with a lane per voxel.
 __global__ void __launch_bounds__(256) k_union(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
                                                const __grid_constant__ SlotList sl) {
+    pdl_begin();
     const int slot = sl.s[blockIdx.y];
     const uint32_t* bits = slot_ptr<uint32_t>(L, slot, L.coarse);
     int* parent = slot_ptr<int>(L, slot, L.parent);
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(256) k_union(const __grid_constant__ Grid g, c
 // voxel's entry (see find_root_readonly).
 __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
                                                   const __grid_constant__ SlotList sl) {
+    pdl_begin();
     const int slot = sl.s[blockIdx.y];
     const uint32_t* bits = slot_ptr<uint32_t>(L, slot, L.coarse);
     int* parent = slot_ptr<int>(L, slot, L.parent);
@@ -202,6 +204,7 @@ __global__ void __launch_bounds__(256) k_compress(const __grid_constant__ Grid g
 // parent entry with -(i+1); reset the per-component statistics.
 __global__ void __launch_bounds__(1024) k_sort_roots(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
                                                      const __grid_constant__ SlotList sl) {
+    pdl_begin();
     __shared__ int key[kMaxComponents];
     const int slot = sl.s[blockIdx.x];
     SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
@@ -255,6 +258,7 @@ __global__ void __launch_bounds__(1024) k_sort_roots(const __grid_constant__ Gri
 // group, whose x range is the span of its lanes.
 __global__ void __launch_bounds__(256) k_stats(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
                                                const __grid_constant__ SlotList sl) {
+    pdl_begin();
     const int slot = sl.s[blockIdx.y];
     const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
     if (info->n_roots <= 0) return;
@@ -310,6 +314,7 @@ __global__ void __launch_bounds__(256) k_stats(const __grid_constant__ Grid g, c
 // word layout.  Capacity overflows set a flag and leave the slot with no ROIs.
 __global__ void __launch_bounds__(1024) k_filter(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
                                                  const __grid_constant__ SlotList sl) {
+    pdl_begin();
     __shared__ uint32_t sh[33];
     __shared__ unsigned long long sh64[33];
     __shared__ int s_fail;
@@ -408,16 +413,16 @@ __global__ void __launch_bounds__(1024) k_filter(const __grid_constant__ Grid g,
 cudaError_t launch_ccl(const Grid& g, const Layout& L, const SlotList& sl, int sms, cudaStream_t st) {
     const long long words = (long long)g.nz * g.ny * g.nxw;
     const int gx = grid_x(sms, sl.n, words, 256);
-    k_union<<<dim3(gx, sl.n), 256, 0, st>>>(g, L, sl);
-    k_compress<<<dim3(gx, sl.n), 256, 0, st>>>(g, L, sl);
-    k_sort_roots<<<sl.n, 1024, 0, st>>>(g, L, sl);
-    k_stats<<<dim3(gx, sl.n), 256, 0, st>>>(g, L, sl);
-    k_filter<<<sl.n, 1024, 0, st>>>(g, L, sl);
+    launch_pdl(k_union, dim3(gx, sl.n), dim3(256), 0, st, g, L, sl);
+    launch_pdl(k_compress, dim3(gx, sl.n), dim3(256), 0, st, g, L, sl);
+    launch_pdl(k_sort_roots, dim3(sl.n), dim3(1024), 0, st, g, L, sl);
+    launch_pdl(k_stats, dim3(gx, sl.n), dim3(256), 0, st, g, L, sl);
+    launch_pdl(k_filter, dim3(sl.n), dim3(1024), 0, st, g, L, sl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_filter(const Grid& g, const Layout& L, const SlotList& sl, cudaStream_t st) {
-    k_filter<<<sl.n, 1024, 0, st>>>(g, L, sl);
+    launch_pdl(k_filter, dim3(sl.n), dim3(1024), 0, st, g, L, sl);
     return cudaGetLastError();
 }
 

@@ -175,6 +175,7 @@ __device__ __forceinline__ int cell_case(const Nbhd& n, int b) {
 
 __global__ void __launch_bounds__(kChunk) k_mc_count(const __grid_constant__ Layout L, const __grid_constant__ SlotList sl,
                                                      const __grid_constant__ McTable mc) {
+    pdl_begin();
     __shared__ uint8_t s_ntri[256];
     __shared__ uint32_t sh[32];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) s_ntri[i] = mc.ntri[i];
@@ -223,6 +224,7 @@ __global__ void __launch_bounds__(kChunk) k_mc_count(const __grid_constant__ Lay
 // One block per slot: chunk sums -> exclusive chunk bases, totals, capacity.
 __global__ void __launch_bounds__(1024) k_mc_scan(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
                                                   const __grid_constant__ SlotList sl) {
+    pdl_begin();
     __shared__ uint32_t sh[33];
     const int slot = sl.s[blockIdx.x];
     SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
@@ -274,6 +276,7 @@ __device__ __forceinline__ uint64_t pack_trec(uint32_t w, int b, int j, int cs, 
 __global__ void __launch_bounds__(kChunk) k_mc_vertices(const __grid_constant__ Layout L,
                                                         const __grid_constant__ SlotList sl,
                                                         const __grid_constant__ McTable mc) {
+    pdl_begin();
     __shared__ uint32_t sh[33];
     __shared__ uint8_t s_ntri[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) s_ntri[i] = mc.ntri[i];
@@ -383,6 +386,7 @@ __device__ __forceinline__ bool segment_all_fg(const CamT& c, const uint32_t* __
 template <int NC>
 __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
                                                 const __grid_constant__ Layout L, const __grid_constant__ SlotList sl) {
+    pdl_begin();
     __shared__ unsigned long long sh_t[32];
     __shared__ SmemCam sc[FVV_MAX_CAMS];
     const int ncam = NC > 0 ? NC : cams.n;
@@ -523,6 +527,7 @@ __device__ __forceinline__ float cam_lambda(const Cam& c, const uint32_t* __rest
 template <int NC>
 __global__ void __launch_bounds__(256) k_lambda(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
                                                 const __grid_constant__ Layout L, const __grid_constant__ SlotList sl) {
+    pdl_begin();
     __shared__ unsigned long long sh_t[32];
     const int slot = sl.s[blockIdx.y];
     const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
@@ -577,6 +582,7 @@ __global__ void __launch_bounds__(256) k_lambda(const __grid_constant__ CamSet c
 __global__ void __launch_bounds__(256) k_mc_triangles(const __grid_constant__ Layout L,
                                                       const __grid_constant__ SlotList sl,
                                                       const __grid_constant__ McTable mc) {
+    pdl_begin();
     __shared__ uint8_t s_edges[256 * kMaxTriPerCell * 3];
     for (int i = threadIdx.x; i < 256 * kMaxTriPerCell * 3; i += blockDim.x) s_edges[i] = mc.edges[i];
     __syncthreads();
@@ -638,9 +644,9 @@ __global__ void __launch_bounds__(256) k_mc_triangles(const __grid_constant__ La
 cudaError_t launch_mc_prefix(const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc, int sms,
                              cudaStream_t st) {
     const int gc = grid_x(sms, sl.n, g.max_chunks, 1);
-    k_mc_count<<<dim3(gc, sl.n), kChunk, 0, st>>>(L, sl, mc);
-    k_mc_scan<<<sl.n, 1024, 0, st>>>(g, L, sl);
-    k_mc_vertices<<<dim3(gc, sl.n), kChunk, 0, st>>>(L, sl, mc);
+    launch_pdl(k_mc_count, dim3(gc, sl.n), dim3(kChunk), 0, st, L, sl, mc);
+    launch_pdl(k_mc_scan, dim3(sl.n), dim3(1024), 0, st, g, L, sl);
+    launch_pdl(k_mc_vertices, dim3(gc, sl.n), dim3(kChunk), 0, st, L, sl, mc);
     return cudaGetLastError();
 }
 
@@ -649,11 +655,11 @@ cudaError_t launch_bisect(const CamSet& cams, const Grid& g, const Layout& L, co
     const int th = tu.threads[FVV_TUNE_BISECT];
     const int gv = tuned_grid(tu, FVV_TUNE_BISECT, sms, sl.n, g.max_verts);
     if (g.rule == FVV_SURFACE_LAMBDA) {
-#define FVV_LAUNCH(NC) k_lambda<NC><<<dim3(gv, sl.n), th, 0, st>>>(cams, g, L, sl)
+#define FVV_LAUNCH(NC) launch_pdl(k_lambda<NC>, dim3(gv, sl.n), dim3(th), 0, st, cams, g, L, sl)
         FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
     } else {
-#define FVV_LAUNCH(NC) k_bisect<NC><<<dim3(gv, sl.n), th, 0, st>>>(cams, g, L, sl)
+#define FVV_LAUNCH(NC) launch_pdl(k_bisect<NC>, dim3(gv, sl.n), dim3(th), 0, st, cams, g, L, sl)
         FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
     }
@@ -663,7 +669,7 @@ cudaError_t launch_bisect(const CamSet& cams, const Grid& g, const Layout& L, co
 cudaError_t launch_mc_triangles(const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc, int sms,
                                 const Tuning& tu, cudaStream_t st) {
     const int gw = tuned_grid(tu, FVV_TUNE_TRIANGLES, sms, sl.n, g.max_tris);
-    k_mc_triangles<<<dim3(gw, sl.n), tu.threads[FVV_TUNE_TRIANGLES], 0, st>>>(L, sl, mc);
+    launch_pdl(k_mc_triangles, dim3(gw, sl.n), dim3(tu.threads[FVV_TUNE_TRIANGLES]), 0, st, L, sl, mc);
     return cudaGetLastError();
 }
 

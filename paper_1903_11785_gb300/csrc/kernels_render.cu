@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(256) k_init_depth(const __grid_constant__ Layo
 __global__ void __launch_bounds__(256) k_clear_depth(const __grid_constant__ CamSet cams,
                                                      const __grid_constant__ Layout L,
                                                      const __grid_constant__ SlotList sl) {
+    pdl_begin();
     const int slot = sl.s[blockIdx.z];
     const Cam& c = cams.c[blockIdx.y];
     const int4 b = slot_ptr<int4>(L, slot, L.dbox)[blockIdx.y];
@@ -52,6 +53,7 @@ __global__ void __launch_bounds__(256) k_clear_depth(const __grid_constant__ Cam
 // camera.  One block per slot, a thread per (camera, ROI).
 __global__ void k_depth_box(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
                             const __grid_constant__ Layout L, const __grid_constant__ SlotList sl) {
+    pdl_begin();
     const int slot = sl.s[blockIdx.x];
     int4* box = slot_ptr<int4>(L, slot, L.dbox);
     for (int n = threadIdx.x; n < cams.n; n += blockDim.x) box[n] = make_int4(INT_MAX, -1, INT_MAX, -1);
@@ -239,6 +241,7 @@ __device__ __forceinline__ void zq_draw(const Cam& c, const ZQueue& q, int i, ui
 // one per lane, instead of by 30% of the lanes while the rest wait.
 __global__ void __launch_bounds__(256) k_zbuffer(const __grid_constant__ CamSet cams, const __grid_constant__ Layout L,
                                                  const __grid_constant__ SlotList sl) {
+    pdl_begin();
     __shared__ ZQueue zq[8];   // one per warp (at most 256 threads)
     const int slot = sl.s[blockIdx.z];
     const Cam& c = cams.c[blockIdx.y];
@@ -336,6 +339,7 @@ __device__ __forceinline__ int colour_point(const CamSet& cams, const int* rank_
 __global__ void __launch_bounds__(256) k_colour(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
                                                 const __grid_constant__ Layout L,
                                                 const __grid_constant__ ColourBatch cb) {
+    pdl_begin();
     __shared__ int rank_cam[FVV_MAX_CAMS];
     const int slot = cb.slot[blockIdx.y];
     rank_cameras(cams, cb.view[blockIdx.y], rank_cam);
@@ -450,17 +454,17 @@ cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, con
                          size_t depth_bytes, const Tuning& tu, cudaStream_t st) {
     (void)depth_bytes;
     const int gc = std::max(1, sms * 4 / std::max(1, sl.n * cams.n));
-    k_clear_depth<<<dim3(gc, cams.n, sl.n), 256, 0, st>>>(cams, L, sl);
-    k_depth_box<<<sl.n, 256, 0, st>>>(cams, g, L, sl);
+    launch_pdl(k_clear_depth, dim3(gc, cams.n, sl.n), dim3(256), 0, st, cams, L, sl);
+    launch_pdl(k_depth_box, dim3(sl.n), dim3(256), 0, st, cams, g, L, sl);
     const int gz = tuned_grid(tu, FVV_TUNE_ZBUFFER, sms, sl.n, (long long)g.max_tris, cams.n);
-    k_zbuffer<<<dim3(gz, cams.n, sl.n), tu.threads[FVV_TUNE_ZBUFFER], 0, st>>>(cams, L, sl);
+    launch_pdl(k_zbuffer, dim3(gz, cams.n, sl.n), dim3(tu.threads[FVV_TUNE_ZBUFFER]), 0, st, cams, L, sl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_colour(const CamSet& cams, const Grid& g, const Layout& L, const ColourBatch& cb, int sms,
                           int total_slots, cudaStream_t st) {
     const int gv = grid_x(sms, total_slots, g.max_verts, 256);
-    k_colour<<<dim3(gv, cb.n), 256, 0, st>>>(cams, g, L, cb);
+    launch_pdl(k_colour, dim3(gv, cb.n), dim3(256), 0, st, cams, g, L, cb);
     return cudaGetLastError();
 }
 
