@@ -58,8 +58,8 @@ FP32_LANES_PER_SM = 128
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of a 4-frame launch of
 # the current kernels, scaled to a launch by its frame count.  None for a
 # kernel changed since that capture.
-DRAM_BYTES_PER_FRAME = {"fine": 7.290368e6 / 4, "bisect": (17.209856e6 + 15104) / 4,
-                        "coarse": None, "depth": (178.862848e6 + 11.137536e6) / 4}
+DRAM_BYTES_PER_FRAME = {"fine": 7.29472e6 / 4, "bisect": (17.210368e6 + 9216) / 4,
+                        "coarse": (4.332032e6 + 5120) / 4, "depth": (178.810368e6 + 10.8864e6) / 4}
 
 
 def parse_args():
