@@ -243,10 +243,21 @@ fvv_status fvv_colour(fvv_rig *rig, const int *slots, int n_slots, const uint8_t
                       int rgb_on_device, const float *viewpoints, void *stream);
 
 /* Synchronise `stream` and read slot's counts; returns FVV_ERR_CAPACITY if a
- * capacity was exceeded (counts->flags says which), else FVV_OK. */
+ * capacity was exceeded (counts->flags says which), else FVV_OK.  The counts
+ * are those the paper's pipeline produces and reports: components before and
+ * after the noise filter of Eq. (1) (Sec. II-B-2), the occupied coarse
+ * voxels of the sparse hull (Sec. II-B-1; the paper counts them for its
+ * volleyball scene in Sec. II-B), the mesh's vertices and triangles
+ * (Sec. II-C), and the camera tests of the hulls and the surface step, the
+ * work behind Table II's stage times. */
 fvv_status fvv_get_counts(fvv_rig *rig, int slot, fvv_counts *counts, void *stream);
 
-/* Copy slot's results into caller-owned buffers (any may be NULL):
+/* The outputs of Sec. II-B to II-D for a slot: the objects with their 3D ROI
+ * (Sec. II-B-2, II-B-3), the mesh of each (Sec. II-C: vertices on the hull
+ * boundary, triangles of the marching-cubes table) and each vertex's colour
+ * and source camera (Sec. II-D-2, II-E), which is what the paper sends to
+ * the client for rendering.
+ * Copy slot's results into caller-owned buffers (any may be NULL):
  * rois[n_rois], verts[n_verts*3] float, tris[n_tris*3] uint32 (indices into
  * the slot's vertices), rgb[n_verts*3] uint8, cam[n_verts] int32.  Sizes come
  * from fvv_get_counts.  dst_on_device says whether the buffers are device
