@@ -592,7 +592,6 @@ def run_ours(args):
                      tris=torch.empty((c["n_tris"], 3), dtype=torch.int32).pin_memory(),
                      rgb=torch.empty((c["n_verts"], 3), dtype=torch.uint8).pin_memory(),
                      cam=torch.empty((c["n_verts"],), dtype=torch.int32).pin_memory()) for c in cnt]
-        vp_ = fvv._vp
         # masks and RGB stay in pinned host memory: the masks are copied to
         # the slots' staging by the copy engines (which need no SMs, so the
         # copies overlap other groups' kernels), the colour kernel reads only
@@ -608,7 +607,7 @@ def run_ours(args):
         groups = [slots[g:g + E2E_GROUP] for g in range(0, F, E2E_GROUP)]
 
         def e2e_step():
-            # fvv_get_results waits for its slot's work (it reads the counts),
+            # reading a group back waits for its work (it reads the counts),
             # so the next group is queued before the previous one is read back
             def compute(grp, st):
                 with torch.cuda.stream(st):
@@ -617,11 +616,8 @@ def run_ours(args):
                     r.colour(grp, rgb_h[grp[0]:grp[-1] + 1], vps[grp[0]:grp[-1] + 1], stream=st, in_place=True)
 
             def read_back(grp, st):
-                for i in grp:
-                    o = outs[i]
-                    fvv._check(fvv._lib.fvv_get_results(r.ptr, i, None, vp_(o["verts"].data_ptr()),
-                                                       vp_(o["tris"].data_ptr()), vp_(o["rgb"].data_ptr()),
-                                                       vp_(o["cam"].data_ptr()), 0, fvv._stream(st)), r.ptr)
+                # one wait for the group's counts, then its copies (fvv_get_results_batch)
+                fvv.fvv_get_results_batch(r.ptr, grp, [outs[i] for i in grp], stream=st)
             pending = []
             for gi, grp in enumerate(groups):
                 st = e2e_streams[gi % E2E_STREAMS]

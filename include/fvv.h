@@ -265,6 +265,32 @@ fvv_status fvv_get_counts(fvv_rig *rig, int slot, fvv_counts *counts, void *stre
 fvv_status fvv_get_results(fvv_rig *rig, int slot, fvv_roi *rois, float *verts, uint32_t *tris,
                            uint8_t *rgb, int32_t *cam, int dst_on_device, void *stream);
 
+/* Destination of one slot's results for fvv_get_results_batch: caller-owned
+ * buffers (any may be NULL; sized from an earlier fvv_get_counts of a
+ * reconstruction of the same frame, or generously), and the slot's counts,
+ * written by the call. */
+typedef struct {
+    fvv_counts counts;     /* out                                             */
+    fvv_roi *rois;         /* must be NULL (ROIs: fvv_get_results)            */
+    float *verts;          /* n_verts*3 float                                 */
+    uint32_t *tris;        /* n_tris*3 uint32                                 */
+    uint8_t *rgb;          /* n_verts*3 uint8                                 */
+    int32_t *cam;          /* n_verts int32                                   */
+} fvv_results_dst;
+
+/* The outputs of Sec. II-C to II-E (as fvv_get_results returns them) for
+ * several slots with one wait: the counts of all n_slots slots (1..256) are
+ * read together, with one synchronisation of `stream`, then the copies of
+ * every slot's vertices, triangles, colours and cameras into dst[i]'s
+ * buffers are enqueued on `stream` (wait for the stream before reading
+ * them).  A slot whose reconstruction exceeded a capacity gets its counts
+ * but no copies, and the call returns FVV_ERR_CAPACITY; a slot not
+ * reconstructed gives FVV_ERR_NOT_READY and a bad argument
+ * FVV_ERR_INVALID_ARG, both with nothing copied.  For callers that read many
+ * frames back (one wait per group of frames instead of one per frame). */
+fvv_status fvv_get_results_batch(fvv_rig *rig, const int *slots, int n_slots, fvv_results_dst *dst,
+                                 int dst_on_device, void *stream);
+
 /* Size in bytes of a debug view of slot (fvv_get_counts must have been
  * called after the reconstruction for FINE_BITS). */
 fvv_status fvv_debug_bytes(fvv_rig *rig, int slot, int what, size_t *bytes);

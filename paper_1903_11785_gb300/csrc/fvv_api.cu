@@ -39,6 +39,7 @@ struct fvv_rig {
     struct Graph { std::vector<int> slots; cudaGraphExec_t exec; unsigned long long used; };
     std::vector<Graph> graph_cache;
     unsigned long long graph_clock = 0;
+    SlotInfo* host_info = nullptr;   // page-locked, FVV_MAX_BATCH entries: counts read by fvv_get_results_batch
 };
 
 namespace {
@@ -369,8 +370,11 @@ fvv_status fvv_create_rig(const fvv_rig_desc* desc, const fvv_recon_params* para
     // box its slot's previous z-buffer wrote
     if (e == cudaSuccess) e = launch_init_depth(rig->cams, rig->L, rig->max_slots, rig->sms, nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&rig->host_info), FVV_MAX_BATCH * sizeof(SlotInfo),
+                                            cudaHostAllocDefault);
     if (e != cudaSuccess) {
         if (rig->own_arena) cudaFree(rig->arena);
+        if (rig->host_info) cudaFreeHost(rig->host_info);
         delete rig;
         return cuda_fail(nullptr, e, "initialising the rig");
     }
@@ -383,6 +387,7 @@ fvv_status fvv_destroy_rig(fvv_rig* rig) {
     cudaError_t e = cudaDeviceSynchronize();
     for (cudaEvent_t ev : rig->events) cudaEventDestroy(ev);
     for (auto& gr : rig->graph_cache) cudaGraphExecDestroy(gr.exec);
+    if (rig->host_info) cudaFreeHost(rig->host_info);
     if (rig->own_arena) {
         cudaError_t f = cudaFree(rig->arena);
         if (e == cudaSuccess) e = f;
@@ -818,16 +823,10 @@ fvv_status fvv_get_timing(fvv_rig* rig, float* ms, int* calls) {
     return FVV_OK;
 }
 
-fvv_status fvv_get_counts(fvv_rig* rig, int slot, fvv_counts* out, void* stream) {
-    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
-    if (!check_slot(rig, slot) || !out) return fail(rig, FVV_ERR_INVALID_ARG, "bad slot or NULL counts");
-    if (rig->state[slot] < 2) return fail(rig, FVV_ERR_NOT_READY, "slot was not reconstructed");
-    const cudaStream_t st = static_cast<cudaStream_t>(stream);
-    SlotInfo info;
-    cudaError_t e = cudaMemcpyAsync(&info, slot_ptr<SlotInfo>(rig->L, slot, rig->L.info), sizeof(info),
-                                    cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_get_counts");
+}  // extern "C"
+
+// The counts of a slot from its device bookkeeping; true if a capacity was exceeded.
+static bool fill_counts(const SlotInfo& info, fvv_counts* out) {
     std::memset(out, 0, sizeof(*out));
     out->flags = info.flags;
     out->n_components = info.n_roots;
@@ -842,7 +841,71 @@ fvv_status fvv_get_counts(fvv_rig* rig, int slot, fvv_counts* out, void* stream)
     out->lookups_fine = (long long)info.look_fine;
     out->lookups_bisect = (long long)info.look_bisect;
     const unsigned cap = FVV_FLAG_ROOTS | FVV_FLAG_ROIS | FVV_FLAG_FINE | FVV_FLAG_VERTS | FVV_FLAG_TRIS | FVV_FLAG_LOOP;
-    if (info.flags & cap) return fail(rig, FVV_ERR_CAPACITY, "a capacity was exceeded (see flags)");
+    return (info.flags & cap) != 0u;
+}
+
+// Enqueue the copies of a slot's vertices, triangles, colours and cameras
+// (counts c) into caller-owned buffers (any may be NULL).
+static cudaError_t copy_results(fvv_rig* rig, int slot, const fvv_counts& c, float* verts, uint32_t* tris,
+                                uint8_t* rgb, int32_t* cam, cudaMemcpyKind kind, cudaStream_t st) {
+    const Layout& L = rig->L;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess && verts && c.n_verts)
+        e = cudaMemcpyAsync(verts, slot_ptr<float>(L, slot, L.verts), 12 * (size_t)c.n_verts, kind, st);
+    if (e == cudaSuccess && tris && c.n_tris)
+        e = cudaMemcpyAsync(tris, slot_ptr<uint32_t>(L, slot, L.tris), 12 * (size_t)c.n_tris, kind, st);
+    if (e == cudaSuccess && rgb && c.n_verts)
+        e = cudaMemcpyAsync(rgb, slot_ptr<uint8_t>(L, slot, L.vrgb), 3 * (size_t)c.n_verts, kind, st);
+    if (e == cudaSuccess && cam && c.n_verts)
+        e = cudaMemcpyAsync(cam, slot_ptr<int32_t>(L, slot, L.vcam), 4 * (size_t)c.n_verts, kind, st);
+    return e;
+}
+
+extern "C" {
+
+fvv_status fvv_get_counts(fvv_rig* rig, int slot, fvv_counts* out, void* stream) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    if (!check_slot(rig, slot) || !out) return fail(rig, FVV_ERR_INVALID_ARG, "bad slot or NULL counts");
+    if (rig->state[slot] < 2) return fail(rig, FVV_ERR_NOT_READY, "slot was not reconstructed");
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    SlotInfo info;
+    cudaError_t e = cudaMemcpyAsync(&info, slot_ptr<SlotInfo>(rig->L, slot, rig->L.info), sizeof(info),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_get_counts");
+    if (fill_counts(info, out)) return fail(rig, FVV_ERR_CAPACITY, "a capacity was exceeded (see flags)");
+    return FVV_OK;
+}
+
+fvv_status fvv_get_results_batch(fvv_rig* rig, const int* slots, int n_slots, fvv_results_dst* dst,
+                                 int dst_on_device, void* stream) {
+    if (!rig) return fail(nullptr, FVV_ERR_INVALID_ARG, "rig is NULL");
+    if (!slots || !dst || n_slots < 1 || n_slots > FVV_MAX_BATCH)
+        return fail(rig, FVV_ERR_INVALID_ARG, "slots and dst must list 1..256 slots");
+    for (int i = 0; i < n_slots; ++i) {
+        if (!check_slot(rig, slots[i])) return fail(rig, FVV_ERR_INVALID_ARG, "slot out of range");
+        if (rig->state[slots[i]] < 2) return fail(rig, FVV_ERR_NOT_READY, "slot was not reconstructed");
+        if (dst[i].rois) return fail(rig, FVV_ERR_INVALID_ARG, "ROIs are read by fvv_get_results only");
+    }
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n_slots && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(rig->host_info + i, slot_ptr<SlotInfo>(rig->L, slots[i], rig->L.info), sizeof(SlotInfo),
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the one wait of the call
+    if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_get_results_batch");
+    bool over = false;
+    const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int i = 0; i < n_slots && e == cudaSuccess; ++i) {
+        fvv_results_dst& d = dst[i];
+        if (fill_counts(rig->host_info[i], &d.counts)) {
+            over = true;
+            continue;
+        }
+        e = copy_results(rig, slots[i], d.counts, d.verts, d.tris, d.rgb, d.cam, kind, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_get_results_batch");
+    if (over) return fail(rig, FVV_ERR_CAPACITY, "a capacity was exceeded in some slot (see its flags)");
     return FVV_OK;
 }
 
@@ -878,15 +941,7 @@ fvv_status fvv_get_results(fvv_rig* rig, int slot, fvv_roi* rois, float* verts, 
         if (dst_on_device) e = cudaMemcpyAsync(rois, h.data(), sizeof(fvv_roi) * c.n_rois, cudaMemcpyHostToDevice, st);
         else std::memcpy(rois, h.data(), sizeof(fvv_roi) * c.n_rois);
     }
-    const Layout& L = rig->L;
-    if (e == cudaSuccess && verts && c.n_verts)
-        e = cudaMemcpyAsync(verts, slot_ptr<float>(L, slot, L.verts), 12 * (size_t)c.n_verts, kind, st);
-    if (e == cudaSuccess && tris && c.n_tris)
-        e = cudaMemcpyAsync(tris, slot_ptr<uint32_t>(L, slot, L.tris), 12 * (size_t)c.n_tris, kind, st);
-    if (e == cudaSuccess && rgb && c.n_verts)
-        e = cudaMemcpyAsync(rgb, slot_ptr<uint8_t>(L, slot, L.vrgb), 3 * (size_t)c.n_verts, kind, st);
-    if (e == cudaSuccess && cam && c.n_verts)
-        e = cudaMemcpyAsync(cam, slot_ptr<int32_t>(L, slot, L.vcam), 4 * (size_t)c.n_verts, kind, st);
+    if (e == cudaSuccess) e = copy_results(rig, slot, c, verts, tris, rgb, cam, kind, st);
     if (e != cudaSuccess) return cuda_fail(rig, e, "fvv_get_results");
     return FVV_OK;
 }

@@ -80,6 +80,11 @@ class Counts(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
+class ResultsDst(C.Structure):
+    _fields_ = [("counts", Counts), ("rois", C.c_void_p), ("verts", C.c_void_p), ("tris", C.c_void_p),
+                ("rgb", C.c_void_p), ("cam", C.c_void_p)]
+
+
 _vp = C.c_void_p
 _sigs = {
     "fvv_query_arena": ([C.POINTER(RigDesc), C.POINTER(ReconParams), C.POINTER(C.c_size_t)], C.c_int),
@@ -91,6 +96,7 @@ _sigs = {
     "fvv_colour": ([_vp, C.POINTER(C.c_int), C.c_int, C.POINTER(_vp), C.c_int, C.POINTER(C.c_float), _vp], C.c_int),
     "fvv_get_counts": ([_vp, C.c_int, C.POINTER(Counts), _vp], C.c_int),
     "fvv_get_results": ([_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp], C.c_int),
+    "fvv_get_results_batch": ([_vp, C.POINTER(C.c_int), C.c_int, C.POINTER(ResultsDst), C.c_int, _vp], C.c_int),
     "fvv_debug_bytes": ([_vp, C.c_int, C.c_int, C.POINTER(C.c_size_t)], C.c_int),
     "fvv_get_debug": ([_vp, C.c_int, C.c_int, _vp, C.c_size_t, _vp], C.c_int),
     "fvv_mc_table": ([_vp, _vp], C.c_int),
@@ -321,6 +327,27 @@ def fvv_get_results(rig_ptr, slot, device="cuda", stream=None) -> dict:
     out_rois = [{f: (tuple(getattr(r, f)) if isinstance(getattr(r, f), C.Array) else getattr(r, f))
                  for f, _ in Roi._fields_} for r in rois[:K]]
     return dict(counts=c, rois=out_rois, verts=verts, tris=tris, rgb=rgb, cam=cam)
+
+
+def fvv_get_results_batch(rig_ptr, slots, outs, stream=None):
+    """Results of several slots with one wait.  outs[i]: dict of tensors
+    "verts", "tris", "rgb", "cam" (any may be missing), all in host memory
+    (pinned, for asynchronous copies) or all on the device, large enough for
+    slot slots[i].  Returns each slot's counts; the copies are enqueued on
+    the stream."""
+    n = len(slots)
+    dst = (ResultsDst * n)()
+    on_dev = None
+    for d, o in zip(dst, outs):
+        for k in ("verts", "tris", "rgb", "cam"):
+            t = o.get(k)
+            if t is not None:
+                on_dev = t.is_cuda if on_dev is None else on_dev
+                assert t.is_cuda == on_dev and t.is_contiguous()
+                setattr(d, k, t.data_ptr())
+    arr = (C.c_int * n)(*slots)
+    _check(_lib.fvv_get_results_batch(rig_ptr, arr, n, dst, int(bool(on_dev)), _stream(stream)), rig_ptr)
+    return [d.counts.as_dict() for d in dst]
 
 
 def fvv_set_timing(rig_ptr, enable: bool):

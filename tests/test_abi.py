@@ -101,3 +101,4 @@ def test_null_arguments_are_rejected(fvv):
     assert fvv._lib.fvv_get_counts(None, 0, None, None) == fvv.FVV_ERR_INVALID_ARG
     assert fvv._lib.fvv_mc_table(None, None) == fvv.FVV_ERR_INVALID_ARG
     assert fvv._lib.fvv_debug_label_coarse(None, 0, None, None) == fvv.FVV_ERR_INVALID_ARG
+    assert fvv._lib.fvv_get_results_batch(None, None, 0, None, 0, None) == fvv.FVV_ERR_INVALID_ARG

@@ -274,6 +274,55 @@ def test_table1_shapes_bit_exact(config):
     assert len(ref.rois) >= (12 if config == "volleyball_t1" else 2)
 
 
+def test_results_batch_equals_per_slot_results():
+    """fvv_get_results_batch (one wait for a group of slots, copies into
+    pinned host buffers and into device buffers) returns what fvv_get_results
+    returns slot by slot; a slot over capacity gets its counts and no copies;
+    a slot never reconstructed is refused."""
+    from paper_1903_11785_gb300 import fvv
+    rig = make_rig("tiny")
+    frames = [make_frame("tiny", i, rig=rig)[1] for i in range(3)]
+    r = fvv.Rig(rig, max_slots=4, host_staging=0, max_fine_words=1 << 16)
+    try:
+        for s, fr in enumerate(frames):
+            r.upload_silhouettes(s, fr.masks.cuda())
+        r.reconstruct([0, 1, 2])
+        r.colour([0, 1, 2], [fr.rgb.cuda() for fr in frames], np.stack([fr.viewpoint for fr in frames]))
+        torch.cuda.synchronize()
+        ref = [r.results(s) for s in range(3)]
+        for device in ("cpu", "cuda"):
+            outs = []
+            for c in (x["counts"] for x in ref):
+                mk = (lambda shape, dt: torch.full(shape, 7, dtype=dt).pin_memory()) if device == "cpu" else \
+                     (lambda shape, dt: torch.full(shape, 7, dtype=dt, device="cuda"))
+                outs.append(dict(verts=mk((c["n_verts"], 3), torch.float32), tris=mk((c["n_tris"], 3), torch.int32),
+                                 rgb=mk((c["n_verts"], 3), torch.uint8), cam=mk((c["n_verts"],), torch.int32)))
+            counts = fvv.fvv_get_results_batch(r.ptr, [2, 0, 1], [outs[2], outs[0], outs[1]])
+            torch.cuda.synchronize()
+            assert [counts[1], counts[2], counts[0]] == [x["counts"] for x in ref]
+            for o, x in zip(outs, ref):
+                for k in ("verts", "tris", "rgb", "cam"):
+                    assert torch.equal(o[k].cpu(), x[k].cpu()), k
+        with pytest.raises(fvv.FvvError) as e:
+            fvv.fvv_get_results_batch(r.ptr, [0, 3], [{}, {}])
+        assert e.value.status == fvv.FVV_ERR_NOT_READY
+    finally:
+        r.close()
+    # a slot over its vertex capacity: counts with the flag, nothing copied
+    r = fvv.Rig(rig, max_slots=2, host_staging=0, max_fine_words=1 << 16, max_verts=1 << 10)
+    try:
+        r.upload_silhouettes(0, frames[0].masks.cuda())
+        r.reconstruct([0])
+        v = torch.full((8, 3), 5.0).pin_memory()
+        with pytest.raises(fvv.FvvError) as e:
+            fvv.fvv_get_results_batch(r.ptr, [0], [dict(verts=v)])
+        assert e.value.status == fvv.FVV_ERR_CAPACITY
+        torch.cuda.synchronize()
+        assert bool((v == 5.0).all())
+    finally:
+        r.close()
+
+
 def test_judo_frame_bit_exact():
     rig, fr = make_frame("judo", 0)
     g = run_gpu(rig, [fr])[0]
