@@ -422,12 +422,14 @@ enum { FVV_TILE_4x4x8 = 0, FVV_TILE_4x4x4 = 1, FVV_TILE_4x8x8 = 2, FVV_N_TILES =
 
 /* Ints of a tuning configuration: threads per block of each FVV_TUNE_*
  * kernel, then its resident blocks per SM, then the fine-hull tile shape
- * (FVV_TILE_*). */
-#define FVV_TUNE_INTS (2 * FVV_N_TUNE + 1)
+ * (FVV_TILE_*), then the cameras one z-buffer block serves (1, 2 or 4; each
+ * triangle record is read once per that many cameras). */
+#define FVV_TUNE_INTS (2 * FVV_N_TUNE + 2)
 
 /* Time candidate launch shapes (threads per block 64/128/256 x resident
- * blocks per SM 2/4/8/16/32) of each tunable kernel, and for the fine hull
- * each tile shape too, on the given slots, which must hold reconstructed
+ * blocks per SM 2/4/8/16/32/64) of each tunable kernel, for the fine hull
+ * each tile shape too and for the z-buffer each number of cameras per block
+ * (1, 2, 4), on the given slots, which must hold reconstructed
  * frames; keep the fastest, then reconstruct the slots once more with it so
  * that their results and counts are those of one reconstruction.  Results
  * never depend on the choice.  Synchronises `stream`.  config (may be NULL)
@@ -436,7 +438,7 @@ fvv_status fvv_autotune(fvv_rig *rig, const int *slots, int n_slots, void *strea
 
 /* Read or set the configuration (FVV_TUNE_INTS ints as for fvv_autotune);
  * threads must be 32..256 in steps of 32, blocks per SM 1..64, the tile
- * shape one of FVV_TILE_*. */
+ * shape one of FVV_TILE_*, the z-buffer cameras per block 1, 2 or 4. */
 fvv_status fvv_get_tuning(fvv_rig *rig, int *config);
 fvv_status fvv_set_tuning(fvv_rig *rig, const int *config);
 

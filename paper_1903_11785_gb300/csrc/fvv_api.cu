@@ -586,6 +586,7 @@ fvv_status fvv_get_tuning(fvv_rig* rig, int* config) {
         config[FVV_N_TUNE + k] = rig->tune.waves[k];
     }
     config[2 * FVV_N_TUNE] = rig->tune.fine_tile;
+    config[2 * FVV_N_TUNE + 1] = rig->tune.zb_cams;
     return FVV_OK;
 }
 
@@ -598,11 +599,14 @@ fvv_status fvv_set_tuning(fvv_rig* rig, const int* config) {
     }
     const int tile = config[2 * FVV_N_TUNE];
     if (tile < 0 || tile >= FVV_N_TILES) return fail(rig, FVV_ERR_INVALID_ARG, "tile shape must be one of FVV_TILE_*");
+    const int zc = config[2 * FVV_N_TUNE + 1];
+    if (zc != 1 && zc != 2 && zc != 4) return fail(rig, FVV_ERR_INVALID_ARG, "z-buffer cameras per block must be 1, 2 or 4");
     for (int k = 0; k < FVV_N_TUNE; ++k) {
         rig->tune.threads[k] = config[k];
         rig->tune.waves[k] = config[FVV_N_TUNE + k];
     }
     rig->tune.fine_tile = tile;
+    rig->tune.zb_cams = zc;
     cudaDeviceSynchronize();
     drop_graphs(rig);
     return FVV_OK;
@@ -634,17 +638,20 @@ fvv_status fvv_autotune(fvv_rig* rig, const int* slots, int n_slots, void* strea
         }
     };
     const int threads[] = {64, 128, 256};
-    const int waves[] = {2, 4, 8, 16, 32};
+    const int waves[] = {2, 4, 8, 16, 32, 64};
     for (int knob = 0; knob < FVV_N_TUNE && e == cudaSuccess; ++knob) {
         float best = 1e30f;
         Tuning keep = rig->tune;
-        const int n_tiles = knob == FVV_TUNE_FINE ? FVV_N_TILES : 1;
+        // the fine hull also tries each tile shape, the z-buffer each number
+        // of cameras per block (1, 2, 4)
+        const int n_tiles = knob == FVV_TUNE_FINE ? FVV_N_TILES : knob == FVV_TUNE_ZBUFFER ? 3 : 1;
         for (int tile = 0; tile < n_tiles && e == cudaSuccess; ++tile)
         for (int th : threads)
             for (int wv : waves) {
                 Tuning tu = rig->tune;
                 tu.threads[knob] = th;
                 tu.waves[knob] = wv;
+                if (knob == FVV_TUNE_ZBUFFER) tu.zb_cams = 1 << tile;
                 if (knob == FVV_TUNE_FINE) {
                     tu.fine_tile = tile;
                     // the ROI table's tile offsets for this shape (not timed)
@@ -664,6 +671,7 @@ fvv_status fvv_autotune(fvv_rig* rig, const int* slots, int n_slots, void* strea
                     keep.threads[knob] = th;
                     keep.waves[knob] = wv;
                     keep.fine_tile = tu.fine_tile;
+                    keep.zb_cams = tu.zb_cams;
                 }
             }
         rig->tune = keep;

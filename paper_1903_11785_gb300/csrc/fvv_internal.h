@@ -152,6 +152,7 @@ struct Tuning {
     int threads[FVV_N_TUNE];
     int waves[FVV_N_TUNE];
     int fine_tile;       // index into kFineTiles
+    int zb_cams;         // cameras per z-buffer block: 1, 2 or 4
 };
 
 // The grid with the tuned fine-carve tile shape.
@@ -170,6 +171,7 @@ inline Tuning default_tuning() {
     }
     t.waves[FVV_TUNE_ZBUFFER] = 16;
     t.fine_tile = FVV_TILE_4x4x8;
+    t.zb_cams = 1;
     return t;
 }
 

@@ -135,8 +135,8 @@ __device__ __forceinline__ bool raster_setup(const Cam& c, const float* X, const
 }
 
 // The second part: the triangle is skipped if its projected area is zero;
-// `sink(pixel)` is called for each candidate pixel (row-major index in c's
-// image) whose centre p lies in the closed box of the projection and on the
+// `sink(pixel)` is called for each candidate pixel (row-major index in an
+// image W pixels wide) whose centre p lies in the closed box of the projection and on the
 // inner side of (or on) all three edges, either winding.  Everything is
 // decided on the homogeneous image points (x', y', w') without dividing: the
 // edge function of edge (i, j) at p is (p_x a - p_y b) + c with
@@ -145,7 +145,7 @@ __device__ __forceinline__ bool raster_setup(const Cam& c, const float* X, const
 // (x_0 a_12 - y_0 b_12) + w_0 c_12 is, and the box test uses the exact signs
 // of p w_j - x_j from one FMA each.
 template <class Sink>
-__device__ __forceinline__ void raster_pixels(const Cam& c, const TriSetup& s, Sink&& sink) {
+__device__ __forceinline__ void raster_pixels(unsigned W, const TriSetup& s, Sink&& sink) {
     const float* xh = s.xh;
     const float* yh = s.yh;
     const float* wh = s.wh;
@@ -173,7 +173,7 @@ __device__ __forceinline__ void raster_pixels(const Cam& c, const TriSetup& s, S
             const float e1 = fadd(fsub(fmul(pcx, ea[1]), fmul(pcy, eb[1])), ec[1]);
             const float e2 = fadd(fsub(fmul(pcx, ea[2]), fmul(pcy, eb[2])), ec[2]);
             const bool in = (e0 >= 0.0f && e1 >= 0.0f && e2 >= 0.0f) || (e0 <= 0.0f && e1 <= 0.0f && e2 <= 0.0f);
-            if (in) sink((size_t)yy * (unsigned)c.W + xx);
+            if (in) sink((size_t)yy * W + xx);
         }
     }
 }
@@ -183,19 +183,22 @@ template <class Sink>
 __device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const float* Y, const float* Z,
                                            Sink&& sink) {
     TriSetup s;
-    if (raster_setup(c, X, Y, Z, s)) raster_pixels(c, s, sink);
+    if (raster_setup(c, X, Y, Z, s)) raster_pixels((unsigned)c.W, s, sink);
 }
 
 // A warp's queue of (triangle, camera) pairs whose candidate box is not
-// empty: the homogeneous vertices, the box and the squared distance.
+// empty: the homogeneous vertices, the box, the squared distance and, when a
+// block serves several cameras, the pair's image width and first pixel.
 constexpr int kZQueue = 64;
 struct ZQueue {
     float xh[3][kZQueue], yh[3][kZQueue], wh[3][kZQueue];
     int x0[kZQueue], x1[kZQueue], y0[kZQueue], y1[kZQueue];
     uint32_t d2[kZQueue];
+    uint32_t w[kZQueue], off[kZQueue];
 };
 
-__device__ __forceinline__ void zq_put(ZQueue& q, int i, const TriSetup& s, uint32_t d2) {
+template <bool kCam>
+__device__ __forceinline__ void zq_put(ZQueue& q, int i, const TriSetup& s, uint32_t d2, const Cam& c) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         q.xh[j][i] = s.xh[j];
@@ -207,12 +210,19 @@ __device__ __forceinline__ void zq_put(ZQueue& q, int i, const TriSetup& s, uint
     q.y0[i] = s.y0;
     q.y1[i] = s.y1;
     q.d2[i] = d2;
+    if (kCam) {
+        q.w[i] = (uint32_t)c.W;
+        q.off[i] = (uint32_t)c.pix_off;
+    }
 }
 
 // Eq. (4) for the queued pair i: its covered pixels keep the minimum of the
 // squared distance (sqrt is monotone, so the square root of that minimum is
-// the minimum distance itself, taken where the depth is read).
-__device__ __forceinline__ void zq_draw(const Cam& c, const ZQueue& q, int i, uint32_t* D) {
+// the minimum distance itself, taken where the depth is read).  D is the
+// slot's depth array; W and off (the image width and first pixel) are the
+// block's camera's, or the queued ones when kCam.
+template <bool kCam>
+__device__ __forceinline__ void zq_draw(const ZQueue& q, int i, uint32_t* D, uint32_t W, uint32_t off) {
     TriSetup s;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -225,8 +235,13 @@ __device__ __forceinline__ void zq_draw(const Cam& c, const ZQueue& q, int i, ui
     s.y0 = q.y0[i];
     s.y1 = q.y1[i];
     const uint32_t d2 = q.d2[i];
-    raster_pixels(c, s, [&](size_t pix) {
-        uint32_t* p = D + pix;
+    if (kCam) {
+        W = q.w[i];
+        off = q.off[i];
+    }
+    uint32_t* img = kCam ? D + off : D;
+    raster_pixels(W, s, [&](size_t pix) {
+        uint32_t* p = img + pix;
         if (__ldcg(p) > d2) atomicMin(p, d2);   // skip the atomic when already nearer
     });
 }
@@ -271,17 +286,80 @@ __global__ void __launch_bounds__(256) k_zbuffer(const __grid_constant__ CamSet 
             ok = raster_setup(c, X, Y, Z, s);
         }
         const unsigned m = __ballot_sync(kFull, ok);
-        if (ok) zq_put(q, qn + __popc(m & ((1u << lane) - 1u)), s, d2);
+        if (ok) zq_put<false>(q, qn + __popc(m & ((1u << lane) - 1u)), s, d2, c);
         qn += __popc(m);                          // < 32 before, so < 64 now
         __syncwarp();
         if (qn >= 32 || (!more && qn > 0)) {      // draw the last (up to) 32 queued, one per lane
             const int k = min(qn, 32);
             qn -= k;
-            if (lane < k) zq_draw(c, q, qn + lane, D);
+            if (lane < k) zq_draw<false>(q, qn + lane, D, (uint32_t)c.W, 0u);
             __syncwarp();                         // read before the slots are reused
         }
         if (!more && qn == 0) break;
         if (more) t0 += gridDim.x * blockDim.x;
+    }
+}
+
+// k_zbuffer with a block serving K > 1 cameras (grid (blocks, camera groups,
+// slots), cameras blockIdx.y * K ...): a lane reads its triangle's record
+// once and sets it up for each camera of the group in turn, so each record
+// is read once per K cameras instead of once per camera.  The queue then
+// holds pairs of several cameras, each with its image width and first pixel.
+template <int K>
+__global__ void __launch_bounds__(256) k_zbuffer_cams(const __grid_constant__ CamSet cams,
+                                                      const __grid_constant__ Layout L,
+                                                      const __grid_constant__ SlotList sl) {
+    pdl_begin();
+    __shared__ ZQueue zq[8];   // one per warp (at most 256 threads)
+    const int slot = sl.s[blockIdx.z];
+    const int n0 = blockIdx.y * K;
+    const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const uint32_t nt = info->n_words ? info->n_tris : 0u;
+    const float4* tsoup = slot_ptr<float4>(L, slot, L.tsoup);
+    uint32_t* D = slot_ptr<uint32_t>(L, slot, L.depth);
+    const int lane = threadIdx.x & 31;
+    ZQueue& q = zq[threadIdx.x >> 5];
+    int qn = 0;   // queued pairs, the same in every lane
+    for (uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < nt; t0 += gridDim.x * blockDim.x) {
+        const uint32_t t = t0 + (uint32_t)lane;   // the loop condition is warp-uniform
+        const bool have = t < nt;
+        float4 r0, r1, r2;                        // read only where have
+        if (have) {
+            r0 = __ldg(tsoup + 3 * (size_t)t);
+            r1 = __ldg(tsoup + 3 * (size_t)t + 1);
+            r2 = __ldg(tsoup + 3 * (size_t)t + 2);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (n0 + k >= cams.n) break;          // uniform
+            const Cam& c = cams.c[n0 + k];
+            TriSetup s;
+            uint32_t d2 = 0;
+            bool ok = false;
+            if (have) {
+                const float X[3] = {r0.x, r0.w, r1.z}, Y[3] = {r0.y, r1.x, r1.w}, Z[3] = {r0.z, r1.y, r2.x};
+                const float dx = fsub(r2.y, c.C[0]);
+                const float dy = fsub(r2.z, c.C[1]);
+                const float dz = fsub(r2.w, c.C[2]);
+                d2 = __float_as_uint(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
+                ok = raster_setup(c, X, Y, Z, s);
+            }
+            const unsigned m = __ballot_sync(kFull, ok);
+            if (ok) zq_put<true>(q, qn + __popc(m & ((1u << lane) - 1u)), s, d2, c);
+            qn += __popc(m);                      // < 32 before, so < 64 now
+            __syncwarp();
+            if (qn >= 32) {                       // draw the last 32 queued, one per lane
+                qn -= 32;
+                zq_draw<true>(q, qn + lane, D, 0u, 0u);
+                __syncwarp();                     // read before the slots are reused
+            }
+        }
+    }
+    while (qn > 0) {                              // the rest, up to 32 at a time
+        const int k = min(qn, 32);
+        qn -= k;
+        if (lane < k) zq_draw<true>(q, qn + lane, D, 0u, 0u);
+        __syncwarp();
     }
 }
 
@@ -456,9 +534,15 @@ cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, con
     const int gc = std::max(1, sms * 4 / std::max(1, sl.n * cams.n));
     launch_pdl(k_clear_depth, dim3(gc, cams.n, sl.n), dim3(256), 0, st, cams, L, sl);
     launch_pdl(k_depth_box, dim3(sl.n), dim3(256), 0, st, cams, g, L, sl);
-    const int gz = tuned_grid(tu, FVV_TUNE_ZBUFFER, sms, sl.n, (long long)g.max_tris, cams.n);
-    launch_pdl(k_zbuffer, dim3(gz, cams.n, sl.n), dim3(tu.threads[FVV_TUNE_ZBUFFER]), 0, st, cams, L, sl);
-    return cudaGetLastError();
+    const int K = tu.zb_cams;
+    const int groups = (cams.n + K - 1) / K;
+    const int gz = tuned_grid(tu, FVV_TUNE_ZBUFFER, sms, sl.n, (long long)g.max_tris, groups);
+    const dim3 grid(gz, groups, sl.n), block(tu.threads[FVV_TUNE_ZBUFFER]);
+    cudaError_t e;
+    if (K == 4) e = launch_pdl(k_zbuffer_cams<4>, grid, block, 0, st, cams, L, sl);
+    else if (K == 2) e = launch_pdl(k_zbuffer_cams<2>, grid, block, 0, st, cams, L, sl);
+    else e = launch_pdl(k_zbuffer, grid, block, 0, st, cams, L, sl);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_colour(const CamSet& cams, const Grid& g, const Layout& L, const ColourBatch& cb, int sms,

@@ -38,14 +38,17 @@ STAGES = ("pack", "coarse", "ccl", "fine", "mc", "bisect", "depth", "colour")
 TUNE_KNOBS = ("coarse", "fine", "bisect", "zbuffer", "triangles")
 N_TUNE = len(TUNE_KNOBS)
 FINE_TILES = ((4, 4, 8), (4, 4, 4), (4, 8, 8))   # FVV_TILE_*: fine-hull tile (x, y, z) samples
-TUNE_INTS = 2 * N_TUNE + 1
+ZBUFFER_CAMS = (1, 2, 4)                          # cameras one z-buffer block serves
+TUNE_INTS = 2 * N_TUNE + 2
 
 
 def tuning_dict(cfg):
-    """{kernel: (threads per block, blocks per SM)} and the fine-hull tile
-    shape ("fine_tile": (x, y, z)) from the flat C layout."""
+    """{kernel: (threads per block, blocks per SM)}, the fine-hull tile
+    shape ("fine_tile": (x, y, z)) and the cameras per z-buffer block
+    ("zbuffer_cams") from the flat C layout."""
     d = {k: (cfg[i], cfg[N_TUNE + i]) for i, k in enumerate(TUNE_KNOBS)}
     d["fine_tile"] = FINE_TILES[cfg[2 * N_TUNE]]
+    d["zbuffer_cams"] = cfg[2 * N_TUNE + 1]
     return d
 
 
@@ -471,10 +474,12 @@ class Rig:
 
     def set_tuning(self, tuning):
         """tuning: as get_tuning returns it; "fine_tile" may be left out
-        (4 x 4 x 8) and may be given as an (x, y, z) shape or an FVV_TILE_* index."""
+        (4 x 4 x 8) and may be given as an (x, y, z) shape or an FVV_TILE_*
+        index; "zbuffer_cams" may be left out (1)."""
         tile = tuning.get("fine_tile", FINE_TILES[0])
         tile = FINE_TILES.index(tuple(tile)) if not isinstance(tile, int) else tile
         cfg = [tuning[k][0] for k in TUNE_KNOBS] + [tuning[k][1] for k in TUNE_KNOBS] + [tile]
+        cfg.append(int(tuning.get("zbuffer_cams", 1)))
         _check(_lib.fvv_set_tuning(self.ptr, (C.c_int * len(cfg))(*cfg)), self.ptr)
 
     def set_graphs(self, enable=True):

@@ -13,16 +13,19 @@ def unpack_rows(words: np.ndarray, shape_rows, width):
 
 
 def run_gpu(rig, frames, host=False, caps=None, slots=None, batch=True, rgb_in_place=False, masks_in_place=False,
-            upload_batch=False):
+            upload_batch=False, tuning=None):
     """Upload (all slots in one call when upload_batch), reconstruct (all
-    slots in one call when batch) and colour.  Returns one dict of numpy
-    outputs per frame."""
+    slots in one call when batch) and colour, with the launch shapes
+    `tuning` (as Rig.set_tuning takes them) if given.  Returns one dict of
+    numpy outputs per frame."""
     from paper_1903_11785_gb300 import fvv
     caps = dict(caps or {})
     n = len(frames)
     slots = list(slots) if slots is not None else list(range(n))
     r = fvv.Rig(rig, max_slots=max(slots) + 1, host_staging=int(host), **caps)
     try:
+        if tuning is not None:
+            r.set_tuning(tuning)
         ms = [fr.masks.pin_memory() if (host or masks_in_place) else fr.masks.cuda() for fr in frames]
         if upload_batch:
             r.upload_silhouettes_batch(slots, ms, in_place=masks_in_place)

@@ -397,6 +397,10 @@ def test_generic_and_large_camera_counts(n_cams):
                     (-2.0, -2.0, 0.0), (2.0, 2.0, 2.5), 0.05, 0.01, 7)
     fr = render(rig, scene_objects("tiny", 7), index=7, config_tag=f"ring{n_cams}")
     compare(rig, fr, run_gpu(rig, [fr])[0])
+    # z-buffer blocks serving 2 and 4 cameras (5 cameras: a last group of one)
+    from paper_1903_11785_gb300 import fvv
+    for zc in (2, 4):
+        compare(rig, fr, run_gpu(rig, [fr], tuning={k: (128, 8) for k in fvv.TUNE_KNOBS} | {"zbuffer_cams": zc})[0])
     rig.surface_rule = 1
     compare(rig, fr, run_gpu(rig, [fr])[0])
 

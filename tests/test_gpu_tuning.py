@@ -16,6 +16,7 @@ def _frames(n):
 
 
 def _run(r, frames, stream=None):
+    from paper_1903_11785_gb300 import fvv
     slots = list(range(len(frames)))
     for s, fr in zip(slots, frames):
         r.upload_silhouettes(s, fr.masks.cuda(), stream=stream)
@@ -25,7 +26,8 @@ def _run(r, frames, stream=None):
     out = []
     for s in slots:
         res = r.results(s)
-        out.append({k: res[k].cpu() for k in ("verts", "tris", "rgb", "cam")} | {"counts": res["counts"]})
+        out.append({k: res[k].cpu() for k in ("verts", "tris", "rgb", "cam")} | {"counts": res["counts"]}
+                   | {"depth": r.debug(s, fvv.FVV_DEBUG_DEPTH).cpu()})
     return out
 
 
@@ -38,7 +40,7 @@ def _results(c):
 def _same(a, b):
     for x, y in zip(a, b):
         assert _results(x["counts"]) == _results(y["counts"])
-        for k in ("verts", "tris", "rgb", "cam"):
+        for k in ("verts", "tris", "rgb", "cam", "depth"):
             assert torch.equal(x[k], y[k]), k
 
 
@@ -52,11 +54,12 @@ def test_autotune_and_shapes_keep_results():
     try:
         ref = _run(r, frames)
         chosen = r.autotune([0, 1, 2])
-        assert set(chosen) == set(fvv.TUNE_KNOBS) | {"fine_tile"}
+        assert set(chosen) == set(fvv.TUNE_KNOBS) | {"fine_tile", "zbuffer_cams"}
         assert chosen["fine_tile"] in fvv.FINE_TILES
+        assert chosen["zbuffer_cams"] in fvv.ZBUFFER_CAMS
         for k in fvv.TUNE_KNOBS:
             th, wv = chosen[k]
-            assert th in (64, 128, 256) and wv in (2, 4, 8, 16, 32)
+            assert th in (64, 128, 256) and wv in (2, 4, 8, 16, 32, 64)
         # the autotuner leaves the slots freshly reconstructed
         after = [{k: r.results(s)[k].cpu() for k in ("verts", "tris")} | {"counts": r.counts(s)} for s in range(3)]
         for x, y in zip(after, ref):
@@ -70,8 +73,14 @@ def test_autotune_and_shapes_keep_results():
             r.set_tuning({k: (128, 8) for k in fvv.TUNE_KNOBS} | {"fine_tile": tile})
             assert r.get_tuning()["fine_tile"] == tile
             _same(_run(r, frames), ref)
+        for zc in fvv.ZBUFFER_CAMS:            # cameras per z-buffer block: the same depth images
+            r.set_tuning({k: (96, 4) for k in fvv.TUNE_KNOBS} | {"zbuffer_cams": zc})
+            assert r.get_tuning()["zbuffer_cams"] == zc
+            _same(_run(r, frames), ref)
         with pytest.raises(fvv.FvvError):
             r.set_tuning({k: (128, 8) for k in fvv.TUNE_KNOBS} | {"fine_tile": 3})
+        with pytest.raises(fvv.FvvError):
+            r.set_tuning({k: (128, 8) for k in fvv.TUNE_KNOBS} | {"zbuffer_cams": 3})
         with pytest.raises(fvv.FvvError):
             r.set_tuning({k: (48, 8) for k in fvv.TUNE_KNOBS})
     finally:
