@@ -103,35 +103,45 @@ __global__ void k_depth_box(const __grid_constant__ CamSet cams, const __grid_co
 // approximate projections; their error is below 1e-3 px for images up to
 // 65535 px, and the exact box test in raster_pixels decides).  False if a
 // vertex is not in front of the camera or no pixel centre is a candidate.
+//
+// The candidate columns are ceil(umin - 1/2 - 1/64) .. floor((umax + 1/64)
+// - 1/2), clamped to the image (rows alike).  They are rounded on the FMA
+// pipe: for |t| < 2^22, t + 1.5 * 2^23 rounded down (up) is 1.5 * 2^23 +
+// floor(t) (ceil(t)) exactly, since floats in [2^23, 2^24) are the
+// integers; the box ends are kept in that form (kMagic + integer), so that
+// comparing them compares the integers, and the integer is the float's bits
+// minus those of kMagic.  A clamped end is always in that range; an end
+// outside it only arises for an empty box, which the comparison then shows.
+constexpr float kMagic = 12582912.0f;        // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
 struct TriSetup {
     float xh[3], yh[3], wh[3];
-    int x0, x1, y0, y1;
+    float x0, x1, y0, y1;                    // kMagic + first/last candidate column and row
 };
+
+__device__ __forceinline__ int magic_int(float m) { return __float_as_int(m) - kMagicBits; }
 
 __device__ __forceinline__ bool raster_setup(const Cam& c, const float* X, const float* Y, const float* Z,
                                              TriSetup& s) {
     bool ok = true;
+    float u[3], v[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         project(c.P, X[j], Y[j], Z[j], s.xh[j], s.yh[j], s.wh[j]);
         ok &= s.wh[j] > 0.0f;
-    }
-    if (!ok) return false;
-    float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
         const float r = rcp_approx(s.wh[j]);
-        const float u = fmul(s.xh[j], r), v = fmul(s.yh[j], r);
-        umin = fminf(umin, u); umax = fmaxf(umax, u);
-        vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
+        u[j] = fmul(s.xh[j], r);
+        v[j] = fmul(s.yh[j], r);
     }
+    const float umin = fminf(u[0], fminf(u[1], u[2])), umax = fmaxf(u[0], fmaxf(u[1], u[2]));
+    const float vmin = fminf(v[0], fminf(v[1], v[2])), vmax = fmaxf(v[0], fmaxf(v[1], v[2]));
     constexpr float kSlack = 0.5f + 1.0f / 64.0f;
-    if (!(umax >= 0.0f && vmax >= 0.0f && umin <= c.Wf && vmin <= c.Hf)) return false;
-    s.x0 = max(0, (int)ceilf(fsub(umin, kSlack)));
-    s.y0 = max(0, (int)ceilf(fsub(vmin, kSlack)));
-    s.x1 = umax > c.Wf ? c.W - 1 : min(c.W - 1, (int)floorf(fsub(fadd(umax, 1.0f / 64.0f), 0.5f)));
-    s.y1 = vmax > c.Hf ? c.H - 1 : min(c.H - 1, (int)floorf(fsub(fadd(vmax, 1.0f / 64.0f), 0.5f)));
-    return s.x0 <= s.x1 && s.y0 <= s.y1;
+    s.x0 = __fadd_ru(fmaxf(fsub(umin, kSlack), 0.0f), kMagic);
+    s.y0 = __fadd_ru(fmaxf(fsub(vmin, kSlack), 0.0f), kMagic);
+    s.x1 = __fadd_rd(fminf(fsub(fadd(umax, 1.0f / 64.0f), 0.5f), fsub(c.Wf, 1.0f)), kMagic);
+    s.y1 = __fadd_rd(fminf(fsub(fadd(vmax, 1.0f / 64.0f), 0.5f), fsub(c.Hf, 1.0f)), kMagic);
+    // (umax >= 0 and vmax >= 0 also turn away all-NaN image positions)
+    return ok && umax >= 0.0f && vmax >= 0.0f && s.x0 <= s.x1 && s.y0 <= s.y1;
 }
 
 // The second part: the triangle is skipped if its projected area is zero;
@@ -159,12 +169,13 @@ __device__ __forceinline__ void raster_pixels(unsigned W, const TriSetup& s, Sin
     }
     const float det = fadd(fsub(fmul(xh[0], ea[1]), fmul(yh[0], eb[1])), fmul(wh[0], ec[1]));
     if (!(det > 0.0f || det < 0.0f)) return;
-    for (int yy = s.y0; yy <= s.y1; ++yy) {
+    const int x0 = magic_int(s.x0), x1 = magic_int(s.x1), y1 = magic_int(s.y1);
+    for (int yy = magic_int(s.y0); yy <= y1; ++yy) {
         const float pcy = fadd((float)yy, 0.5f);
         const float s0 = __fmaf_rn(pcy, wh[0], -yh[0]), s1 = __fmaf_rn(pcy, wh[1], -yh[1]),
                     s2 = __fmaf_rn(pcy, wh[2], -yh[2]);
         if (!((s0 >= 0.0f || s1 >= 0.0f || s2 >= 0.0f) && (s0 <= 0.0f || s1 <= 0.0f || s2 <= 0.0f))) continue;
-        for (int xx = s.x0; xx <= s.x1; ++xx) {
+        for (int xx = x0; xx <= x1; ++xx) {
             const float pcx = fadd((float)xx, 0.5f);
             const float r0 = __fmaf_rn(pcx, wh[0], -xh[0]), r1 = __fmaf_rn(pcx, wh[1], -xh[1]),
                         r2 = __fmaf_rn(pcx, wh[2], -xh[2]);
@@ -192,7 +203,7 @@ __device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const f
 constexpr int kZQueue = 64;
 struct ZQueue {
     float xh[3][kZQueue], yh[3][kZQueue], wh[3][kZQueue];
-    int x0[kZQueue], x1[kZQueue], y0[kZQueue], y1[kZQueue];
+    float x0[kZQueue], x1[kZQueue], y0[kZQueue], y1[kZQueue];
     uint32_t d2[kZQueue];
     uint32_t w[kZQueue], off[kZQueue];
 };
