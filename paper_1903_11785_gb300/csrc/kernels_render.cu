@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(256) k_zbuffer(const __grid_constant__ CamSet 
 // is read once per K cameras instead of once per camera.  The queue then
 // holds pairs of several cameras, each with its image width and first pixel.
 template <int K>
-__global__ void __launch_bounds__(256) k_zbuffer_cams(const __grid_constant__ CamSet cams,
+__global__ void __launch_bounds__(256, 4) k_zbuffer_cams(const __grid_constant__ CamSet cams,
                                                       const __grid_constant__ Layout L,
                                                       const __grid_constant__ SlotList sl) {
     pdl_begin();
