@@ -58,8 +58,9 @@ FP32_LANES_PER_SM = 128
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of a 4-frame launch of
 # the current kernels, scaled to a launch by its frame count.  None for a
 # kernel changed since that capture.
-DRAM_BYTES_PER_FRAME = {"fine": 7.29472e6 / 4, "bisect": (17.210368e6 + 9216) / 4,
-                        "coarse": (4.332032e6 + 5120) / 4, "depth": (178.810368e6 + 10.8864e6) / 4}
+DRAM_BYTES_PER_FRAME = {"k_fine_carve": 7.29472e6 / 4, "k_bisect": (17.210368e6 + 9216) / 4,
+                        "k_coarse_carve": (4.332032e6 + 5120) / 4, "k_zbuffer": None,
+                        "k_zbuffer_cams<2>": None, "k_zbuffer_cams<4>": None}
 
 
 def parse_args():
@@ -78,6 +79,8 @@ def parse_args():
                     help="serving: pinned masks read in place by the packing kernel, or copied by the copy engines")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--zbuffer-cams", type=int, choices=(1, 2, 4), default=None,
+                    help="cameras per z-buffer block, set after any tuning (for profiling one variant)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--study", choices=("surface", "fig10", "table1", "view"), default=None,
                     help="instead of the benchmark line: surface-rule errors (Sec. II-C), the coarse/fine "
@@ -454,6 +457,11 @@ def run_ours(args):
         tuning = r.autotune(slots)          # launch shapes picked on this batch
         step()
         torch.cuda.synchronize()
+    if args.zbuffer_cams is not None:
+        tuning = dict(r.get_tuning(), zbuffer_cams=args.zbuffer_cams)
+        r.set_tuning(tuning)
+        step()
+        torch.cuda.synchronize()
     counts = [r.counts(i) for i in slots]
     tests = sum(c["tests_coarse"] + c["tests_fine"] + c["tests_bisect"] for c in counts)
     tsum = {k: sum(c[k] for c in counts) for k in ("tests_coarse", "tests_fine", "tests_bisect", "n_verts",
@@ -531,7 +539,9 @@ def run_ours(args):
                    FLOPS_PER_TEST, "camera tests (+ midpoints as test equivalents)"),
         "depth": (tsum["n_tris"] * rig.n_cams, FLOPS_PER_PAIR, "(triangle, camera) pairs"),
     }
-    kernel_of = {"coarse": "k_coarse_carve", "fine": "k_fine_carve", "bisect": "k_bisect", "depth": "k_zbuffer"}
+    zc = r.get_tuning()["zbuffer_cams"]
+    kernel_of = {"coarse": "k_coarse_carve", "fine": "k_fine_carve", "bisect": "k_bisect",
+                 "depth": "k_zbuffer" if zc == 1 else f"k_zbuffer_cams<{zc}>"}
 
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     alu = measure_alu(fvv, torch, sms)
@@ -543,7 +553,7 @@ def run_ours(args):
         n_units, fpu, what = units[k]
         launch_ms = per_step[k] / max(launches[k], 1)
         achieved = n_units * fpu / max(launches[k], 1) / (launch_ms / 1000.0) / 1e12
-        traffic = DRAM_BYTES_PER_FRAME.get(k)
+        traffic = DRAM_BYTES_PER_FRAME.get(kernel_of[k])
         return {"bound": "alu", "kernel": kernel_of[k], "achieved": achieved, "peak": alu["tflops"],
                 "unit": "TFLOP/s", "frac": achieved / alu["tflops"],
                 "traffic": traffic * F if traffic is not None else None,
@@ -692,11 +702,11 @@ def run_ours(args):
         cpu["single_core_per_config"] = per_cfg
         flips = fp64_flips(rig, cpu_sample[0][0])
 
-    # kernels per step: one packing launch per 128 frames; the reconstruction's 17
+    # kernels per step: one packing launch per 128 frames; the reconstruction's 15
     # (info reset; coarse hull; 5 for CCL, boxes and filter; fine-grid clear
-    # and fine hull; 3 for MC counts, scan and records; bisection; triangles;
-    # depth clear, box and z-buffer); one colour launch per 48 frames
-    n_launch = args.steps * ((F + 127) // 128 + 17 + (F + 47) // 48)
+    # and fine hull; MC compaction; bisection; triangles; depth clear, box and
+    # z-buffer); one colour launch per 48 frames
+    n_launch = args.steps * ((F + 127) // 128 + 15 + (F + 47) // 48)
     p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -115,7 +115,8 @@ enum {
                                       side longer than 32765 fine voxels          */
     FVV_FLAG_VERTS = 1u << 3,      /* vertices > max_verts                         */
     FVV_FLAG_TRIS = 1u << 4,       /* triangles > max_tris                         */
-    FVV_FLAG_LOOP = 1u << 5        /* an iteration bound of union-find was hit    */
+    FVV_FLAG_LOOP = 1u << 5        /* an iteration bound of union-find, or of a
+                                      * bounded wait in the compaction, was hit     */
 };
 
 /* The cameras (Sec. II-A: calibrated in advance, static).  All arrays are

@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(256) k_coarse_carve(const __grid_constant__ Ca
     }
 }
 
-// Clears the fine grids and resets the fine carve's tile counter.
+// Clears the fine grids and the compaction's chunk states, and resets the
+// fine carve's tile counter.
 __global__ void __launch_bounds__(256) k_clear_fine(const __grid_constant__ Layout L,
                                                     const __grid_constant__ SlotList sl) {
     pdl_begin();
@@ -117,6 +118,10 @@ __global__ void __launch_bounds__(256) k_clear_fine(const __grid_constant__ Layo
     const uint32_t nwords = info->n_words;
     uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) fine[w] = 0u;
+    // the compaction's look-back states of this reconstruction's chunks
+    unsigned long long* cst = slot_ptr<unsigned long long>(L, slot, L.chunk_st);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 2u * info->n_chunks; i += gridDim.x * blockDim.x)
+        cst[i] = 0ull;
     if (blockIdx.x == 0 && threadIdx.x == 0) info->next_tile = 0u;
 }
 

@@ -3,12 +3,13 @@
 // Each fine grid is padded by one unoccupied sample per side and stored as
 // rows of 32-bit words, so one thread owns 32 cells (or 32 samples) and works
 // with word-wide bit operations:
-//   count     bipolar-edge masks (x: w ^ w>>1, y: w ^ w(y+1), z: w ^ w(z+1)),
+//   compact   bipolar-edge masks (x: w ^ w>>1, y: w ^ w(y+1), z: w ^ w(z+1)),
 //             vertices = popcounts, triangles = table counts of mixed cells;
-//             per-256-word chunk sums.
-//   scan      one block per frame: exclusive prefix of the chunk sums.
-//   vertices  exclusive prefix per word (block scan + chunk base) and one
-//             record per bipolar edge, in edge-key order (3*Lpad + axis).
+//             exclusive prefix per word (block scan + a look-back over the
+//             earlier 256-word chunks) and one record per bipolar edge, in
+//             edge-key order (3*Lpad + axis), and one per triangle; the
+//             grid slab a chunk reads is staged in shared memory by a bulk
+//             copy.
 //   bisect    one thread per vertex: fixed-count bisection of its edge
 //             against the silhouettes (the exact intersection of Eqs. (2)-(3)
 //             read as the hull crossing on the edge).
@@ -173,88 +174,104 @@ __device__ __forceinline__ int cell_case(const Nbhd& n, int b) {
     return c;
 }
 
-__global__ void __launch_bounds__(kChunk) k_mc_count(const __grid_constant__ Layout L, const __grid_constant__ SlotList sl,
-                                                     const __grid_constant__ McTable mc) {
-    pdl_begin();
-    __shared__ uint8_t s_ntri[256];
-    __shared__ uint32_t sh[32];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) s_ntri[i] = mc.ntri[i];
-    __syncthreads();
-    const int slot = sl.s[blockIdx.y];
-    const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
-    const uint32_t nwords = info->n_words, nchunks = info->n_chunks;
-    const int nrois = info->n_rois;
-    const DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
-    const uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
-    uint32_t* vcnt = slot_ptr<uint32_t>(L, slot, L.vcnt);
-    uint32_t* tcnt = slot_ptr<uint32_t>(L, slot, L.tcnt);
-    uint32_t* emask = slot_ptr<uint32_t>(L, slot, L.emask);
-    uint32_t* cpart = slot_ptr<uint32_t>(L, slot, L.cpart);
-    RoiCursor cur;
-    for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const uint32_t w = c * kChunk + threadIdx.x;
-        uint32_t vc = 0, tc = 0;
-        if (w < nwords) {
-            cur.seek(rois, nrois, w);
-            Nbhd n;
-            load_nbhd(fine, cur, w, n);
-            const uint32_t xm = n.w[0] ^ n.s[0], ym = n.w[0] ^ n.w[1], zm = n.w[0] ^ n.w[2];
-            vc = __popc(xm) + __popc(ym) + __popc(zm);
-            uint32_t mx = mixed_cells(n);
-            while (mx) {
-                const int b = __ffs(mx) - 1;
-                mx &= mx - 1;
-                tc += s_ntri[cell_case(n, b)];
-            }
-            vcnt[w] = vc;
-            tcnt[w] = tc;
-            emask[3 * (size_t)w + 0] = xm;
-            emask[3 * (size_t)w + 1] = ym;
-            emask[3 * (size_t)w + 2] = zm;
-        }
-        const uint32_t sv = block_sum<uint32_t>(vc, sh);
-        const uint32_t st = block_sum<uint32_t>(tc, sh);
-        if (threadIdx.x == 0) {
-            cpart[2 * (size_t)c] = sv;
-            cpart[2 * (size_t)c + 1] = st;
-        }
+// The 8 words of load_nbhd, read from a slab of the slot's fine words
+// staged in shared memory (slab[i] = fine word lo + i).
+__device__ __forceinline__ void load_nbhd_slab(const uint32_t* slab, uint32_t lo, const RoiCursor& r, uint32_t w,
+                                               Nbhd& n) {
+    const uint32_t rs = (uint32_t)r.nxw, ps = (uint32_t)r.nxw * (uint32_t)(r.fdim[1] + 2);
+    const bool hx = r.wx + 1 < r.nxw, hy = r.yp + 1 < r.fdim[1] + 2, hz = r.zp + 1 < r.fdim[2] + 2;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool dy = k & 1, dz = k >> 1;
+        const bool ok = (!dy || hy) && (!dz || hz);
+        const uint32_t i = w - lo + (dy ? rs : 0u) + (dz ? ps : 0u);
+        const uint32_t a = ok ? slab[i] : 0u;
+        const uint32_t b = (ok && hx) ? slab[i + 1] : 0u;
+        n.w[k] = a;
+        n.s[k] = (a >> 1) | (b << 31);
     }
 }
 
-// One block per slot: chunk sums -> exclusive chunk bases, totals, capacity.
-__global__ void __launch_bounds__(1024) k_mc_scan(const __grid_constant__ Grid g, const __grid_constant__ Layout L,
-                                                  const __grid_constant__ SlotList sl) {
-    pdl_begin();
-    __shared__ uint32_t sh[33];
-    const int slot = sl.s[blockIdx.x];
-    SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
-    const uint32_t nchunks = info->n_chunks;
-    uint32_t* cpart = slot_ptr<uint32_t>(L, slot, L.cpart);
-    unsigned long long bv = 0, bt = 0;
-    for (uint32_t t0 = 0; t0 < nchunks; t0 += blockDim.x) {
-        const uint32_t i = t0 + threadIdx.x;
-        const uint32_t v = i < nchunks ? cpart[2 * (size_t)i] : 0u;
-        const uint32_t t = i < nchunks ? cpart[2 * (size_t)i + 1] : 0u;
-        uint32_t tv, tt;
-        const uint32_t ev = block_exclusive_scan(v, sh, tv);
-        const uint32_t et = block_exclusive_scan(t, sh, tt);
-        if (i < nchunks) {
-            cpart[2 * (size_t)i] = (uint32_t)(bv + ev);
-            cpart[2 * (size_t)i + 1] = (uint32_t)(bt + et);
-        }
-        bv += tv;
-        bt += tt;
-    }
-    if (threadIdx.x == 0) {
-        unsigned fl = 0;
-        if (bv > g.max_verts) fl |= FVV_FLAG_VERTS;
-        if (bt > g.max_tris) fl |= FVV_FLAG_TRIS;
-        info->flags |= fl;
-        info->n_verts = fl ? 0u : (uint32_t)bv;
-        info->n_tris = fl ? 0u : (uint32_t)bt;
-        if (fl) info->n_words = 0;   // nothing downstream runs on this frame
-    }
+// ---- staging through the tensor memory accelerator (1-D bulk copies into
+// shared memory, completion counted on an mbarrier)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+
+// One arrival that also expects `bytes` of copies to complete on the barrier.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0u;
+}
+
+// Copy `bytes` (a multiple of 16; both addresses 16-byte aligned) from
+// global to shared memory; completes on `bar`.  Shared memory that generic
+// loads read before must be ordered before the copy (fence_proxy_async).
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Decoupled look-back state of a chunk, one word per count (vertices,
+// triangles): bits 62-63 say what bits 0-61 hold -- 0 nothing yet, 1 the
+// chunk's own count, 2 the count of chunks 0..c together.
+constexpr unsigned long long kStAgg = 1ull << 62, kStInc = 2ull << 62, kStVal = (1ull << 62) - 1ull;
+
+__device__ __forceinline__ void st_state(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_state(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Polls of a bounded wait (the slab copy, or the states of earlier chunks)
+// before the kernel gives up on it and sets FVV_FLAG_LOOP.
+constexpr int kMaxPolls = 1 << 22;
+
+// Count j (0 vertices, 1 triangles) of the chunks before chunk c: the
+// states of c-1, c-2, ... are added until one holds an inclusive count.
+// False if the polls ran out (sum then incomplete).
+__device__ __forceinline__ bool look_back(const unsigned long long* st, uint32_t c, int j, unsigned long long& sum,
+                                          int& polls) {
+    sum = 0;
+    for (uint32_t q = c; q-- > 0;) {
+        unsigned long long s = ld_state(st + 2 * (size_t)q + j);
+        while ((s >> 62) == 0ull) {
+            if (++polls > kMaxPolls) return false;
+            s = ld_state(st + 2 * (size_t)q + j);
+        }
+        sum += s & kStVal;
+        if ((s >> 62) == 2ull) return true;
+    }
+    return true;   // (chunk 0 is always inclusive)
+}
+
+// Words of a staged slab: a chunk's 256 words and the neighbours its cells
+// reach (a word in +x, a row in +y, a plane in +z).  Chunks whose ROIs reach
+// further read the grid from global memory instead.
+constexpr uint32_t kSlabWords = 6144;
 
 // Vertex record: ROI (14 bits) | axis (2) | ON at lower sample (1) | xp, yp, zp (15 bits each).
 __device__ __forceinline__ uint64_t pack_vrec(int k, int axis, int s0on, int xp, int yp, int zp) {
@@ -268,69 +285,179 @@ __device__ __forceinline__ uint64_t pack_trec(uint32_t w, int b, int j, int cs, 
     return (uint64_t)w | (uint64_t)b << 26 | (uint64_t)j << 31 | (uint64_t)cs << 35 | (uint64_t)k << 43;
 }
 
-// After the scans: per fine word its vertex and triangle offsets, a record
-// per vertex (the bipolar edges in canonical order) and a record per
-// triangle (the word's surface cells in order, each cell's triangles in
-// table order), so that the bisection and the triangle kernel take one
-// vertex or triangle per thread.
-__global__ void __launch_bounds__(kChunk) k_mc_vertices(const __grid_constant__ Layout L,
-                                                        const __grid_constant__ SlotList sl,
-                                                        const __grid_constant__ McTable mc) {
+// Sec. II-C classify and compact, in one pass over each slot's fine words:
+// 256-word chunks are claimed in order from a per-slot counter; a chunk's
+// words and the neighbours its cells reach (a slab) are copied into shared
+// memory by one bulk copy; each thread takes one word: its bipolar-edge
+// masks (x: w ^ w>>1, y: w ^ w(y+1), z: w ^ w(z+1)), vertex count (their
+// popcounts) and triangle count (table counts of its mixed cells).  Block
+// scans give the offsets within the chunk, and a decoupled look-back over
+// the earlier chunks' published counts gives the chunk's base, so vertex
+// ids follow the edge-key order (3*Lpad + axis) and triangles (ROI, cell,
+// table order) of a serial scan.  Each word then writes its prefix, masks,
+// one record per vertex and one per triangle; the last chunk sets the
+// totals and the capacity flags.  A chunk waits only on chunks claimed
+// before it, whose blocks are running, so the look-back always ends.
+__global__ void __launch_bounds__(kChunk) k_mc_compact(const __grid_constant__ Grid g,
+                                                       const __grid_constant__ Layout L,
+                                                       const __grid_constant__ SlotList sl,
+                                                       const __grid_constant__ McTable mc) {
     pdl_begin();
-    __shared__ uint32_t sh[33];
+    extern __shared__ __align__(128) uint32_t slab[];   // kSlabWords
     __shared__ uint8_t s_ntri[256];
+    __shared__ uint32_t sh[33];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_c, s_use;
+    __shared__ unsigned long long s_base[2];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) s_ntri[i] = mc.ntri[i];
+    if (threadIdx.x == 0) mbar_init(&bar);
     __syncthreads();
     const int slot = sl.s[blockIdx.y];
-    const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
-    const uint32_t nwords = info->n_words, nchunks = (nwords + kChunk - 1) / kChunk;
+    SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
+    const uint32_t nwords = info->n_words, nchunks = info->n_chunks;
     const int nrois = info->n_rois;
     DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
     const uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
-    const uint32_t* vcnt = slot_ptr<uint32_t>(L, slot, L.vcnt);
-    const uint32_t* tcnt = slot_ptr<uint32_t>(L, slot, L.tcnt);
-    const uint32_t* emask = slot_ptr<uint32_t>(L, slot, L.emask);
-    const uint32_t* cpart = slot_ptr<uint32_t>(L, slot, L.cpart);
+    uint32_t* emask = slot_ptr<uint32_t>(L, slot, L.emask);
     uint32_t* vpre = slot_ptr<uint32_t>(L, slot, L.vpre);
-    uint32_t* tpre = slot_ptr<uint32_t>(L, slot, L.tpre);
     uint64_t* vrec = slot_ptr<uint64_t>(L, slot, L.vrec);
     uint64_t* trec = slot_ptr<uint64_t>(L, slot, L.trec);
+    unsigned long long* cst = slot_ptr<unsigned long long>(L, slot, L.chunk_st);
+    uint32_t parity = 0;
+    bool pending = false;   // a copy whose wait ran out may still be in flight (thread 0's view)
     RoiCursor p;
-    for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const uint32_t w = c * kChunk + threadIdx.x;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t c = nchunks ? atomicAdd(&info->next_chunk, 1u) : 0u;
+            s_c = c;
+            s_use = 0;
+            if (c < nchunks && !pending) {
+                // the slab: words lo .. hi-1, hi past the farthest neighbour of the chunk's words
+                const uint32_t lo = c * kChunk, last = min(lo + (uint32_t)kChunk, nwords) - 1u;
+                const int k0 = roi_of_word(rois, nrois, lo), k1 = roi_of_word(rois, nrois, last);
+                uint32_t reach = 0;
+                for (int k = k0; k <= k1; ++k) {
+                    const uint32_t rs = (uint32_t)rois[k].nxw;
+                    reach = max(reach, 1u + rs + rs * (uint32_t)(rois[k].fdim[1] + 2));
+                }
+                const uint32_t hi = min(nwords, last + 1u + reach);
+                const uint32_t n4 = (hi - lo + 3u) & ~3u;   // whole 16-byte units (inside the array's padding)
+                if (n4 <= kSlabWords) {
+                    s_use = 1;
+                    fence_proxy_async();
+                    mbar_expect_tx(&bar, n4 * 4u);
+                    bulk_copy_g2s(slab, fine + lo, n4 * 4u, &bar);
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t c = s_c;
+        if (c >= nchunks) break;
+        bool use = s_use != 0u;
+        if (use) {
+            bool done = false;
+            for (int it = 0; it < kMaxPolls && !done; ++it) done = mbar_try_wait(&bar, parity);
+            if (__syncthreads_or(!done)) {
+                // the copy did not complete in time: this chunk and the later
+                // ones read global memory, and the slot is flagged
+                use = false;
+                if (threadIdx.x == 0) {
+                    pending = true;
+                    atomicOr(&info->flags, (unsigned)FVV_FLAG_LOOP);
+                }
+            } else {
+                parity ^= 1u;
+            }
+        }
+        const uint32_t lo = c * kChunk, w = lo + threadIdx.x;
         const bool in = w < nwords;
-        uint32_t tv, tt;
-        const uint32_t ev = block_exclusive_scan(in ? vcnt[w] : 0u, sh, tv) + cpart[2 * (size_t)c];
-        const uint32_t et = block_exclusive_scan(in ? tcnt[w] : 0u, sh, tt) + cpart[2 * (size_t)c + 1];
-        if (!in) continue;
-        vpre[w] = ev;
-        tpre[w] = et;
-        p.seek(rois, nrois, w);
-        if (w == p.lo) {
-            rois[p.k].vert_off = ev;
-            rois[p.k].tri_off = et;
-        }
-        const uint32_t xm = emask[3 * (size_t)w], ym = emask[3 * (size_t)w + 1], zm = emask[3 * (size_t)w + 2];
-        const uint32_t own = __ldg(fine + w);
-        uint32_t any = xm | ym | zm, id = ev;
-        while (any) {
-            const int b = __ffs(any) - 1;
-            any &= any - 1;
-            const int s0 = (own >> b) & 1u, xp = p.wx * 32 + b;
-            if ((xm >> b) & 1u) vrec[id++] = pack_vrec(p.k, 0, s0, xp, p.yp, p.zp);
-            if ((ym >> b) & 1u) vrec[id++] = pack_vrec(p.k, 1, s0, xp, p.yp, p.zp);
-            if ((zm >> b) & 1u) vrec[id++] = pack_vrec(p.k, 2, s0, xp, p.yp, p.zp);
-        }
-        if (tcnt[w]) {
-            Nbhd n;
-            load_nbhd(fine, p, w, n);
-            uint32_t mx = mixed_cells(n), t = et;
+        Nbhd n;
+        uint32_t xm = 0, ym = 0, zm = 0, vc = 0, tc = 0;
+        if (in) {
+            p.seek(rois, nrois, w);
+            if (use) load_nbhd_slab(slab, lo, p, w, n);
+            else load_nbhd(fine, p, w, n);
+            xm = n.w[0] ^ n.s[0];
+            ym = n.w[0] ^ n.w[1];
+            zm = n.w[0] ^ n.w[2];
+            vc = __popc(xm) + __popc(ym) + __popc(zm);
+            uint32_t mx = mixed_cells(n);
             while (mx) {
                 const int b = __ffs(mx) - 1;
                 mx &= mx - 1;
-                const int cs = cell_case(n, b);
-                for (int j = 0; j < (int)s_ntri[cs]; ++j) trec[t++] = pack_trec(w, b, j, cs, p.k);
+                tc += s_ntri[cell_case(n, b)];
             }
+        }
+        uint32_t tv, tt;
+        const uint32_t ev = block_exclusive_scan(vc, sh, tv);
+        const uint32_t et = block_exclusive_scan(tc, sh, tt);
+        if (threadIdx.x == 0) {
+            unsigned long long bv = 0, bt = 0;
+            int polls = 0;
+            bool ok = true;
+            if (c > 0) {
+                st_state(cst + 2 * (size_t)c, kStAgg | tv);
+                st_state(cst + 2 * (size_t)c + 1, kStAgg | tt);
+                ok = look_back(cst, c, 0, bv, polls) && look_back(cst, c, 1, bt, polls);
+            }
+            st_state(cst + 2 * (size_t)c, kStInc | ((bv + tv) & kStVal));
+            st_state(cst + 2 * (size_t)c + 1, kStInc | ((bt + tt) & kStVal));
+            if (!ok) atomicOr(&info->flags, (unsigned)FVV_FLAG_LOOP);
+            s_base[0] = bv;
+            s_base[1] = bt;
+            if (c == nchunks - 1u) {
+                // totals and capacities (the records past a capacity were not written)
+                const unsigned long long nv = bv + tv, nt = bt + tt;
+                unsigned fl = 0;
+                if (nv > g.max_verts) fl |= FVV_FLAG_VERTS;
+                if (nt > g.max_tris) fl |= FVV_FLAG_TRIS;
+                if (fl) atomicOr(&info->flags, fl);
+                info->n_verts = fl ? 0u : (uint32_t)nv;
+                info->n_tris = fl ? 0u : (uint32_t)nt;
+                if (fl) info->n_words = 0;   // nothing downstream runs on this frame
+            }
+        }
+        __syncthreads();
+        if (in) {
+            const unsigned long long vb = s_base[0] + ev, tb = s_base[1] + et;
+            vpre[w] = (uint32_t)vb;
+            if (w == p.lo) {
+                rois[p.k].vert_off = (uint32_t)vb;
+                rois[p.k].tri_off = (uint32_t)tb;
+            }
+            emask[3 * (size_t)w + 0] = xm;
+            emask[3 * (size_t)w + 1] = ym;
+            emask[3 * (size_t)w + 2] = zm;
+            const uint32_t own = n.w[0];
+            uint32_t any = xm | ym | zm;
+            unsigned long long id = vb;
+            while (any) {
+                const int b = __ffs(any) - 1;
+                any &= any - 1;
+                const int s0 = (own >> b) & 1u, xp = p.wx * 32 + b;
+                if (((xm >> b) & 1u) && id < g.max_verts) vrec[id] = pack_vrec(p.k, 0, s0, xp, p.yp, p.zp);
+                id += (xm >> b) & 1u;
+                if (((ym >> b) & 1u) && id < g.max_verts) vrec[id] = pack_vrec(p.k, 1, s0, xp, p.yp, p.zp);
+                id += (ym >> b) & 1u;
+                if (((zm >> b) & 1u) && id < g.max_verts) vrec[id] = pack_vrec(p.k, 2, s0, xp, p.yp, p.zp);
+                id += (zm >> b) & 1u;
+            }
+            if (tc) {
+                uint32_t mx = mixed_cells(n);
+                unsigned long long t = tb;
+                while (mx) {
+                    const int b = __ffs(mx) - 1;
+                    mx &= mx - 1;
+                    const int cs = cell_case(n, b);
+                    for (int j = 0; j < (int)s_ntri[cs]; ++j, ++t)
+                        if (t < g.max_tris) trec[t] = pack_trec(w, b, j, cs, p.k);
+                }
+            }
+        }
+    }
+    if (threadIdx.x == 0 && pending) {
+        // a copy whose wait ran out: wait (bounded) before the block's shared memory goes
+        for (int it = 0; it < kMaxPolls && !mbar_try_wait(&bar, parity); ++it) {
         }
     }
 }
@@ -644,10 +771,9 @@ __global__ void __launch_bounds__(256) k_mc_triangles(const __grid_constant__ La
 cudaError_t launch_mc_prefix(const Grid& g, const Layout& L, const SlotList& sl, const McTable& mc, int sms,
                              cudaStream_t st) {
     const int gc = grid_x(sms, sl.n, g.max_chunks, 1);
-    launch_pdl(k_mc_count, dim3(gc, sl.n), dim3(kChunk), 0, st, L, sl, mc);
-    launch_pdl(k_mc_scan, dim3(sl.n), dim3(1024), 0, st, g, L, sl);
-    launch_pdl(k_mc_vertices, dim3(gc, sl.n), dim3(kChunk), 0, st, L, sl, mc);
-    return cudaGetLastError();
+    const cudaError_t e = launch_pdl(k_mc_compact, dim3(gc, sl.n), dim3(kChunk), kSlabWords * sizeof(uint32_t), st, g,
+                                     L, sl, mc);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_bisect(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,

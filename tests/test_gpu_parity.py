@@ -405,6 +405,28 @@ def test_generic_and_large_camera_counts(n_cams):
     compare(rig, fr, run_gpu(rig, [fr])[0])
 
 
+def test_wide_roi_compaction_reads_global_memory():
+    """A flat 4.6 m disc at 1 cm: its ROI's fine planes hold about 7,100
+    words, more than a compaction chunk stages in shared memory, so its
+    chunks read the grid from global memory; the ball's small ROI in the
+    same frame is staged.  Both give the oracle's vertices and triangles."""
+    from synth.scenes import Ellipsoid
+    n, r, h = 8, 9.0, 5.0
+    cs = [(r * math.cos(2 * math.pi * k / n), r * math.sin(2 * math.pi * k / n), h) for k in range(n)]
+    rig = _make_rig("disc", cs, [(0, 0, 0.3)] * n, 500.0, 640, 360, _gen("disc/rig"),
+                    (-3.0, -3.0, 0.0), (3.0, 3.0, 0.8), 0.05, 0.01, 7)
+    objs = [Ellipsoid(centre=np.array([0.0, 0.0, 0.3]), rot=np.eye(3), axes=np.array([2.3, 2.3, 0.1]),
+                      colour=(200, 60, 40), obj=0),
+            Ellipsoid(centre=np.array([2.75, 2.75, 0.5]), rot=np.eye(3), axes=np.full(3, 0.12),
+                      colour=(40, 60, 200), obj=1)]
+    fr = render(rig, objs, index=0, config_tag="disc")
+    caps = dict(max_fine_words=1 << 20, max_verts=1 << 21, max_tris=1 << 22)
+    ref = compare(rig, fr, run_gpu(rig, [fr], caps=caps)[0])
+    nxw = [(r.fdim[0] + 2 + 31) // 32 for r in ref.rois]
+    assert max(w * (r.fdim[1] + 2) for w, r in zip(nxw, ref.rois)) > 6144
+    assert min(w * (r.fdim[1] + 2) for w, r in zip(nxw, ref.rois)) < 1000
+
+
 def test_ragged_image_width():
     """Images whose width is not a multiple of 32 (scalar packing path, partial
     last word of every silhouette row)."""
