@@ -59,8 +59,9 @@ FP32_LANES_PER_SM = 128
 # the current kernels, scaled to a launch by its frame count.  None for a
 # kernel changed since that capture.
 DRAM_BYTES_PER_FRAME = {"k_fine_carve": 7.29472e6 / 4, "k_bisect": (17.210368e6 + 9216) / 4,
-                        "k_coarse_carve": (4.332032e6 + 5120) / 4, "k_zbuffer": None,
-                        "k_zbuffer_cams<2>": None, "k_zbuffer_cams<4>": None}
+                        "k_coarse_carve": (4.332032e6 + 5120) / 4,
+                        "k_zbuffer": (178.829824e6 + 10.511616e6) / 4, "k_zbuffer_cams<2>": None,
+                        "k_zbuffer_cams<4>": (179.497216e6 + 10.753024e6) / 4}
 
 
 def parse_args():
