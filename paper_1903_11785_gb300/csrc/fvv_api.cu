@@ -232,6 +232,7 @@ fvv_status make_plan(const fvv_rig_desc* d, const fvv_recon_params* p, Plan& pl,
     take(L.emask, (size_t)fw * 12);
     take(L.vpre, (size_t)fw * 4);
     take(L.chunk_st, (size_t)g.max_chunks * 16);
+    take(L.chunk_len, (size_t)g.max_chunks * 4);
     take(L.vrec, (size_t)mv * 8);
     take(L.verts, (size_t)mv * 12);
     take(L.tris, (size_t)mt * 12);

@@ -17,6 +17,10 @@
 namespace fvv {
 
 constexpr int kMaxComponents = 8192;  // raw components sortable by one block
+// Words of the slab the MC compaction stages per 256-word chunk: the chunk
+// and the neighbours its cells reach (a word in +x, a row in +y, a plane in
+// +z).  Chunks whose ROIs reach further read global memory instead.
+constexpr uint32_t kSlabWords = 6144;
 constexpr int kMaxRois = 4096;
 constexpr int kChunk = 256;           // fine words per scan chunk (= block size)
 constexpr uint32_t kEmptyDepth = 0xFFFFFFFFu;  // depth-buffer bits meaning +inf
@@ -108,6 +112,7 @@ struct Layout {
     size_t emask;               // uint32 x3 bipolar-edge masks per fine word
     size_t vpre;                // uint32 exclusive vertex prefix per fine word
     size_t chunk_st;            // uint64 x2 per 256-word chunk: look-back states (vertices, triangles)
+    size_t chunk_len;           // uint32 per chunk: words of its staged slab (a multiple of 4), 0: not staged
     size_t vrec;                // uint64 vertex records, max_verts
     size_t verts;               // float x3, max_verts
     size_t tris;                // uint32 x3, max_tris

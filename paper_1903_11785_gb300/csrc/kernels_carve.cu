@@ -118,10 +118,28 @@ __global__ void __launch_bounds__(256) k_clear_fine(const __grid_constant__ Layo
     const uint32_t nwords = info->n_words;
     uint32_t* fine = slot_ptr<uint32_t>(L, slot, L.fine);
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) fine[w] = 0u;
-    // the compaction's look-back states of this reconstruction's chunks
+    // the compaction's look-back states of this reconstruction's chunks, and
+    // each chunk's slab: words lo .. hi-1, hi past the farthest neighbour of
+    // its words, in whole 16-byte units (the fine array is padded to 256
+    // bytes), or 0 when that is more than kSlabWords
+    const uint32_t nchunks = info->n_chunks;
+    const int nrois = info->n_rois;
+    const DRoi* rois = slot_ptr<DRoi>(L, slot, L.rois);
     unsigned long long* cst = slot_ptr<unsigned long long>(L, slot, L.chunk_st);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 2u * info->n_chunks; i += gridDim.x * blockDim.x)
-        cst[i] = 0ull;
+    uint32_t* clen = slot_ptr<uint32_t>(L, slot, L.chunk_len);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nchunks; i += gridDim.x * blockDim.x) {
+        cst[2 * (size_t)i] = 0ull;
+        cst[2 * (size_t)i + 1] = 0ull;
+        const uint32_t lo = i * kChunk, last = min(lo + (uint32_t)kChunk, nwords) - 1u;
+        const int k0 = roi_of_word(rois, nrois, lo), k1 = roi_of_word(rois, nrois, last);
+        uint32_t reach = 0;
+        for (int k = k0; k <= k1; ++k) {
+            const uint32_t rs = (uint32_t)rois[k].nxw;
+            reach = max(reach, 1u + rs + rs * (uint32_t)(rois[k].fdim[1] + 2));
+        }
+        const uint32_t n4 = (min(nwords, last + 1u + reach) - lo + 3u) & ~3u;
+        clen[i] = n4 <= kSlabWords ? n4 : 0u;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) info->next_tile = 0u;
 }
 

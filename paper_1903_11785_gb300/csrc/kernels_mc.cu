@@ -250,28 +250,42 @@ __device__ __forceinline__ unsigned long long ld_state(const unsigned long long*
 // before the kernel gives up on it and sets FVV_FLAG_LOOP.
 constexpr int kMaxPolls = 1 << 22;
 
-// Count j (0 vertices, 1 triangles) of the chunks before chunk c: the
-// states of c-1, c-2, ... are added until one holds an inclusive count.
-// False if the polls ran out (sum then incomplete).
-__device__ __forceinline__ bool look_back(const unsigned long long* st, uint32_t c, int j, unsigned long long& sum,
-                                          int& polls) {
-    sum = 0;
-    for (uint32_t q = c; q-- > 0;) {
-        unsigned long long s = ld_state(st + 2 * (size_t)q + j);
-        while ((s >> 62) == 0ull) {
+// Counts (vertices, triangles) of the chunks before chunk c, by warp 0: the
+// lanes read the states of 32 earlier chunks at a time (lane i: chunk
+// top - i), wait until all 32 are published, and add the values from the
+// nearest chunk back to the first inclusive one; without an inclusive one
+// in the window, all 32 and the window before.  False if the polls ran out.
+__device__ __forceinline__ bool look_back_warp(const unsigned long long* st, uint32_t c, unsigned long long& sv,
+                                               unsigned long long& stt) {
+    const int lane = threadIdx.x & 31;
+    sv = stt = 0;
+    bool need_v = true, need_t = true;
+    int polls = 0;
+    for (long long top = (long long)c - 1; top >= 0 && (need_v || need_t);) {
+        const long long q = top - lane;
+        // chunks before chunk 0 read as an inclusive zero, which ends the walk
+        const unsigned long long a = q >= 0 ? ld_state(st + 2 * q) : kStInc;
+        const unsigned long long b = q >= 0 ? ld_state(st + 2 * q + 1) : kStInc;
+        if (__any_sync(kFull, (a >> 62) == 0ull || (b >> 62) == 0ull)) {
             if (++polls > kMaxPolls) return false;
-            s = ld_state(st + 2 * (size_t)q + j);
+            continue;
         }
-        sum += s & kStVal;
-        if ((s >> 62) == 2ull) return true;
+        const unsigned iv = __ballot_sync(kFull, (a >> 62) == 2ull), it = __ballot_sync(kFull, (b >> 62) == 2ull);
+        const int lv = iv ? __ffs(iv) - 1 : 31, lt = it ? __ffs(it) - 1 : 31;
+        unsigned long long xv = (need_v && lane <= lv) ? (a & kStVal) : 0ull;
+        unsigned long long xt = (need_t && lane <= lt) ? (b & kStVal) : 0ull;
+        for (int o = 16; o > 0; o >>= 1) {
+            xv += __shfl_xor_sync(kFull, xv, o);
+            xt += __shfl_xor_sync(kFull, xt, o);
+        }
+        sv += xv;
+        stt += xt;
+        need_v = need_v && !iv;
+        need_t = need_t && !it;
+        top -= 32;
     }
-    return true;   // (chunk 0 is always inclusive)
+    return true;
 }
-
-// Words of a staged slab: a chunk's 256 words and the neighbours its cells
-// reach (a word in +x, a row in +y, a plane in +z).  Chunks whose ROIs reach
-// further read the grid from global memory instead.
-constexpr uint32_t kSlabWords = 6144;
 
 // Vertex record: ROI (14 bits) | axis (2) | ON at lower sample (1) | xp, yp, zp (15 bits each).
 __device__ __forceinline__ uint64_t pack_vrec(int k, int axis, int s0on, int xp, int yp, int zp) {
@@ -323,6 +337,7 @@ __global__ void __launch_bounds__(kChunk) k_mc_compact(const __grid_constant__ G
     uint64_t* vrec = slot_ptr<uint64_t>(L, slot, L.vrec);
     uint64_t* trec = slot_ptr<uint64_t>(L, slot, L.trec);
     unsigned long long* cst = slot_ptr<unsigned long long>(L, slot, L.chunk_st);
+    const uint32_t* clen = slot_ptr<uint32_t>(L, slot, L.chunk_len);
     uint32_t parity = 0;
     bool pending = false;   // a copy whose wait ran out may still be in flight (thread 0's view)
     RoiCursor p;
@@ -331,23 +346,12 @@ __global__ void __launch_bounds__(kChunk) k_mc_compact(const __grid_constant__ G
             const uint32_t c = nchunks ? atomicAdd(&info->next_chunk, 1u) : 0u;
             s_c = c;
             s_use = 0;
-            if (c < nchunks && !pending) {
-                // the slab: words lo .. hi-1, hi past the farthest neighbour of the chunk's words
-                const uint32_t lo = c * kChunk, last = min(lo + (uint32_t)kChunk, nwords) - 1u;
-                const int k0 = roi_of_word(rois, nrois, lo), k1 = roi_of_word(rois, nrois, last);
-                uint32_t reach = 0;
-                for (int k = k0; k <= k1; ++k) {
-                    const uint32_t rs = (uint32_t)rois[k].nxw;
-                    reach = max(reach, 1u + rs + rs * (uint32_t)(rois[k].fdim[1] + 2));
-                }
-                const uint32_t hi = min(nwords, last + 1u + reach);
-                const uint32_t n4 = (hi - lo + 3u) & ~3u;   // whole 16-byte units (inside the array's padding)
-                if (n4 <= kSlabWords) {
-                    s_use = 1;
-                    fence_proxy_async();
-                    mbar_expect_tx(&bar, n4 * 4u);
-                    bulk_copy_g2s(slab, fine + lo, n4 * 4u, &bar);
-                }
+            const uint32_t n4 = c < nchunks && !pending ? __ldcg(clen + c) : 0u;   // (k_clear_fine)
+            if (n4) {
+                s_use = 1;
+                fence_proxy_async();
+                mbar_expect_tx(&bar, n4 * 4u);
+                bulk_copy_g2s(slab, fine + c * kChunk, n4 * 4u, &bar);
             }
         }
         __syncthreads();
@@ -391,30 +395,33 @@ __global__ void __launch_bounds__(kChunk) k_mc_compact(const __grid_constant__ G
         uint32_t tv, tt;
         const uint32_t ev = block_exclusive_scan(vc, sh, tv);
         const uint32_t et = block_exclusive_scan(tc, sh, tt);
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
             unsigned long long bv = 0, bt = 0;
-            int polls = 0;
             bool ok = true;
             if (c > 0) {
-                st_state(cst + 2 * (size_t)c, kStAgg | tv);
-                st_state(cst + 2 * (size_t)c + 1, kStAgg | tt);
-                ok = look_back(cst, c, 0, bv, polls) && look_back(cst, c, 1, bt, polls);
+                if (threadIdx.x == 0) {
+                    st_state(cst + 2 * (size_t)c, kStAgg | tv);
+                    st_state(cst + 2 * (size_t)c + 1, kStAgg | tt);
+                }
+                ok = look_back_warp(cst, c, bv, bt);
             }
-            st_state(cst + 2 * (size_t)c, kStInc | ((bv + tv) & kStVal));
-            st_state(cst + 2 * (size_t)c + 1, kStInc | ((bt + tt) & kStVal));
-            if (!ok) atomicOr(&info->flags, (unsigned)FVV_FLAG_LOOP);
-            s_base[0] = bv;
-            s_base[1] = bt;
-            if (c == nchunks - 1u) {
-                // totals and capacities (the records past a capacity were not written)
-                const unsigned long long nv = bv + tv, nt = bt + tt;
-                unsigned fl = 0;
-                if (nv > g.max_verts) fl |= FVV_FLAG_VERTS;
-                if (nt > g.max_tris) fl |= FVV_FLAG_TRIS;
-                if (fl) atomicOr(&info->flags, fl);
-                info->n_verts = fl ? 0u : (uint32_t)nv;
-                info->n_tris = fl ? 0u : (uint32_t)nt;
-                if (fl) info->n_words = 0;   // nothing downstream runs on this frame
+            if (threadIdx.x == 0) {
+                st_state(cst + 2 * (size_t)c, kStInc | ((bv + tv) & kStVal));
+                st_state(cst + 2 * (size_t)c + 1, kStInc | ((bt + tt) & kStVal));
+                if (!ok) atomicOr(&info->flags, (unsigned)FVV_FLAG_LOOP);
+                s_base[0] = bv;
+                s_base[1] = bt;
+                if (c == nchunks - 1u) {
+                    // totals and capacities (the records past a capacity were not written)
+                    const unsigned long long nv = bv + tv, nt = bt + tt;
+                    unsigned fl = 0;
+                    if (nv > g.max_verts) fl |= FVV_FLAG_VERTS;
+                    if (nt > g.max_tris) fl |= FVV_FLAG_TRIS;
+                    if (fl) atomicOr(&info->flags, fl);
+                    info->n_verts = fl ? 0u : (uint32_t)nv;
+                    info->n_tris = fl ? 0u : (uint32_t)nt;
+                    if (fl) info->n_words = 0;   // nothing downstream runs on this frame
+                }
             }
         }
         __syncthreads();
