@@ -643,7 +643,7 @@ def run_ours(args):
         for _ in range(3):
             e2e_step()
         ok = all(torch.equal(o["verts"], r.results(i)["verts"].cpu()) for i, o in zip(slots[:2], outs[:2]))
-        ks = max(10, args.steps)
+        ks = max(30, args.steps)   # single slow steps (35-55 ms) occur; more steps dilute them
         torch.cuda.synchronize()
         per = []
         t0 = time.perf_counter()
