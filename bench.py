@@ -60,8 +60,8 @@ FP32_LANES_PER_SM = 128
 # kernel changed since that capture.
 DRAM_BYTES_PER_FRAME = {"k_fine_carve": 7.29472e6 / 4, "k_bisect": (17.210368e6 + 9216) / 4,
                         "k_coarse_carve": (4.332032e6 + 5120) / 4,
-                        "k_zbuffer": (178.829824e6 + 10.511616e6) / 4, "k_zbuffer_cams<2>": None,
-                        "k_zbuffer_cams<4>": (179.497216e6 + 10.753024e6) / 4}
+                        "k_zbuffer<1>": None, "k_zbuffer<2>": None,
+                        "k_zbuffer<4>": (179.26144e6 + 9.915392e6) / 4}
 
 
 def parse_args():
@@ -542,7 +542,7 @@ def run_ours(args):
     }
     zc = r.get_tuning()["zbuffer_cams"]
     kernel_of = {"coarse": "k_coarse_carve", "fine": "k_fine_carve", "bisect": "k_bisect",
-                 "depth": "k_zbuffer" if zc == 1 else f"k_zbuffer_cams<{zc}>"}
+                 "depth": f"k_zbuffer<{zc}>"}
 
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     alu = measure_alu(fvv, torch, sms)

@@ -176,7 +176,7 @@ inline Tuning default_tuning() {
     }
     t.waves[FVV_TUNE_ZBUFFER] = 16;
     t.fine_tile = FVV_TILE_4x4x8;
-    t.zb_cams = 1;
+    t.zb_cams = 4;
     return t;
 }
 

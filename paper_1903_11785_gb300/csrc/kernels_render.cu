@@ -197,140 +197,64 @@ __device__ __forceinline__ void raster_tri(const Cam& c, const float* X, const f
     if (raster_setup(c, X, Y, Z, s)) raster_pixels((unsigned)c.W, s, sink);
 }
 
-// A warp's queue of (triangle, camera) pairs whose candidate box is not
-// empty: the homogeneous vertices, the box, the squared distance and, when a
-// block serves several cameras, the pair's image width and first pixel.
-constexpr int kZQueue = 64;
-struct ZQueue {
-    float xh[3][kZQueue], yh[3][kZQueue], wh[3][kZQueue];
-    float x0[kZQueue], x1[kZQueue], y0[kZQueue], y1[kZQueue];
-    uint32_t d2[kZQueue];
-    uint32_t w[kZQueue], off[kZQueue];
-};
+constexpr int kZQueue = 64;   // queue entries per camera and warp
 
-template <bool kCam>
-__device__ __forceinline__ void zq_put(ZQueue& q, int i, const TriSetup& s, uint32_t d2, const Cam& c) {
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        q.xh[j][i] = s.xh[j];
-        q.yh[j][i] = s.yh[j];
-        q.wh[j][i] = s.wh[j];
-    }
-    q.x0[i] = s.x0;
-    q.x1[i] = s.x1;
-    q.y0[i] = s.y0;
-    q.y1[i] = s.y1;
-    q.d2[i] = d2;
-    if (kCam) {
-        q.w[i] = (uint32_t)c.W;
-        q.off[i] = (uint32_t)c.pix_off;
-    }
-}
-
-// Eq. (4) for the queued pair i: its covered pixels keep the minimum of the
-// squared distance (sqrt is monotone, so the square root of that minimum is
-// the minimum distance itself, taken where the depth is read).  D is the
-// slot's depth array; W and off (the image width and first pixel) are the
-// block's camera's, or the queued ones when kCam.
-template <bool kCam>
-__device__ __forceinline__ void zq_draw(const ZQueue& q, int i, uint32_t* D, uint32_t W, uint32_t off) {
+// Draws the n (<= 32) queued triangles ids[0..n-1] in camera c, one per
+// lane: each is set up again from its record (the same arithmetic as when
+// it was queued, so the same candidate box) and its covered pixels keep the
+// minimum of the squared centroid distance (sqrt is monotone, so the square
+// root of that minimum is the minimum distance itself, taken where the
+// depth is read).
+__device__ __forceinline__ void zdraw_ids(const Cam& c, const uint32_t* ids, int n, const float4* tsoup,
+                                          uint32_t* D) {
+    const int lane = threadIdx.x & 31;
+    if (lane >= n) return;
+    const uint32_t t = ids[lane];
+    const float4 r0 = __ldg(tsoup + 3 * (size_t)t), r1 = __ldg(tsoup + 3 * (size_t)t + 1),
+                 r2 = __ldg(tsoup + 3 * (size_t)t + 2);
+    const float X[3] = {r0.x, r0.w, r1.z}, Y[3] = {r0.y, r1.x, r1.w}, Z[3] = {r0.z, r1.y, r2.x};
+    const float dx = fsub(r2.y, c.C[0]);
+    const float dy = fsub(r2.z, c.C[1]);
+    const float dz = fsub(r2.w, c.C[2]);
+    const uint32_t d2 = __float_as_uint(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
     TriSetup s;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        s.xh[j] = q.xh[j][i];
-        s.yh[j] = q.yh[j][i];
-        s.wh[j] = q.wh[j][i];
-    }
-    s.x0 = q.x0[i];
-    s.x1 = q.x1[i];
-    s.y0 = q.y0[i];
-    s.y1 = q.y1[i];
-    const uint32_t d2 = q.d2[i];
-    if (kCam) {
-        W = q.w[i];
-        off = q.off[i];
-    }
-    uint32_t* img = kCam ? D + off : D;
-    raster_pixels(W, s, [&](size_t pix) {
+    raster_setup(c, X, Y, Z, s);   // true, as when the triangle was queued
+    uint32_t* img = D + c.pix_off;
+    raster_pixels((unsigned)c.W, s, [&](size_t pix) {
         uint32_t* p = img + pix;
         if (__ldcg(p) > d2) atomicMin(p, d2);   // skip the atomic when already nearer
     });
 }
 
-// Grid (blocks, cameras, slots): the camera is uniform over a block, so its
-// matrix is read through uniform registers, and blocks are issued frame by
-// frame, so one frame's depth images are worked on together.  A warp takes 32
-// triangles at a time, one per lane, and sets them up (raster_setup); the
-// centroid ((v0 + v1) + v2) / 3 was formed once per triangle when the
-// triangle was emitted.  About 70% of the pairs have no candidate pixel
-// centre, so the others go to a per-warp queue and are drawn 32 at a time,
-// one per lane, instead of by 30% of the lanes while the rest wait.
-__global__ void __launch_bounds__(256) k_zbuffer(const __grid_constant__ CamSet cams, const __grid_constant__ Layout L,
-                                                 const __grid_constant__ SlotList sl) {
-    pdl_begin();
-    __shared__ ZQueue zq[8];   // one per warp (at most 256 threads)
-    const int slot = sl.s[blockIdx.z];
-    const Cam& c = cams.c[blockIdx.y];
-    const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
-    const uint32_t nt = info->n_words ? info->n_tris : 0u;
-    const float4* tsoup = slot_ptr<float4>(L, slot, L.tsoup);
-    uint32_t* D = slot_ptr<uint32_t>(L, slot, L.depth) + c.pix_off;
-    const int lane = threadIdx.x & 31;
-    ZQueue& q = zq[threadIdx.x >> 5];
-    int qn = 0;   // queued pairs, the same in every lane
-    uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
-    for (;;) {                                    // warp-uniform
-        const bool more = t0 < nt;
-        const uint32_t t = t0 + (uint32_t)lane;
-        TriSetup s;
-        uint32_t d2 = 0;
-        bool ok = false;
-        if (more && t < nt) {
-            const float4 r0 = __ldg(tsoup + 3 * (size_t)t), r1 = __ldg(tsoup + 3 * (size_t)t + 1);
-            const float X[3] = {r0.x, r0.w, r1.z}, Y[3] = {r0.y, r1.x, r1.w};
-            const float4 r2 = __ldg(tsoup + 3 * (size_t)t + 2);
-            const float Z[3] = {r0.z, r1.y, r2.x};
-            const float dx = fsub(r2.y, c.C[0]);
-            const float dy = fsub(r2.z, c.C[1]);
-            const float dz = fsub(r2.w, c.C[2]);
-            d2 = __float_as_uint(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
-            ok = raster_setup(c, X, Y, Z, s);
-        }
-        const unsigned m = __ballot_sync(kFull, ok);
-        if (ok) zq_put<false>(q, qn + __popc(m & ((1u << lane) - 1u)), s, d2, c);
-        qn += __popc(m);                          // < 32 before, so < 64 now
-        __syncwarp();
-        if (qn >= 32 || (!more && qn > 0)) {      // draw the last (up to) 32 queued, one per lane
-            const int k = min(qn, 32);
-            qn -= k;
-            if (lane < k) zq_draw<false>(q, qn + lane, D, (uint32_t)c.W, 0u);
-            __syncwarp();                         // read before the slots are reused
-        }
-        if (!more && qn == 0) break;
-        if (more) t0 += gridDim.x * blockDim.x;
-    }
-}
-
-// k_zbuffer with a block serving K > 1 cameras (grid (blocks, camera groups,
-// slots), cameras blockIdx.y * K ...): a lane reads its triangle's record
-// once and sets it up for each camera of the group in turn, so each record
-// is read once per K cameras instead of once per camera.  The queue then
-// holds pairs of several cameras, each with its image width and first pixel.
+// Eq. (4) depth images.  Grid (blocks, camera groups, slots): a block serves
+// K cameras (blockIdx.y * K ...; K = 1, 2 or 4, the autotuner's choice), the
+// same for all its threads, so their matrices are read through uniform
+// registers, and blocks are issued frame by frame, so one frame's depth
+// images are worked on together.  A warp takes 32 triangles at a time, one
+// per lane, reads each triangle's 48-byte record once (vertices and the
+// centroid ((v0 + v1) + v2) / 3 formed when the triangle was emitted) and
+// sets it up for each camera of the group in turn (raster_setup).  About 70%
+// of the (triangle, camera) pairs have no candidate pixel centre; the warp
+// queues the indices of the others, per camera, and draws them 32 at a
+// time, one per lane (zdraw_ids), instead of by 30% of the lanes while the
+// rest wait.  A queue entry is 4 bytes: the set-up is done again at drawing,
+// which costs less than keeping its 64 bytes in shared memory.
 template <int K>
-__global__ void __launch_bounds__(256, 4) k_zbuffer_cams(const __grid_constant__ CamSet cams,
-                                                      const __grid_constant__ Layout L,
-                                                      const __grid_constant__ SlotList sl) {
+__global__ void __launch_bounds__(256, 4) k_zbuffer(const __grid_constant__ CamSet cams,
+                                                    const __grid_constant__ Layout L,
+                                                    const __grid_constant__ SlotList sl) {
     pdl_begin();
-    __shared__ ZQueue zq[8];   // one per warp (at most 256 threads)
+    __shared__ uint32_t zq[8][K * kZQueue];   // per warp (at most 256 threads), per camera
     const int slot = sl.s[blockIdx.z];
     const int n0 = blockIdx.y * K;
+    const int kn = min(K, cams.n - n0);       // cameras of this group
     const SlotInfo* info = slot_ptr<SlotInfo>(L, slot, L.info);
     const uint32_t nt = info->n_words ? info->n_tris : 0u;
     const float4* tsoup = slot_ptr<float4>(L, slot, L.tsoup);
     uint32_t* D = slot_ptr<uint32_t>(L, slot, L.depth);
     const int lane = threadIdx.x & 31;
-    ZQueue& q = zq[threadIdx.x >> 5];
-    int qn = 0;   // queued pairs, the same in every lane
+    uint32_t* q = zq[threadIdx.x >> 5];
+    uint32_t qn = 0;   // queued triangles per camera, 8 bits each (the same in every lane; each < 64)
     for (uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < nt; t0 += gridDim.x * blockDim.x) {
         const uint32_t t = t0 + (uint32_t)lane;   // the loop condition is warp-uniform
         const bool have = t < nt;
@@ -342,35 +266,38 @@ __global__ void __launch_bounds__(256, 4) k_zbuffer_cams(const __grid_constant__
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            if (n0 + k >= cams.n) break;          // uniform
+            if (k >= kn) break;                   // uniform
             const Cam& c = cams.c[n0 + k];
             TriSetup s;
-            uint32_t d2 = 0;
             bool ok = false;
             if (have) {
                 const float X[3] = {r0.x, r0.w, r1.z}, Y[3] = {r0.y, r1.x, r1.w}, Z[3] = {r0.z, r1.y, r2.x};
-                const float dx = fsub(r2.y, c.C[0]);
-                const float dy = fsub(r2.z, c.C[1]);
-                const float dz = fsub(r2.w, c.C[2]);
-                d2 = __float_as_uint(fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz)));
                 ok = raster_setup(c, X, Y, Z, s);
             }
             const unsigned m = __ballot_sync(kFull, ok);
-            if (ok) zq_put<true>(q, qn + __popc(m & ((1u << lane) - 1u)), s, d2, c);
-            qn += __popc(m);                      // < 32 before, so < 64 now
-            __syncwarp();
-            if (qn >= 32) {                       // draw the last 32 queued, one per lane
-                qn -= 32;
-                zq_draw<true>(q, qn + lane, D, 0u, 0u);
-                __syncwarp();                     // read before the slots are reused
+            if (ok) q[k * kZQueue + ((qn >> (8 * k)) & 0xFFu) + __popc(m & ((1u << lane) - 1u))] = t;
+            qn += (uint32_t)__popc(m) << (8 * k);
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int k = 0; k < kn; ++k) {            // a camera with 32 queued: draw them
+            const uint32_t cnt = (qn >> (8 * k)) & 0xFFu;
+            if (cnt >= 32u) {
+                qn -= 32u << (8 * k);
+                zdraw_ids(cams.c[n0 + k], q + k * kZQueue + (cnt - 32u), 32, tsoup, D);
+                __syncwarp();                     // read before the entries are reused
             }
         }
     }
-    while (qn > 0) {                              // the rest, up to 32 at a time
-        const int k = min(qn, 32);
-        qn -= k;
-        if (lane < k) zq_draw<true>(q, qn + lane, D, 0u, 0u);
-        __syncwarp();
+#pragma unroll 1
+    for (int k = 0; k < kn; ++k) {                // the rest, up to 32 at a time
+        uint32_t cnt = (qn >> (8 * k)) & 0xFFu;
+        while (cnt > 0u) {
+            const uint32_t n = min(cnt, 32u);
+            cnt -= n;
+            zdraw_ids(cams.c[n0 + k], q + k * kZQueue + cnt, (int)n, tsoup, D);
+            __syncwarp();
+        }
     }
 }
 
@@ -550,9 +477,9 @@ cudaError_t launch_depth(const CamSet& cams, const Grid& g, const Layout& L, con
     const int gz = tuned_grid(tu, FVV_TUNE_ZBUFFER, sms, sl.n, (long long)g.max_tris, groups);
     const dim3 grid(gz, groups, sl.n), block(tu.threads[FVV_TUNE_ZBUFFER]);
     cudaError_t e;
-    if (K == 4) e = launch_pdl(k_zbuffer_cams<4>, grid, block, 0, st, cams, L, sl);
-    else if (K == 2) e = launch_pdl(k_zbuffer_cams<2>, grid, block, 0, st, cams, L, sl);
-    else e = launch_pdl(k_zbuffer, grid, block, 0, st, cams, L, sl);
+    if (K == 4) e = launch_pdl(k_zbuffer<4>, grid, block, 0, st, cams, L, sl);
+    else if (K == 2) e = launch_pdl(k_zbuffer<2>, grid, block, 0, st, cams, L, sl);
+    else e = launch_pdl(k_zbuffer<1>, grid, block, 0, st, cams, L, sl);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 

@@ -475,11 +475,11 @@ class Rig:
     def set_tuning(self, tuning):
         """tuning: as get_tuning returns it; "fine_tile" may be left out
         (4 x 4 x 8) and may be given as an (x, y, z) shape or an FVV_TILE_*
-        index; "zbuffer_cams" may be left out (1)."""
+        index; "zbuffer_cams" may be left out (4, the default)."""
         tile = tuning.get("fine_tile", FINE_TILES[0])
         tile = FINE_TILES.index(tuple(tile)) if not isinstance(tile, int) else tile
         cfg = [tuning[k][0] for k in TUNE_KNOBS] + [tuning[k][1] for k in TUNE_KNOBS] + [tile]
-        cfg.append(int(tuning.get("zbuffer_cams", 1)))
+        cfg.append(int(tuning.get("zbuffer_cams", 4)))
         _check(_lib.fvv_set_tuning(self.ptr, (C.c_int * len(cfg))(*cfg)), self.ptr)
 
     def set_graphs(self, enable=True):
