@@ -58,7 +58,7 @@ FP32_LANES_PER_SM = 128
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of a 4-frame launch of
 # the current kernels, scaled to a launch by its frame count.  None for a
 # kernel changed since that capture.
-DRAM_BYTES_PER_FRAME = {"k_fine_carve": 7.29472e6 / 4, "k_bisect": (17.210368e6 + 9216) / 4,
+DRAM_BYTES_PER_FRAME = {"k_fine_carve": 7.28576e6 / 4, "k_bisect": 17.22496e6 / 4,
                         "k_coarse_carve": (4.332032e6 + 5120) / 4,
                         "k_zbuffer<1>": None, "k_zbuffer<2>": None,
                         "k_zbuffer<4>": (179.26144e6 + 9.915392e6) / 4}

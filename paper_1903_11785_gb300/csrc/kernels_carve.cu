@@ -314,8 +314,18 @@ __device__ __forceinline__ void fine_tiles(const CamSet& cams, const Grid& g, co
         // the tile's samples, one sub-tile of 4 x 2 x 4 (one per lane) at a time
         const int nb = bgm ? __ffsll((long long)bgm) - 1 : ncam;
         const uint64_t before = nb >= 64 ? ~0ull : (1ull << nb) - 1ull;
-#pragma unroll 1
         constexpr int kSubsY = TY / kSubY, kSubTiles = kSubsY * (TZ / kSubZ);
+        if (nb < ncam && (~(fgm | bgm) & before) == 0ull) {
+            // Every camera before the first all-background one votes
+            // foreground on the whole tile: each sample stops at camera nb
+            // (nb + 1 tests) and none is occupied.  Count this lane's samples
+            // of the sub-tile walk below without walking it.
+            const int dy = fy - y0 - yi, dz = fz - z0 - zi;
+            const int ny_ = dy > 0 ? min((dy + kSubY - 1) / kSubY, kSubsY) : 0;
+            const int nz_ = dz > 0 ? min((dz + kSubZ - 1) / kSubZ, TZ / kSubZ) : 0;
+            if (x0 + xi < fx) tests += (unsigned)(ny_ * nz_ * (nb + 1));
+            continue;
+        }
         for (int sub = 0; sub < kSubTiles; ++sub) {
             const int sy0 = y0 + (sub % kSubsY) * kSubY, sz0 = z0 + (sub / kSubsY) * kSubZ;
             if (sy0 >= fy || sz0 >= fz) continue;          // the same in every lane

@@ -17,6 +17,8 @@
 //             rank of the edge inside its word.
 // Vertex and triangle order is therefore (ROI, key) and (ROI, cell, table
 // order): independent of scheduling, identical to a serial scan.
+#include <atomic>
+
 #include "fvv_device.cuh"
 
 namespace fvv {
@@ -507,22 +509,128 @@ __device__ __forceinline__ bool segment_all_fg(const CamT& c, const uint32_t* __
 
 // Sec. II-C, exact intersection: between the ON end a and the OFF end b of a
 // bipolar edge, `steps` times m = (a+b)/2, a = m if m is occupied else b = m;
-// the vertex is the final midpoint.  One vertex per thread.
+// the vertex is the final midpoint.
 //
 // Every point tested lies on the edge (up to rounding), so a camera that sees
 // the whole edge inside its silhouette (segment_all_fg) votes foreground for
 // all of them: it is decided once per edge, and only the other cameras are
-// tested at each midpoint, from a per-lane list.  A midpoint's first
+// tested at each midpoint, from the vertex's list.  A midpoint's first
 // background camera in index order is then the first listed camera that votes
 // background, so the occupancy and the test count (that camera's index + 1,
 // or N when the midpoint is occupied) are those of the plain early-exit loop
 // over all cameras.
+
+// The ends of vertex record `rec`'s grid edge: a the ON sample, b the OFF one.
+__device__ __forceinline__ void bisect_ends(uint64_t rec, const DRoi* rois, const Grid& g, float* a, float* b) {
+    const int k = (int)(rec & 0x3FFFu), axis = (int)(rec >> 14 & 3u), s0 = (int)(rec >> 16 & 1u);
+    const int q[3] = {(int)(rec >> 17 & 0x7FFFu), (int)(rec >> 32 & 0x7FFFu), (int)(rec >> 47 & 0x7FFFu)};
+    const DRoi& r = rois[k];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float c0 = fadd(r.fo[d], fmul(fadd((float)(q[d] - 1), 0.5f), g.sf));
+        const float c1 = fadd(r.fo[d], fmul(fadd((float)(q[d] - 1 + (d == axis)), 0.5f), g.sf));
+        a[d] = s0 ? c0 : c1;
+        b[d] = s0 ? c1 : c0;
+    }
+}
+
+// The cameras that must be tested at each midpoint of the edge (a, b) (bit n:
+// camera n); seen_fg: some camera votes foreground on the whole edge.
+__device__ __forceinline__ uint64_t bisect_undecided(const SmemCam* sc, int ncam, const uint32_t* __restrict__ sil,
+                                                     const float* a, const float* b, bool& seen_fg,
+                                                     unsigned long long& reads) {
+    uint64_t undecided = 0;
+    seen_fg = false;
+    // one compact loop over the cameras' fields in shared memory (the camera
+    // is the same in every lane): 16 inlined copies of this check cost more
+    // in instruction-cache misses than the loads
+#pragma unroll 1
+    for (int n = 0; n < ncam; ++n) {
+        const bool fg = segment_all_fg(sc[n], sil, a, b, reads);
+        undecided |= fg ? 0ull : 1ull << n;
+        seen_fg |= fg;
+    }
+    return undecided;
+}
+
+// The `steps` bisection steps of the edge (a, b) with the cameras of
+// `undecided` tested at each midpoint; a and b end as the last bracket.
+__device__ __forceinline__ void bisect_steps(const SmemCam* sc, int ncam, const uint32_t* __restrict__ sil, int steps,
+                                             bool abstain, uint64_t undecided, bool seen_fg, float* a, float* b,
+                                             unsigned long long& tests, unsigned long long& reads) {
+    for (int it = 0; it < steps; ++it) {
+        float m[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) m[d] = fmul(fadd(a[d], b[d]), 0.5f);
+        int stop = -1;
+        bool voted = !abstain || seen_fg;
+        for (uint64_t u = undecided; u; u &= u - 1) {
+            const int n = __ffsll((long long)u) - 1;
+            const SmemCam& c = sc[n];
+            float xp, yp, wp;
+            project(c.P, m[0], m[1], m[2], xp, yp, wp);
+            const float rw = rcp_approx(wp);
+            const int px = pixel_floor(xp, wp, rw, c.Wf);
+            const int py = pixel_floor(yp, wp, rw, c.Hf);
+            const bool in = wp > 0.0f && (unsigned)px < (unsigned)c.W && (unsigned)py < (unsigned)c.H;
+            const uint32_t word =
+                in ? __ldg(sil + c.bit_off + (unsigned)py * (unsigned)c.Wq + ((unsigned)px >> 5)) : 0u;
+            reads += in ? 1u : 0u;
+            const bool bit = (word >> (px & 31)) & 1u;
+            if (abstain ? (in && !bit) : !bit) {
+                stop = n;
+                break;
+            }
+            voted |= bit;
+        }
+        tests += stop < 0 ? (unsigned)ncam : (unsigned)(stop + 1);
+        const bool on = stop < 0 && voted;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            a[d] = on ? m[d] : a[d];
+            b[d] = on ? b[d] : m[d];
+        }
+    }
+}
+
+// Vertices a warp sorts at once, per lane, and the bucket of the sort that
+// holds every list of kSortCap - 1 or more cameras (one more bucket, the
+// last, holds the window's empty places).
+constexpr int kBisectWin = 4;
+constexpr int kSortCap = 7;
+constexpr int kSortBuckets = kSortCap + 1;
+constexpr int kSortPerLane = kSortBuckets * kBisectWin / 32;   // sort counters per lane
+static_assert(kSortBuckets * kBisectWin % 32 == 0 && kBisectWin <= 8, "sort counters");
+
+// Per-warp shared memory of the sorted path (dynamic shared memory, one per
+// warp of the block).
+struct BisectWarpSmem {
+    unsigned long long und[32 * kBisectWin];   // undecided cameras, in window order
+    uint32_t id[32 * kBisectWin];              // vertex | seen_fg << 31, or ~0u for an empty place
+    uint8_t perm[32 * kBisectWin];             // window places in sorted order
+    int cnt[kSortBuckets * kBisectWin];        // bucket-major counts, then their exclusive prefix
+};
+
+// One vertex per thread.  Lanes whose undecided lists differ in length idle in
+// the midpoint loop while the longest list is walked (about 42% of the lanes
+// busy there in vertex order, on a CPU model of a volleyball-shaped frame).
+// When a slot has enough vertices for every warp of the launch that can be
+// resident for it (`resident_warps`) to take two windows of 32 * kv
+// consecutive vertices (kv = 2 or 4), each warp takes such windows instead:
+// it finds every vertex's undecided cameras, sorts the window's vertices by
+// the length of that list (a counting sort in the warp's shared memory, no
+// block barrier) and then bisects them 32 at a time in that order, so that a
+// warp's lanes walk lists of about the same length.  Each vertex's
+// arithmetic is the same in both orders; only the lane that does it changes.
 template <int NC>
 __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet cams, const __grid_constant__ Grid g,
-                                                const __grid_constant__ Layout L, const __grid_constant__ SlotList sl) {
+                                                const __grid_constant__ Layout L, const __grid_constant__ SlotList sl,
+                                                uint32_t resident_warps) {
     pdl_begin();
     __shared__ unsigned long long sh_t[32];
     __shared__ SmemCam sc[FVV_MAX_CAMS];
+    extern __shared__ __align__(16) unsigned char bisect_smem[];   // BisectWarpSmem per warp
+    BisectWarpSmem* wsm = reinterpret_cast<BisectWarpSmem*>(bisect_smem);
     const int ncam = NC > 0 ? NC : cams.n;
     load_smem_cams(cams, ncam, sc);
     __syncthreads();
@@ -535,68 +643,98 @@ __global__ void __launch_bounds__(256) k_bisect(const __grid_constant__ CamSet c
     const uint64_t* vrec = slot_ptr<uint64_t>(L, slot, L.vrec);
     float* verts = slot_ptr<float>(L, slot, L.verts);
     unsigned long long tests = 0, reads = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
-        const uint64_t rec = vrec[i];
-        const int k = (int)(rec & 0x3FFFu), axis = (int)(rec >> 14 & 3u), s0 = (int)(rec >> 16 & 1u);
-        const int q[3] = {(int)(rec >> 17 & 0x7FFFu), (int)(rec >> 32 & 0x7FFFu), (int)(rec >> 47 & 0x7FFFu)};
-        const DRoi& r = rois[k];
-        float a[3], b[3];
+    const uint32_t nthreads = gridDim.x * blockDim.x;
+    int kv = 1;                                    // the same in every block of the slot
+    for (int k = kBisectWin; k >= 2; k >>= 1)
+        if (kv == 1 && (unsigned long long)nv >= 64ull * resident_warps * (unsigned)k) kv = k;
+    if (kv == 1 || g.steps == 0) {
+        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += nthreads) {
+            float a[3], b[3];
+            bisect_ends(vrec[i], rois, g, a, b);
+            bool seen_fg = false;
+            const uint64_t undecided = g.steps > 0 ? bisect_undecided(sc, ncam, sil, a, b, seen_fg, reads) : 0ull;
+            bisect_steps(sc, ncam, sil, g.steps, abstain, undecided, seen_fg, a, b, tests, reads);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const float c0 = fadd(r.fo[d], fmul(fadd((float)(q[d] - 1), 0.5f), g.sf));
-            const float c1 = fadd(r.fo[d], fmul(fadd((float)(q[d] - 1 + (d == axis)), 0.5f), g.sf));
-            a[d] = s0 ? c0 : c1;
-            b[d] = s0 ? c1 : c0;
+            for (int d = 0; d < 3; ++d) verts[3 * (size_t)i + d] = fmul(fadd(a[d], b[d]), 0.5f);
         }
-        // cameras that must be tested at each midpoint (bit n: camera n)
-        uint64_t undecided = 0;
-        bool seen_fg = false;          // ABSTAIN: some camera votes foreground everywhere
-        if (g.steps > 0) {
-            // one compact loop over the cameras' fields in shared memory (the
-            // camera is the same in every lane): 16 inlined copies of this
-            // check cost more in instruction-cache misses than the loads
-#pragma unroll 1
-            for (int n = 0; n < ncam; ++n) {
-                const bool fg = segment_all_fg(sc[n], sil, a, b, reads);
-                undecided |= fg ? 0ull : 1ull << n;
-                seen_fg |= fg;
-            }
-        }
-        for (int it = 0; it < g.steps; ++it) {
-            float m[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) m[d] = fmul(fadd(a[d], b[d]), 0.5f);
-            int stop = -1;
-            bool voted = !abstain || seen_fg;
-            for (uint64_t u = undecided; u; u &= u - 1) {
-                const int n = __ffsll((long long)u) - 1;
-                const SmemCam& c = sc[n];
-                float xp, yp, wp;
-                project(c.P, m[0], m[1], m[2], xp, yp, wp);
-                const float rw = rcp_approx(wp);
-                const int px = pixel_floor(xp, wp, rw, c.Wf);
-                const int py = pixel_floor(yp, wp, rw, c.Hf);
-                const bool in = wp > 0.0f && (unsigned)px < (unsigned)c.W && (unsigned)py < (unsigned)c.H;
-                const uint32_t word =
-                    in ? __ldg(sil + c.bit_off + (unsigned)py * (unsigned)c.Wq + ((unsigned)px >> 5)) : 0u;
-                reads += in ? 1u : 0u;
-                const bool bit = (word >> (px & 31)) & 1u;
-                if (abstain ? (in && !bit) : !bit) {
-                    stop = n;
-                    break;
+    } else {
+        const int lane = threadIdx.x & 31;
+        BisectWarpSmem& w = wsm[threadIdx.x >> 5];
+        const uint32_t win = 32u * (uint32_t)kv;
+        const uint32_t nwarps = nthreads >> 5;
+        // windows of the slot's vertices, taken by the warps in turn (the loop
+        // condition is the same in every lane)
+        for (uint32_t base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * win; base < nv;
+             base += nwarps * win) {
+            // (1) each lane's kv vertices: their undecided cameras
+            for (int j = 0; j < kv; ++j) {
+                const uint32_t i = base + (uint32_t)(j * 32 + lane);
+                uint64_t und = 0;
+                uint32_t id = ~0u;
+                if (i < nv) {
+                    float a[3], b[3];
+                    bisect_ends(vrec[i], rois, g, a, b);
+                    bool seen_fg;
+                    und = bisect_undecided(sc, ncam, sil, a, b, seen_fg, reads);
+                    id = i | (seen_fg ? 0x80000000u : 0u);
                 }
-                voted |= bit;
+                w.und[j * 32 + lane] = und;
+                w.id[j * 32 + lane] = id;
             }
-            tests += stop < 0 ? (unsigned)ncam : (unsigned)(stop + 1);
-            const bool on = stop < 0 && voted;
+            // (2) counting sort of the window's places by list length
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                a[d] = on ? m[d] : a[d];
-                b[d] = on ? b[d] : m[d];
+            for (int e = 0; e < kSortPerLane; ++e) w.cnt[kSortPerLane * lane + e] = 0;
+            __syncwarp();
+            // a place's key and its rank among the lanes of its window row with
+            // that key (worked out twice, so that nothing stays in registers)
+            auto place = [&](int j, int& key, int& rank) {
+                const int p = j * 32 + lane;
+                key = w.id[p] == ~0u ? kSortCap : min(__popcll(w.und[p]), kSortCap - 1);
+                const unsigned same = __match_any_sync(kFull, key);
+                rank = __popc(same & ((1u << lane) - 1u));
+                return __popc(same);
+            };
+            for (int j = 0; j < kv; ++j) {
+                int key, rank;
+                const int n = place(j, key, rank);
+                if (rank == 0) w.cnt[key * kBisectWin + j] = n;
             }
+            __syncwarp();
+            {   // exclusive prefix of the counts (bucket-major, then window row)
+                int c[kSortPerLane], incl = 0;
+#pragma unroll
+                for (int e = 0; e < kSortPerLane; ++e) incl += c[e] = w.cnt[kSortPerLane * lane + e];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += t;
+                }
+#pragma unroll
+                for (int e = kSortPerLane - 1; e >= 0; --e) w.cnt[kSortPerLane * lane + e] = incl -= c[e];
+            }
+            __syncwarp();
+            for (int j = 0; j < kv; ++j) {
+                int key, rank;
+                place(j, key, rank);
+                w.perm[w.cnt[key * kBisectWin + j] + rank] = (uint8_t)(j * 32 + lane);
+            }
+            __syncwarp();
+            // (3) the bisections, 32 at a time in sorted order (empty places last)
+            for (int j = 0; j < kv; ++j) {
+                const int p = w.perm[j * 32 + lane];
+                const uint32_t id = w.id[p];
+                if (__all_sync(kFull, id == ~0u)) break;
+                if (id != ~0u) {
+                    const uint32_t i = id & 0x7FFFFFFFu;
+                    float a[3], b[3];
+                    bisect_ends(vrec[i], rois, g, a, b);
+                    bisect_steps(sc, ncam, sil, g.steps, abstain, w.und[p], (id >> 31) != 0u, a, b, tests, reads);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) verts[3 * (size_t)i + d] = fmul(fadd(a[d], b[d]), 0.5f);
+                }
+            }
+            __syncwarp();   // the window's shared memory is read before the next one writes it
         }
-#pragma unroll
-        for (int d = 0; d < 3; ++d) verts[3 * (size_t)i + d] = fmul(fadd(a[d], b[d]), 0.5f);
     }
     const unsigned long long t = block_sum<unsigned long long>(tests, sh_t);
     const unsigned long long rd = block_sum<unsigned long long>(reads, sh_t);
@@ -783,6 +921,24 @@ cudaError_t launch_mc_prefix(const Grid& g, const Layout& L, const SlotList& sl,
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// Resident blocks per SM of a k_bisect instantiation (index nc: its camera
+// count, 0 for the generic one) with `threads` threads and `smem` bytes of
+// dynamic shared memory, asked of the runtime once per shape and kept.
+template <class K>
+int bisect_blocks_per_sm(K kernel, int nc, int threads, size_t smem) {
+    static std::atomic<int> known[FVV_MAX_CAMS + 1][9];   // [nc][threads / 32]; 0: not asked yet
+    std::atomic<int>& slot = known[nc][threads / 32];
+    int n = slot.load(std::memory_order_relaxed);
+    if (n == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) {
+            (void)cudaGetLastError();
+            n = 1;
+        }
+        slot.store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
 cudaError_t launch_bisect(const CamSet& cams, const Grid& g, const Layout& L, const SlotList& sl, int sms,
                           const Tuning& tu, cudaStream_t st) {
     const int th = tu.threads[FVV_TUNE_BISECT];
@@ -792,7 +948,17 @@ cudaError_t launch_bisect(const CamSet& cams, const Grid& g, const Layout& L, co
         FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
     } else {
-#define FVV_LAUNCH(NC) launch_pdl(k_bisect<NC>, dim3(gv, sl.n), dim3(th), 0, st, cams, g, L, sl)
+        // the warps that can be resident for each slot: those launched, or the
+        // slot's share of what the GPU holds if that is fewer
+        const size_t smem = (size_t)(th / 32) * sizeof(BisectWarpSmem);
+        int per_sm = 0;
+#define FVV_OCC(NC) per_sm = bisect_blocks_per_sm(k_bisect<NC>, NC, th, smem)
+        FVV_DISPATCH_NC(cams.n, FVV_OCC)
+#undef FVV_OCC
+        const long long launched = (long long)gv * (th / 32);
+        const long long fit = (long long)std::max(per_sm, 1) * sms * (th / 32) / std::max(sl.n, 1);
+        const uint32_t resident = (uint32_t)std::max(1LL, std::min(launched, fit));
+#define FVV_LAUNCH(NC) launch_pdl(k_bisect<NC>, dim3(gv, sl.n), dim3(th), smem, st, cams, g, L, sl, resident)
         FVV_DISPATCH_NC(cams.n, FVV_LAUNCH)
 #undef FVV_LAUNCH
     }

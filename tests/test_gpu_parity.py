@@ -384,6 +384,52 @@ def test_abstain_policy_with_bisection():
     assert ref.tests_bisect > 0
 
 
+def _bisect_window(n_verts, n_slots, threads, waves):
+    """Vertices per lane that k_bisect sorts at once for a slot of n_verts
+    vertices when the launch has these shapes and the default capacities (1:
+    no sorting).  The kernel takes windows of 32 * k vertices (k = 4 or 2)
+    when there are at least two per warp that can be resident for the slot;
+    at the small grids used here that is every warp launched."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    warps = max(1, sms * min(waves, 16 * n_slots) // n_slots) * threads // 32
+    return 4 if n_verts >= 2 * warps * 32 * 4 else 2 if n_verts >= 2 * warps * 32 * 2 else 1
+
+
+@pytest.mark.parametrize("config,first,n_frames,threads,window",
+                         [("tiny", 3, 1, 32, 2), ("tiny", 5, 2, 32, 4), ("volleyball", 3, 1, 256, 4)])
+def test_bisection_in_sorted_windows_bit_exact(config, first, n_frames, threads, window):
+    """Bisection launches small enough that every warp takes windows of
+    32 x `window` vertices and sorts them by their number of undecided cameras
+    before bisecting them (the path of batched launches): every output equals
+    the oracle's, the last, partly filled window included."""
+    from paper_1903_11785_gb300 import fvv
+    rig = make_rig(config)
+    frames = [make_frame(config, first + i, rig=rig)[1] for i in range(n_frames)]
+    tuning = {k: (256, 8) for k in fvv.TUNE_KNOBS} | {"bisect": (threads, 1)}
+    gs = run_gpu(rig, frames, tuning=tuning)
+    for fr, g in zip(frames, gs):
+        assert _bisect_window(g["counts"]["n_verts"], n_frames, threads, 1) == window
+        assert g["counts"]["n_verts"] % (32 * window) != 0
+        compare(rig, fr, g)
+
+
+def test_bisection_in_sorted_windows_abstain():
+    """The sorted windows under ABSTAIN on 630 px images: a vertex carries
+    whether some camera saw its whole edge in the silhouette (its vote) into
+    the lane that bisects it."""
+    from paper_1903_11785_gb300 import fvv
+    n, r, h = 6, 6.0, 3.0
+    cs = [(r * math.cos(2 * math.pi * k / n), r * math.sin(2 * math.pi * k / n), h) for k in range(n)]
+    rig = _make_rig("ragged", cs, [(0, 0, 0.9)] * n, 480.0, 630, 349, _gen("ragged/rig"),
+                    (-2.0, -2.0, 0.0), (2.0, 2.0, 2.5), 0.05, 0.01, 9)
+    rig.oob_policy = ABSTAIN
+    fr = render(rig, scene_objects("tiny", 6), index=6, config_tag="ragged")
+    g = run_gpu(rig, [fr], tuning={k: (256, 8) for k in fvv.TUNE_KNOBS} | {"bisect": (32, 1)})[0]
+    assert _bisect_window(g["counts"]["n_verts"], 1, 32, 1) >= 2
+    ref = compare(rig, fr, g)
+    assert ref.tests_bisect > 0
+
+
 @pytest.mark.parametrize("n_cams", [5, 20, 64])
 def test_generic_and_large_camera_counts(n_cams):
     """5 cameras (no unrolled instantiation: the generic camera loops), 20
