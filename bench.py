@@ -581,8 +581,8 @@ def run_ours(args):
                    "peak": l2["gather_Gwords_per_s"], "unit": "G silhouette-word gathers/s",
                    "frac": gathers / 1e9 / l2["gather_Gwords_per_s"],
                    "definition": "silhouette words the kernel actually reads per second over the measured random "
-                                 "32-bit gather rate of L2: the utilisation of the L2 path the hull tests use; the "
-                                 "north star's 50% L2 target is read this way",
+                                 "32-bit gather rate of L2: the utilisation of the L2 path the hull tests use, "
+                                 "the reading taken for a 50% L2-roofline target",
                    "algorithmic_tests_G_per_s": tests_rate / 1e9,
                    "reads_per_test": reads_dom / max(tsum["tests_" + dom], 1),
                    "step_algorithmic": {"tests_G_per_s": step_tests_per_s / 1e9,
