@@ -923,7 +923,10 @@ cudaError_t launch_mc_prefix(const Grid& g, const Layout& L, const SlotList& sl,
 
 // Resident blocks per SM of a k_bisect instantiation (index nc: its camera
 // count, 0 for the generic one) with `threads` threads and `smem` bytes of
-// dynamic shared memory, asked of the runtime once per shape and kept.
+// dynamic shared memory, asked of the runtime once per shape and kept.  The
+// figure is that of the GPU current at the first call; on a host that mixes
+// GPU models it may not fit the others, which changes only how the
+// vertices are grouped into windows, never a result.
 template <class K>
 int bisect_blocks_per_sm(K kernel, int nc, int threads, size_t smem) {
     static std::atomic<int> known[FVV_MAX_CAMS + 1][9];   // [nc][threads / 32]; 0: not asked yet
