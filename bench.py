@@ -80,6 +80,9 @@ def parse_args():
                     help="serving: pinned masks read in place by the packing kernel, or copied by the copy engines")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--tuning-cache", default=None,
+                    help="JSON file of tuned launch shapes: reuse the entry for this GPU and workload, "
+                         "or autotune and add it")
     ap.add_argument("--zbuffer-cams", type=int, choices=(1, 2, 4), default=None,
                     help="cameras per z-buffer block, set after any tuning (for profiling one variant)")
     ap.add_argument("--no-cpu", action="store_true")
@@ -455,7 +458,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     tuning = None
     if not args.no_tune:
-        tuning = r.autotune(slots)          # launch shapes picked on this batch
+        if args.tuning_cache:               # shapes an earlier run picked for this GPU and workload
+            from paper_1903_11785_gb300 import tuning_cache
+            tuning, cached = tuning_cache.tuned(r, rig, slots, args.tuning_cache, torch.cuda.get_device_name(local))
+            tuning = dict(tuning, from_cache=cached)
+        else:
+            tuning = r.autotune(slots)      # launch shapes picked on this batch
         step()
         torch.cuda.synchronize()
     if args.zbuffer_cams is not None:
