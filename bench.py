@@ -734,7 +734,8 @@ def run_ours(args):
             "gtests_per_s": world * tests / (ms / 1000.0) / 1e9, "tests_per_frame": tests / F,
             "plain": {"frames_per_s": plain_fps, "latency_ms_p50": p50, "latency_ms_p99": p99, "frames": len(lat),
                       "cuda_graph": True},
-            "roofline": roofline, "e2e": e2e, "clocks": clk}
+            "roofline": roofline, "e2e": e2e, "clocks": clk,
+            "device": {"name": torch.cuda.get_device_name(local), "sms": int(sms)}}
     # the figures a reader of the last lines of the output needs, at the end
     line["headline"] = {
         "batched_fps": value, "graph": True, "gtests_per_s": line["gtests_per_s"],
