@@ -192,20 +192,25 @@ enum {
 };
 
 /* Bytes of device memory fvv_create_rig needs for these arguments (after the
- * defaults for zero capacities are applied). */
+ * defaults for zero capacities are applied): the memory that, as in
+ * Sec. III-B, is taken once at start-up.  desc, params and bytes are host
+ * pointers; NULL or an invalid argument gives FVV_ERR_INVALID_ARG. */
 fvv_status fvv_query_arena(const fvv_rig_desc *desc, const fvv_recon_params *params,
                            size_t *bytes);
 
-/* Create a rig: validate the cameras and parameters, lay out the arena and
- * build the marching-cubes table.  `arena` is a device buffer of at least
+/* Create a rig for cameras calibrated in advance and static (Sec. II-A), with
+ * all device memory taken at once (Sec. III-B): validate the cameras and
+ * parameters, lay out the arena and build the marching-cubes table
+ * (Sec. II-C).  `arena` is a device buffer of at least
  * fvv_query_arena bytes, aligned to 256 bytes, owned by the caller and kept
  * alive until fvv_destroy_rig; or NULL, in which case the library allocates
  * (and later frees) it.  On success *out is the new rig. */
 fvv_status fvv_create_rig(const fvv_rig_desc *desc, const fvv_recon_params *params,
                           void *arena, size_t arena_bytes, fvv_rig **out);
 
-/* Free the rig (and the arena if the library allocated it). Synchronises the
- * device first.  NULL is accepted. */
+/* Free the rig (and the arena if the library allocated it): the end of the
+ * start-up allocation of Sec. III-B. Synchronises the device first.  NULL is
+ * accepted. */
 fvv_status fvv_destroy_rig(fvv_rig *rig);
 
 /* Pack one frame's silhouettes into slot `slot` (step a0): masks[n] points
@@ -218,9 +223,10 @@ fvv_status fvv_destroy_rig(fvv_rig *rig);
 fvv_status fvv_upload_silhouettes(fvv_rig *rig, int slot, const uint8_t *const *masks,
                                   int masks_on_device, void *stream);
 
-/* fvv_upload_silhouettes for several frames at once: frame j's masks
- * (masks[j*n_cams + n] for camera n, memory as for fvv_upload_silhouettes)
- * go into slots[j], n_slots distinct slots (1..256).  One packing launch
+/* fvv_upload_silhouettes (the silhouettes of Sec. II-A, step a0) for several
+ * frames at once: frame j's masks (masks[j*n_cams + n] for camera n, memory
+ * as for fvv_upload_silhouettes) go into slots[j], n_slots distinct slots
+ * (1..256).  One packing launch
  * takes up to min(512, 2048 / n_cams) frames, so a batch costs a few
  * launches instead of one per frame.  Nothing is packed if an argument is
  * rejected. */
@@ -229,9 +235,14 @@ fvv_status fvv_upload_silhouettes_batch(fvv_rig *rig, const int *slots, int n_sl
                                         void *stream);
 
 /* Reconstruct the frames in `slots` (n_slots distinct slots, each uploaded):
- * coarse hull, CCL, filter and ROIs, fine hull, bisected marching-cubes mesh
- * and per-camera depth images (steps a1..a9).  All slots are processed by the
- * same launches.  No host synchronisation happens inside. */
+ * coarse hull (Sec. II-B-1), 26-connected components, the filter of Eq. (1)
+ * and the 3D ROIs (Sec. II-B-2), fine hull (Sec. II-B-3), marching-cubes
+ * mesh with each vertex placed by the surface rule (Sec. II-C, Eqs. (2)-(3))
+ * and per-camera depth images (Sec. II-D-1, Eq. (4)): steps a1..a9.  All
+ * slots are processed by the same launches.  No host synchronisation
+ * happens inside.  A NULL rig or slot list, a slot out of range or listed
+ * twice gives FVV_ERR_INVALID_ARG, a slot not uploaded FVV_ERR_NOT_READY,
+ * both with nothing launched. */
 fvv_status fvv_reconstruct(fvv_rig *rig, const int *slots, int n_slots, void *stream);
 
 /* Colour the meshes of `slots` for a virtual viewpoint (step a10, Sec. II-D-2
@@ -292,11 +303,14 @@ typedef struct {
 fvv_status fvv_get_results_batch(fvv_rig *rig, const int *slots, int n_slots, fvv_results_dst *dst,
                                  int dst_on_device, void *stream);
 
-/* Size in bytes of a debug view of slot (fvv_get_counts must have been
- * called after the reconstruction for FINE_BITS). */
+/* Size in bytes of a debug view of slot, an intermediate result of
+ * Sec. II-A to II-D-1 (fvv_get_counts must have been called after the
+ * reconstruction for FINE_BITS). */
 fvv_status fvv_debug_bytes(fvv_rig *rig, int slot, int what, size_t *bytes);
 
-/* Write a debug view of slot into device buffer dst (bytes from
+/* Write a debug view of slot (silhouette bits of Sec. II-A, coarse occupancy
+ * of Sec. II-B-1, labels of Sec. II-B-2, fine grids of Sec. II-B-3, depth
+ * images of Sec. II-D-1) into device buffer dst (bytes from
  * fvv_debug_bytes), enqueued on `stream`. */
 fvv_status fvv_get_debug(fvv_rig *rig, int slot, int what, void *dst, size_t bytes, void *stream);
 
@@ -396,18 +410,21 @@ fvv_status fvv_render_view(fvv_rig *rig, int slot, const uint8_t *const *rgb, in
                            const float *centre, int width, int height, uint64_t *key, uint8_t *out_rgb,
                            int32_t *out_cam, void *stream);
 
-/* Switch per-stage timing on (1) or off (0).  When on, each call records CUDA
- * events around its stages on its stream (no synchronisation). */
+/* Switch per-stage timing (the stage buckets of Table II) on (1) or off
+ * (0).  When on, each call records CUDA events around its stages on its
+ * stream (no synchronisation). */
 fvv_status fvv_set_timing(fvv_rig *rig, int enable);
 
-/* Wait for the recorded events and return, per stage, the summed device
- * milliseconds (ms[FVV_N_STAGES]) and the number of timed intervals
- * (calls[FVV_N_STAGES], may be NULL) since the previous fvv_get_timing or
- * fvv_set_timing; then start a new accumulation. */
+/* Wait for the recorded events and return, per stage (Table II's buckets),
+ * the summed device milliseconds (ms[FVV_N_STAGES]) and the number of timed
+ * intervals (calls[FVV_N_STAGES], may be NULL) since the previous
+ * fvv_get_timing or fvv_set_timing; then start a new accumulation. */
 fvv_status fvv_get_timing(fvv_rig *rig, float *ms, int *calls);
 
 /* Launch shapes of the five heaviest kernels, chosen per rig by fvv_autotune
- * (results never depend on them). */
+ * (results never depend on them).  Batching, autotuning and graphs have no
+ * counterpart in the paper, which runs one frame at a time with fixed launch
+ * shapes; they are services of this library. */
 enum {
     FVV_TUNE_COARSE = 0,     /* coarse hull                     */
     FVV_TUNE_FINE = 1,       /* fine hull                       */
@@ -450,10 +467,11 @@ fvv_status fvv_set_tuning(fvv_rig *rig, const int *config);
  * a change of tuning drops them. */
 fvv_status fvv_set_graphs(fvv_rig *rig, int enable);
 
-/* The marching-cubes table the library built from its face rule: ntri[256]
- * triangle counts and edges[256*12*3] cube-edge numbers (corner c = dx + 2dy
- * + 4dz; cube edge e has axis e/4 and lower corner with the other two
- * coordinates (e%4 & 1, e%4 >> 1) in axis order).  Host memory; no GPU needed. */
+/* The marching-cubes table (Sec. II-C) the library built from its face
+ * rule: ntri[256] triangle counts and edges[256*12*3] cube-edge numbers
+ * (corner c = dx + 2dy + 4dz; cube edge e has axis e/4 and lower corner with
+ * the other two coordinates (e%4 & 1, e%4 >> 1) in axis order).  Host
+ * memory; no GPU needed. */
 fvv_status fvv_mc_table(uint8_t *ntri, uint8_t *edges);
 
 /* L2 micro-benchmark (no counterpart in the paper): the memory side of the
@@ -483,13 +501,15 @@ fvv_status fvv_probe_l2(int mode, const void *buf, size_t bytes, int reps, uint3
  * nothing launched.  Time it with events on `stream`. */
 fvv_status fvv_probe_fma(int reps, float a, float b, float *out, int blocks, int threads, void *stream);
 
-/* Message of the last failure on rig (or of the last failed create if rig is
+/* Error reporting (no counterpart in the paper).
+ * Message of the last failure on rig (or of the last failed create if rig is
  * NULL).  The string stays valid until the next call on the rig. */
 const char *fvv_last_error(const fvv_rig *rig);
 
 /* Static name of a status code. */
 const char *fvv_status_string(fvv_status status);
 
+/* FVV_VERSION of the library (no counterpart in the paper). */
 int fvv_version(void);
 
 #ifdef __cplusplus
