@@ -444,7 +444,8 @@ enum { FVV_TILE_4x4x8 = 0, FVV_TILE_4x4x4 = 1, FVV_TILE_4x8x8 = 2, FVV_N_TILES =
  * triangle record is read once per that many cameras). */
 #define FVV_TUNE_INTS (2 * FVV_N_TUNE + 2)
 
-/* Time candidate launch shapes (threads per block 64/128/256 x resident
+/* Autotuning (no counterpart in the paper).
+ * Time candidate launch shapes (threads per block 64/128/256 x resident
  * blocks per SM 2/4/8/16/32/64) of each tunable kernel, for the fine hull
  * each tile shape too and for the z-buffer each number of cameras per block
  * (1, 2, 4), on the given slots, which must hold reconstructed
@@ -454,13 +455,15 @@ enum { FVV_TILE_4x4x8 = 0, FVV_TILE_4x4x4 = 1, FVV_TILE_4x8x8 = 2, FVV_N_TILES =
  * receives FVV_TUNE_INTS ints. */
 fvv_status fvv_autotune(fvv_rig *rig, const int *slots, int n_slots, void *stream, int *config);
 
-/* Read or set the configuration (FVV_TUNE_INTS ints as for fvv_autotune);
- * threads must be 32..256 in steps of 32, blocks per SM 1..64, the tile
- * shape one of FVV_TILE_*, the z-buffer cameras per block 1, 2 or 4. */
+/* Read or set the configuration (no counterpart in the paper):
+ * FVV_TUNE_INTS ints as for fvv_autotune; threads must be 32..256 in steps
+ * of 32, blocks per SM 1..64, the tile shape one of FVV_TILE_*, the z-buffer
+ * cameras per block 1, 2 or 4 (else FVV_ERR_INVALID_ARG). */
 fvv_status fvv_get_tuning(fvv_rig *rig, int *config);
 fvv_status fvv_set_tuning(fvv_rig *rig, const int *config);
 
-/* With graphs on (1), fvv_reconstruct records its launch sequence for each
+/* CUDA graphs (no counterpart in the paper).
+ * With graphs on (1), fvv_reconstruct records its launch sequence for each
  * distinct slot list into a CUDA graph the first time it sees the list and
  * replays that graph afterwards (up to 16 lists are kept).  Graphs are not
  * used on the legacy default stream (NULL), nor while per-stage timing is on;
@@ -506,7 +509,7 @@ fvv_status fvv_probe_fma(int reps, float a, float b, float *out, int blocks, int
  * NULL).  The string stays valid until the next call on the rig. */
 const char *fvv_last_error(const fvv_rig *rig);
 
-/* Static name of a status code. */
+/* Static name of a status code (no counterpart in the paper). */
 const char *fvv_status_string(fvv_status status);
 
 /* FVV_VERSION of the library (no counterpart in the paper). */
